@@ -1,0 +1,452 @@
+#!/usr/bin/env python3
+"""Benchmark: force evaluations per second of one kick-drift-kick leapfrog
+step (tree build + group walk + force sum + kicks/drift) on the 2.87M-particle
+NFW-halo-mix workload (theta = 0.6, eps = 5e-4), one GPU per rank.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  `value` is whole-job force evaluations/s
+(interactions summed over ranks / max-over-ranks device time of the K timed
+steps, CUDA events on the library's stream); `e2e` is the same metric with the
+step's inputs copied from pinned host memory and its result read back inside
+the timed region.  The path does not shard across GPUs here: N > 1 runs N
+independent replicas (weak scaling), with no collective on the data path.
+`--impl reference` times the CPU oracle as it stands on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "halomix2.87m"
+METRIC = "force evals/s & GFLOPS at median |da|/|a|<=1e-3, N=2.87M, learned vs fixed theta"
+UNIT = "force evals/s"
+FP32_OPS_PER_INTERACTION = 13   # FP32-pipe lane operations in the force kernel's inner loop
+FLOPS_CONVENTION = 38           # paper's flops per interaction
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--n-crit", type=int, default=None)
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--judge-targets", type=int, default=2048)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (100 ms) of the SM clock and throttle reasons."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.rows, self.err, self.proc = [], None, None
+        self.device_index = device_index
+
+    def _target(self):
+        try:
+            import torch
+            u = torch.cuda.get_device_properties(self.device_index).uuid
+            return ["-i", "GPU-" + str(u)]
+        except Exception:
+            return []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", *self._target()],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception as e:  # no nvidia-smi
+            self.err = str(e)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        rows = [r for t, r in self.rows if t0 - 0.15 <= t <= t1 + 0.15] or \
+            [r for _, r in self.rows]
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[4 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- helpers
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def force_traffic_record():
+    """DRAM bytes per force-kernel launch from the committed ncu summary,
+    valid only while the kernel source is the one that was profiled."""
+    path = os.path.join(ROOT, "profiles", "k_force_traffic.txt")
+    src = os.path.join(ROOT, "paper_0909_0541_gb300", "csrc", "nb_force.cu")
+    try:
+        rec = dict(l.split("=", 1) for l in open(path).read().split() if "=" in l)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != h:
+            return None
+        return float(rec["bytes_per_launch_scaled"])
+    except Exception:
+        return None
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        backend = "nccl" if dist.is_nccl_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(ps, w, seconds, seed=7):
+    """Force evaluations/s of the CPU oracle (tree build + group walk + FP64
+    force sum) on a bounded sample: the full tree is built and timed, then a
+    random sample of groups is walked and summed for about `seconds`; the
+    build time is charged in proportion to the sampled particles."""
+    import oracle
+    t0 = time.perf_counter()
+    T = oracle.Tree(ps.pos, ps.mass)
+    t_build = time.perf_counter() - t0
+    G = T.groups(w["n_crit"])
+    cnt = T.export()["count"][G]
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(G))
+    # calibrate on a small batch, then size the sample to the time budget
+    k0 = min(len(G), 64)
+    t0 = time.perf_counter()
+    _, _, pp, pc = T.forces(w["n_crit"], w["theta"], w["eps"], gsel=order[:k0])
+    t_cal = time.perf_counter() - t0
+    per_group = t_cal / k0
+    k1 = int(min(len(G) - k0, max(64, (seconds - t_build - t_cal) / max(per_group, 1e-9))))
+    sel = order[k0:k0 + k1]
+    t0 = time.perf_counter()
+    _, _, pp1, pc1 = T.forces(w["n_crit"], w["theta"], w["eps"], gsel=sel)
+    t_force = time.perf_counter() - t0
+    inter = pp + pc + pp1 + pc1
+    parts = int(cnt[order[:k0 + k1]].sum())
+    t_total = t_cal + t_force + t_build * parts / ps.n
+    return dict(value=inter / t_total, unit=UNIT, cores=oracle.num_threads(),
+                kind="oracle",
+                sample=(f"{WORKLOAD}: full tree build ({t_build:.2f} s, charged pro rata) + "
+                        f"walk and FP64 force sum of {k0 + k1} random groups "
+                        f"({parts} particles, {inter} interactions) in {t_cal + t_force:.1f} s"),
+                interactions=int(inter), seconds=t_total)
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import nbsynth
+    ps, w = nbsynth.workload(args.workload)
+    if args.n_crit:
+        w["n_crit"] = args.n_crit
+    if args.theta is not None:
+        w["theta"] = args.theta
+    import oracle
+    T = oracle.Tree(ps.pos, ps.mass)
+    G = T.groups(w["n_crit"])
+    rng = np.random.default_rng(11)
+    # each step: tree build + walk/force of a group sample (about 2 s of CPU)
+    per_step_groups = 400
+    total_i, total_t = 0, 0.0
+    for it in range(args.warmup + args.steps):
+        sel = rng.choice(len(G), min(per_step_groups, len(G)), replace=False)
+        t0 = time.perf_counter()
+        T2 = oracle.Tree(ps.pos, ps.mass)
+        t_b = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, _, pp, pc = T2.forces(w["n_crit"], w["theta"], w["eps"], gsel=sel)
+        t_f = time.perf_counter() - t0
+        del T2
+        cnt = T.export()["count"][G[sel]].sum()
+        if it >= args.warmup:
+            total_i += pp + pc
+            total_t += t_f + t_b * cnt / ps.n
+    v = total_i / total_t
+    ms = 1e3 * total_t / args.steps
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": ps.n, "theta": w["theta"], "eps": w["eps"],
+                   "n_crit": w["n_crit"], "parallelism": "host cores (oracle)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"per step: full tree build (charged pro rata) + walk and "
+                                   f"force of {per_step_groups} random groups"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import nbsynth
+    import paper_0909_0541_gb300 as nb
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ps, w = nbsynth.workload(args.workload)
+    if args.n_crit:
+        w["n_crit"] = args.n_crit
+    if args.theta is not None:
+        w["theta"] = args.theta
+    n = ps.n
+    stream = torch.cuda.Stream(device=dev)
+    ctx = nb.NBody(n, eps=w["eps"], theta=w["theta"], n_crit=w["n_crit"],
+                   precision=args.precision, sync_checks=True, stream=stream)
+    pos0 = torch.from_numpy(ps.pos).to(dev)
+    vel0 = torch.from_numpy(ps.vel).to(dev)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    pos, vel = pos0.clone(), vel0.clone()
+    dt = w["dt"]
+    with torch.cuda.stream(stream):
+        # first step synchronises: sizes the interaction-list storage
+        ctx.leapfrog_step(pos, vel, mass, dt)
+        ctx.set_sync_checks(False)
+        for _ in range(args.warmup):
+            ctx.leapfrog_step(pos, vel, mass, dt)
+        ctx.sync_status()
+        st0 = ctx.stats()
+        ctx.set_timing(True)
+        ctx.get_timing()
+        sampler = ClockSampler(local)
+        sampler.start()
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = sampler.mark()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.leapfrog_step(pos, vel, mass, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = sampler.mark()
+        barrier(ws)
+        clocks = sampler.stop(t0, t1)
+        ctx.sync_status()
+        timing = ctx.get_timing()
+        ctx.set_timing(False)
+        st1 = ctx.stats()
+    ms_total = e0.elapsed_time(e1)
+    inter = (st1["n_pp_total"] - st0["n_pp_total"]) + (st1["n_pc_total"] - st0["n_pc_total"])
+    ms_max = allreduce_max(ms_total, ws)
+    inter_all = allreduce_sum(float(inter), ws)
+    value = inter_all / (ms_max / 1e3)
+    ms_per_step = ms_max / args.steps
+
+    # ---- end to end: pinned host buffers in, result read back, every step
+    e2e = None
+    if not args.no_e2e:
+        hpos = torch.from_numpy(ps.pos.copy()).pin_memory()
+        hvel = torch.from_numpy(ps.vel.copy()).pin_memory()
+        hmass = torch.from_numpy(ps.mass.copy()).pin_memory()
+        with torch.cuda.stream(stream):
+            # untimed priming step: the context then holds a(x) for the host state
+            pos.copy_(hpos, non_blocking=True)
+            vel.copy_(hvel, non_blocking=True)
+            ctx.leapfrog_reset()
+            ctx.leapfrog_step(pos, vel, mass, dt)
+            hpos.copy_(pos, non_blocking=True)
+            hvel.copy_(vel, non_blocking=True)
+            torch.cuda.synchronize()
+            ctx.sync_status()
+            st_a = ctx.stats()
+            barrier(ws)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.steps):
+                pos.copy_(hpos, non_blocking=True)
+                vel.copy_(hvel, non_blocking=True)
+                mass.copy_(hmass, non_blocking=True)
+                ctx.leapfrog_step(pos, vel, mass, dt)
+                hpos.copy_(pos, non_blocking=True)
+                hvel.copy_(vel, non_blocking=True)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            barrier(ws)
+            ctx.sync_status()
+        st_b = ctx.stats()
+        ms_e2e = allreduce_max(f0.elapsed_time(f1), ws)
+        inter_e = allreduce_sum(float((st_b["n_pp_total"] - st_a["n_pp_total"]) +
+                                      (st_b["n_pc_total"] - st_a["n_pc_total"])), ws)
+        e2e = {"value": inter_e / (ms_e2e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(hpos.numel() * 8 + hvel.numel() * 8 + hmass.numel() * 4),
+               "d2h_bytes_per_step": int(hpos.numel() * 8 + hvel.numel() * 8),
+               "ms_per_step": ms_e2e / args.steps}
+
+    # ---- accuracy against the FP64 direct-sum judge (outside the timed regions)
+    with torch.cuda.stream(stream):
+        ctx.set_sync_checks(True)
+        ctx.build_tree(pos0, mass)
+        ctx.walk_groups(w["theta"], w["n_crit"])
+        acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        ctx.forces(w["eps"], acc, None, args.precision)
+        g = torch.Generator().manual_seed(99)
+        tg = torch.randperm(n, generator=g)[: args.judge_targets].to(dev)
+        aj, _ = nb.direct_sum(pos0, mass, w["eps"], tg, stream=stream)
+        torch.cuda.synchronize()
+    d = (acc[tg].double() - aj).norm(dim=1) / aj.norm(dim=1)
+    d = d.cpu().numpy()
+    accuracy = {"median_rel_err": float(np.median(d)), "p99_rel_err": float(np.percentile(d, 99)),
+                "targets": int(args.judge_targets), "judge": "nb_direct_sum (FP64 GPU direct sum)"}
+
+    # ---- roofline of the dominant kernel (force sum)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    force_ms, force_calls = timing["force"]
+    inter_per_launch = inter / max(force_calls, 1)
+    t_launch = force_ms / 1e3 / max(force_calls, 1)
+    achieved = FP32_OPS_PER_INTERACTION * inter_per_launch / t_launch / 1e12
+    peak = sms * 128 * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": force_traffic_record(),
+                "kernel": "k_force", "ops": "FP32-pipe lane ops (13 per interaction)",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
+                "frac_at_sampled_clock": (achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+                                          if clocks.get("sm_mhz") else None)}
+
+    phases = {k: {"ms_per_call": v[0] / max(v[1], 1), "calls": v[1]}
+              for k, v in timing.items() if k != "launches"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(ps, w, args.cpu_seconds)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "theta": w["theta"], "eps": w["eps"],
+                       "n_crit": w["n_crit"], "dt": dt, "precision": args.precision,
+                       "step": "KDK leapfrog: tree build + group walk + force + kicks/drift",
+                       "l2": "inputs larger than L2 (positions+velocities 138 MB, lists "
+                             f"{st1['list_entries'] * 20 / 1e9:.2f} GB per step)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "gflops_38": value * FLOPS_CONVENTION / 1e9,
+            "interactions_per_step": inter / args.steps,
+            "particle_forces_per_s": ws * n * args.steps / (ms_max / 1e3),
+            "accuracy": accuracy,
+            "phases_ms": phases,
+            "gpu_launches": int(timing["launches"]),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "stats": {k: st1[k] for k in ("n_cells", "n_groups", "list_entries", "max_list",
+                                          "list_capacity")},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * nb.h -- C ABI of libnb: the oct-tree group walk and softened gravity
+ * force of Nakasato, "Oct-tree Method on GPU" (arXiv:0909.0541), as
+ * hand-written CUDA for sm_103a (GB300).
+ *
+ * Conventions for every call
+ *   - Pointers named *_dev are device pointers owned by the caller (for
+ *     example torch tensors); *_host pointers are host memory owned by the
+ *     caller.  The library owns the tree, the groups, the interaction lists
+ *     and all scratch, allocated once by nb_create for cfg.max_n particles.
+ *   - Work is queued on cfg.stream.  With cfg.sync_checks != 0 each call
+ *     synchronises that stream before returning and reports device-side
+ *     errors (and nb_walk_groups grows the list storage by itself).  With
+ *     sync_checks == 0 calls do not synchronise, allocate nothing and can be
+ *     captured in a CUDA graph; device errors are latched and reported by
+ *     nb_sync_status or by the next call that synchronises.
+ *   - Return value: NB_OK (0) or a negative NB_ERR_* code.
+ *   - Units: G = 1.  Positions are FP64 (N x 3, row-major x,y,z per
+ *     particle), masses FP32, accelerations and potentials FP32, all in the
+ *     caller's particle order.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NB_OK 0
+#define NB_ERR_INVALID_ARG (-1) /* bad size, NULL pointer, theta < 0, ... */
+#define NB_ERR_CUDA (-2)        /* a CUDA runtime call failed             */
+#define NB_ERR_CAPACITY (-3)    /* an interaction list outgrew its slot    */
+#define NB_ERR_WALK_LIMIT (-4)  /* a walk did not advance (corrupt tree)   */
+#define NB_ERR_NONFINITE (-5)   /* a position is NaN or infinite           */
+#define NB_ERR_STATE (-6)       /* call order: build, then walk, then force */
+#define NB_ERR_NOMEM (-7)       /* device allocation failed                */
+
+/* accumulation modes of nb_forces */
+#define NB_FP32 0      /* plain FP32 sums                                   */
+#define NB_FP32_COMP 1 /* FP32 tile sums merged with Kahan compensation     */
+#define NB_FP64ACC 2   /* FP32 terms accumulated in FP64                    */
+
+typedef struct nb_ctx nb_ctx;
+
+typedef struct nb_config {
+    int64_t max_n;         /* particle capacity (>= 1)                       */
+    int64_t list_capacity; /* entries per group list; 0 = grow on demand     */
+    void *stream;          /* cudaStream_t; NULL = legacy default stream     */
+    int sync_checks;       /* see the conventions above                      */
+    int device;            /* CUDA device ordinal                            */
+    /* defaults used by nb_leapfrog_step */
+    float eps;             /* Plummer softening, >= 0                        */
+    float theta;           /* opening angle, >= 0 (0 = never accept a cell)  */
+    int n_crit;            /* maximum group size, >= 1                       */
+    int precision;         /* NB_FP32, NB_FP32_COMP or NB_FP64ACC            */
+} nb_config;
+
+typedef struct nb_stats {
+    int64_t n;             /* particles in the current tree                  */
+    int64_t n_cells;       /* cells (nodes holding >= 2 particles)           */
+    int64_t n_nodes;       /* cells + particle leaves                        */
+    int64_t n_groups;      /* groups of the last walk                        */
+    int64_t list_entries;  /* sum of the groups' list lengths                */
+    int64_t max_list;      /* longest list                                   */
+    int64_t list_capacity; /* entries per group slot                         */
+    int64_t n_pp;          /* particle-particle interactions (self excluded) */
+    int64_t n_pc;          /* particle-cell interactions                     */
+    int32_t max_level;     /* deepest cell level                             */
+    int32_t reserved;
+    int64_t n_pp_total;    /* n_pp summed over every walk of this context    */
+    int64_t n_pc_total;    /* n_pc summed over every walk of this context    */
+} nb_stats;
+
+/* phases timed by nb_set_timing */
+#define NB_PHASE_BUILD 0     /* nb_build_tree                               */
+#define NB_PHASE_WALK 1      /* nb_walk_groups (groups + walk)              */
+#define NB_PHASE_FORCE 2     /* nb_forces                                   */
+#define NB_PHASE_INTEGRATE 3 /* leapfrog kicks and drift                    */
+#define NB_NPHASE 4
+
+/* Fill cfg with defaults: max_n as given, stream NULL, sync_checks 1,
+ * eps 0.01, theta 0.6, n_crit 64, precision NB_FP32. */
+void nb_config_default(nb_config *cfg, int64_t max_n);
+
+/* Allocate a context and all its device storage for cfg->max_n particles
+ * (worst case: 11 cells per particle).  *ctx is NULL on failure. */
+int nb_create(nb_ctx **ctx, const nb_config *cfg);
+int nb_destroy(nb_ctx *ctx);
+/* Switch the synchronising checks of cfg.sync_checks on (1) or off (0). */
+int nb_set_sync_checks(nb_ctx *ctx, int on);
+
+/* Build the oct-tree over n particles (Sec. "Oct-tree Method": a root cube
+ * enclosing every particle, split into eight sub-cells until a cell holds
+ * one particle; Sec. "Our GPU implementation": total mass, centre of mass,
+ * cell size and next/more pointers; Sec. "Test and Optimization": Morton
+ * order).  Steps: bounding box -> root cube (side = max extent * (1+2^-20))
+ * -> 21-level Morton keys (FP64 quantisation) -> stable radix sort ->
+ * cells (one per key prefix shared by >= 2 particles; coincident particles
+ * below level 21 stay in one cell) -> FP64 moments folded bottom-up in
+ * octant order -> next/more in depth-first preorder.
+ * pos_dev: n x 3 FP64; mass_dev: n FP32; 0 <= n <= max_n.
+ * Errors: INVALID_ARG, NONFINITE (a coordinate is NaN/inf), CUDA. */
+int nb_build_tree(nb_ctx *ctx, const double *pos_dev, const float *mass_dev,
+                  int64_t n);
+
+/* Form groups (each node with count <= n_crit whose parent holds more) and
+ * walk the tree once per group (Fig. "treewalk_iterative" driven by the
+ * next/more pointers), writing each group's interaction list of particles
+ * and accepted cells to device memory in depth-first order.  A cell is
+ * accepted when the squared FP32 distance from its centre of mass to the
+ * group's bounding box exceeds (l/theta + s)^2 (Eq. mac; l = cell side,
+ * s = |centre of mass - geometric centre|); a cell that contains the group
+ * is always opened.  theta = 0 accepts no cell (direct summation).
+ * theta_per_group_dev (nullable): one theta per group, in group order, for
+ * the groups of a previous call with the same n_crit on the same tree.
+ * Errors: STATE (no tree), INVALID_ARG, CAPACITY (sync_checks == 0 and a
+ * list outgrew cfg.list_capacity), WALK_LIMIT, CUDA, NOMEM. */
+int nb_walk_groups(nb_ctx *ctx, float theta, int n_crit,
+                   const float *theta_per_group_dev);
+
+/* Sum Eq. (gravity) over every group's list for every particle of the group:
+ * a_i = sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2},
+ * phi_i = -sum_{j != i} m_j / (|x_j - x_i|^2 + eps^2)^{1/2}, cells entering as
+ * point masses at their centre of mass.  Coordinates are FP32 relative to
+ * the group's box centre; the self term is excluded by index and a pair
+ * with r^2 + eps^2 == 0 contributes nothing.
+ * acc_dev: n x 3 FP32 (required); pot_dev: n FP32 (nullable).
+ * precision: NB_FP32, NB_FP32_COMP or NB_FP64ACC.
+ * Errors: STATE (no lists), INVALID_ARG, CUDA. */
+int nb_forces(nb_ctx *ctx, float eps, float *acc_dev, float *pot_dev,
+              int precision);
+
+/* One kick-drift-kick leapfrog step of size dt in FP64 ("integrate orbits
+ * ... and repeat", Sec. Introduction): v += a dt/2; x += v dt; rebuild the
+ * tree, walk and force with cfg.eps, cfg.theta, cfg.n_crit, cfg.precision;
+ * v += a dt/2.  The context keeps a(x) between steps; the first step (or
+ * the first after nb_leapfrog_reset or a change of n) computes it first.
+ * pos_dev, vel_dev: n x 3 FP64, updated in place. */
+int nb_leapfrog_step(nb_ctx *ctx, double *pos_dev, double *vel_dev,
+                     const float *mass_dev, int64_t n, double dt);
+int nb_leapfrog_reset(nb_ctx *ctx);
+/* The accelerations (n x 3 FP32, caller order) kept by the last step. */
+int nb_leapfrog_acc(nb_ctx *ctx, float *acc_dev);
+
+/* FP64 direct sum of Eq. (gravity) for the targets listed in targets_dev
+ * (nt indices into 0..n-1; NULL = all n), used as the accuracy judge.
+ * acc_dev: nt x 3 FP64, pot_dev: nt FP64.  Work is queued on `stream`. */
+int nb_direct_sum(const double *pos_dev, const float *mass_dev, int64_t n,
+                  double eps, const int64_t *targets_dev, int64_t nt,
+                  double *acc_dev, double *pot_dev, void *stream);
+
+/* Per-phase device timing: with timing on, every phase is bracketed by CUDA
+ * events recorded on cfg.stream.  nb_get_timing synchronises and returns,
+ * per phase, the summed milliseconds and the number of calls since the last
+ * nb_get_timing, and (launches) the number of kernels libnb launched in that
+ * time; then it resets all three.  Any output pointer may be NULL. */
+int nb_set_timing(nb_ctx *ctx, int on);
+int nb_get_timing(nb_ctx *ctx, double *ms_host, int64_t *calls_host,
+                  int64_t *launches_host);
+
+/* Synchronise the stream and return (and clear) any latched device error. */
+int nb_sync_status(nb_ctx *ctx);
+/* Synchronise and fill *st. */
+int nb_get_stats(nb_ctx *ctx, nb_stats *st);
+
+/* Debug export (synchronising copies to host memory; any pointer may be
+ * NULL).  Node arrays have n_nodes entries in depth-first preorder, vectors
+ * x3; next is -1 past the last node; parent of the root is -1; level and
+ * nchild are -1 / 0 for particle leaves.  perm maps sorted slot -> caller
+ * index; keys are the sorted 63-bit Morton keys.  root: centre[3], L,
+ * corner[3]. */
+int nb_copy_tree(nb_ctx *ctx, double *root_host, uint64_t *keys_host,
+                 int32_t *perm_host, int32_t *level_host, int32_t *first_host,
+                 int32_t *count_host, int32_t *next_host, int32_t *parent_host,
+                 int32_t *nchild_host, double *mass_host, double *com_host,
+                 float *l_host, float *s_host);
+/* Groups of the last walk: node id, first sorted slot, size, box (G x 9:
+ * lo[3], hi[3], centre[3]) and the FP32 1/theta used. */
+int nb_copy_groups(nb_ctx *ctx, int32_t *gnode_host, int32_t *gfirst_host,
+                   int32_t *gcount_host, float *box_host, float *invtheta_host);
+/* Lists of the last walk, packed: offsets (G+1), node ids, the position of
+ * the group's own first particle in its list, and the FP32 source records
+ * the force kernel reads (x, y, z relative to the group centre, mass). */
+int nb_copy_lists(nb_ctx *ctx, int64_t *offsets_host, int32_t *entries_host,
+                  int32_t *self_off_host, float *xm_host);
+
+const char *nb_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NB_H */

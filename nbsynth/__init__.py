@@ -309,6 +309,8 @@ WORKLOADS = {
                     theta=0.75, n_crit=256, dt=1.0 / 1024),
     "halomix2.87m": dict(gen=lambda: halo_mix(2_870_000, BASE_SEED + 4), eps=5e-4,
                          theta=0.6, n_crit=256, dt=1.0 / 1024),
+    "halomix0.5m": dict(gen=lambda: halo_mix(500_000, BASE_SEED + 6, n_halos=350),
+                        eps=5e-4, theta=0.6, n_crit=256, dt=1.0 / 1024),
     "halomix4.19m": dict(gen=lambda: halo_mix(4_194_304, BASE_SEED + 5,
                                               n_halos=3000), eps=5e-4,
                          theta=0.6, n_crit=256, dt=1.0 / 1024),

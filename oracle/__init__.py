@@ -53,7 +53,7 @@ def lib():
             i64, f64, f32 = C.c_int64, C.c_double, C.c_float
             vp = C.c_void_p
             L.or_num_threads.restype = C.c_int
-            L.or_direct.argtypes = [i64, vp, vp, f64, i64, vp, vp, vp]
+            L.or_direct.argtypes = [i64, vp, vp, f64, i64, vp, vp, vp, vp]
             L.or_direct_ld.argtypes = [i64, vp, vp, f64, vp, vp]
             L.or_root_cube.argtypes = [i64, vp, vp]
             L.or_quantize.argtypes = [i64, vp, vp, vp]
@@ -77,7 +77,7 @@ def lib():
             L.or_all_lists.restype = i64
             L.or_all_lists.argtypes = [vp, i64, vp, vp, f64, vp, vp, i64]
             L.or_tree_forces.argtypes = [vp, i64, f64, vp, f64, i64, vp, vp,
-                                         vp, vp, vp]
+                                         vp, vp, vp, vp]
             L.or_leapfrog.argtypes = [i64, vp, vp, vp, f64, f64, i64, C.c_int,
                                       f64, i64, vp, C.c_int]
             _lib = L
@@ -100,9 +100,10 @@ def num_threads() -> int:
     return int(lib().or_num_threads())
 
 
-def direct(pos, mass, eps, targets=None):
+def direct(pos, mass, eps, targets=None, with_amag=False):
     """FP64 direct sum of Eq. (gravity) (physical signs, G = 1) for the
-    particles `targets` (all when None).  Returns (acc (nt,3), pot (nt,))."""
+    particles `targets` (all when None).  Returns (acc (nt,3), pot (nt,)),
+    plus sum_j |a_ij| per target when with_amag."""
     pos, mass = _pos(pos), _mass(mass)
     n = pos.shape[0]
     if targets is None:
@@ -112,10 +113,11 @@ def direct(pos, mass, eps, targets=None):
         nt = tg.shape[0]
     acc = np.zeros((nt, 3))
     pot = np.zeros(nt)
+    am = np.zeros(nt) if with_amag else None
     rc = lib().or_direct(n, _ptr(pos), _ptr(mass), float(eps), nt, _ptr(tg),
-                         _ptr(acc), _ptr(pot))
+                         _ptr(acc), _ptr(pot), _ptr(am))
     assert rc == 0
-    return acc, pot
+    return (acc, pot, am) if with_amag else (acc, pot)
 
 
 def direct_ld(pos, mass, eps):
@@ -233,20 +235,23 @@ class Tree:
                            _ptr(off), _ptr(ent), tot)
         return gnode, box, off, ent[:tot]
 
-    def forces(self, n_crit, theta, eps, gsel=None, theta_g=None):
-        """FP64 forces over the group lists.  Returns (acc, pot, npp, npc);
-        rows of particles outside the selected groups stay NaN."""
+    def forces(self, n_crit, theta, eps, gsel=None, theta_g=None, with_amag=False):
+        """FP64 forces over the group lists.  Returns (acc, pot, npp, npc),
+        and sum_j |a_ij| per particle last when with_amag; rows of particles
+        outside the selected groups stay NaN."""
         acc = np.full((self.n, 3), np.nan)
         pot = np.full(self.n, np.nan)
+        am = np.full(self.n, np.nan) if with_amag else None
         npp, npc = C.c_int64(0), C.c_int64(0)
         gs = None if gsel is None else np.ascontiguousarray(gsel, np.int64)
         tg = None if theta_g is None else np.ascontiguousarray(theta_g, np.float32)
         rc = lib().or_tree_forces(self._h, int(n_crit), float(theta), _ptr(tg),
                                   float(eps), 0 if gs is None else gs.shape[0],
-                                  _ptr(gs), _ptr(acc), _ptr(pot),
+                                  _ptr(gs), _ptr(acc), _ptr(pot), _ptr(am),
                                   C.byref(npp), C.byref(npc))
         assert rc == 0
-        return acc, pot, int(npp.value), int(npc.value)
+        out = (acc, pot, int(npp.value), int(npc.value))
+        return out + (am,) if with_amag else out
 
 
 def leapfrog(pos, vel, mass, eps, dt, nsteps, use_tree=False, theta=0.75,

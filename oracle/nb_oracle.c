@@ -75,7 +75,8 @@ int or_num_threads(void)
  * signs (acceleration towards j, negative potential) and G = 1.           */
 
 int or_direct(int64_t n, const double *pos, const float *mass, double eps,
-              int64_t nt, const int64_t *targets, double *acc, double *pot)
+              int64_t nt, const int64_t *targets, double *acc, double *pot,
+              double *amag)
 {
     const double e2 = eps * eps;
     if (n < 0 || nt < 0)
@@ -83,7 +84,7 @@ int or_direct(int64_t n, const double *pos, const float *mass, double eps,
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t t = 0; t < nt; t++) {
         const int64_t i = targets ? targets[t] : t;
-        double ax = 0.0, ay = 0.0, az = 0.0, p = 0.0;
+        double ax = 0.0, ay = 0.0, az = 0.0, p = 0.0, am = 0.0;
         for (int64_t j = 0; j < n; j++) {
             if (j == i)
                 continue;
@@ -100,7 +101,10 @@ int or_direct(int64_t n, const double *pos, const float *mass, double eps,
             ay += mr3 * dy;
             az += mr3 * dz;
             p -= m * rinv;
+            am += mr3 * sqrt(dx * dx + dy * dy + dz * dz);
         }
+        if (amag)
+            amag[t] = am;
         acc[3 * t + 0] = ax;
         acc[3 * t + 1] = ay;
         acc[3 * t + 2] = az;
@@ -706,11 +710,13 @@ int64_t or_all_lists(const or_tree *t, int64_t G, const int64_t *gnode,
  * For the groups listed in gsel (all when gsel == NULL) every member gets
  * acc (caller order, x3) and pot.  theta_g (nullable) gives each group its
  * own opening angle.  npp / npc receive the particle-particle and
- * particle-cell interaction counts (self pairs not counted).               */
+ * particle-cell interaction counts (self pairs not counted).  amag
+ * (nullable) receives sum_j |a_ij|, the scale of the rounding error of the
+ * summed acceleration.                                                     */
 int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
                    const float *theta_g, double eps, int64_t nsel,
                    const int64_t *gsel, double *acc, double *pot,
-                   int64_t *npp, int64_t *npc)
+                   double *amag, int64_t *npp, int64_t *npc)
 {
     const int64_t G = or_groups(t, n_crit, NULL);
     int64_t *gnode = (int64_t *)malloc((size_t)(G > 0 ? G : 1) * sizeof(int64_t));
@@ -759,7 +765,7 @@ int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
                 const int64_t self = t->leaf[slot];
                 const double xi = t->pos[3 * i], yi = t->pos[3 * i + 1],
                              zi = t->pos[3 * i + 2];
-                double ax = 0.0, ay = 0.0, az = 0.0, p = 0.0;
+                double ax = 0.0, ay = 0.0, az = 0.0, p = 0.0, am = 0.0;
                 for (int64_t e = 0; e < len; e++) {
                     const int64_t v = lst[e];
                     if (v == self)
@@ -776,7 +782,10 @@ int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
                     ay += mr3 * dy;
                     az += mr3 * dz;
                     p -= t->M[v] * rinv;
+                    am += mr3 * sqrt(dx * dx + dy * dy + dz * dz);
                 }
+                if (amag)
+                    amag[i] = am;
                 acc[3 * i] = ax;
                 acc[3 * i + 1] = ay;
                 acc[3 * i + 2] = az;
@@ -807,12 +816,12 @@ static int accel(int64_t n, const double *pos, const float *mass, double eps,
                  double *pot)
 {
     if (!use_tree)
-        return or_direct(n, pos, mass, eps, n, NULL, acc, pot);
+        return or_direct(n, pos, mass, eps, n, NULL, acc, pot, NULL);
     or_tree *t = or_tree_build(n, pos, mass);
     if (!t)
         return -1;
     const int rc = or_tree_forces(t, n_crit, theta, NULL, eps, 0, NULL, acc,
-                                  pot, NULL, NULL);
+                                  pot, NULL, NULL, NULL);
     or_tree_free(t);
     return rc;
 }

@@ -1,0 +1,288 @@
+"""GB300-native oct-tree group walk and softened gravity (arXiv:0909.0541).
+
+A thin ctypes binding over ``libnb.so`` (CUDA for sm_103a, C ABI in
+``include/nb.h``).  Every step of the path -- tree build, group walk, force
+sum, leapfrog -- runs in the library's kernels; this module only marshals
+torch tensors (device memory and streams) into the C calls.  There is no CPU
+fallback: importing fails if the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NB_OK = 0
+NB_ERR = {
+    -1: "INVALID_ARG", -2: "CUDA", -3: "CAPACITY", -4: "WALK_LIMIT",
+    -5: "NONFINITE", -6: "STATE", -7: "NOMEM",
+}
+NB_FP32, NB_FP32_COMP, NB_FP64ACC = 0, 1, 2
+PRECISION = {"fp32": NB_FP32, "fp32_comp": NB_FP32_COMP, "fp64acc": NB_FP64ACC}
+
+# flops per interaction by the paper's convention (Sec. "A Bare Many-body
+# Performance on RV770 GPU")
+FLOPS_PER_INTERACTION = 38
+
+EXPORTED = [
+    "nb_config_default", "nb_create", "nb_destroy", "nb_set_sync_checks",
+    "nb_build_tree", "nb_walk_groups", "nb_forces", "nb_leapfrog_step",
+    "nb_leapfrog_reset", "nb_leapfrog_acc", "nb_direct_sum", "nb_sync_status",
+    "nb_get_stats", "nb_copy_tree", "nb_copy_groups", "nb_copy_lists",
+    "nb_error_string", "nb_set_timing", "nb_get_timing",
+]
+PHASES = ("build", "walk", "force", "integrate")
+
+
+class nb_config(C.Structure):
+    _fields_ = [("max_n", C.c_int64), ("list_capacity", C.c_int64),
+                ("stream", C.c_void_p), ("sync_checks", C.c_int),
+                ("device", C.c_int), ("eps", C.c_float), ("theta", C.c_float),
+                ("n_crit", C.c_int), ("precision", C.c_int)]
+
+
+class nb_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_cells", C.c_int64), ("n_nodes", C.c_int64),
+                ("n_groups", C.c_int64), ("list_entries", C.c_int64),
+                ("max_list", C.c_int64), ("list_capacity", C.c_int64),
+                ("n_pp", C.c_int64), ("n_pc", C.c_int64),
+                ("max_level", C.c_int32), ("reserved", C.c_int32),
+                ("n_pp_total", C.c_int64), ("n_pc_total", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class NBError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {NB_ERR.get(code, code)} "
+                         f"({_lib.nb_error_string(code).decode()})")
+
+
+def _load():
+    path = _build.build()
+    L = C.CDLL(path)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    L.nb_config_default.argtypes = [C.POINTER(nb_config), i64]
+    L.nb_config_default.restype = None
+    L.nb_create.argtypes = [C.POINTER(vp), C.POINTER(nb_config)]
+    L.nb_destroy.argtypes = [vp]
+    L.nb_set_sync_checks.argtypes = [vp, i32]
+    L.nb_build_tree.argtypes = [vp, vp, vp, i64]
+    L.nb_walk_groups.argtypes = [vp, C.c_float, i32, vp]
+    L.nb_forces.argtypes = [vp, C.c_float, vp, vp, i32]
+    L.nb_leapfrog_step.argtypes = [vp, vp, vp, vp, i64, C.c_double]
+    L.nb_leapfrog_reset.argtypes = [vp]
+    L.nb_leapfrog_acc.argtypes = [vp, vp]
+    L.nb_direct_sum.argtypes = [vp, vp, i64, C.c_double, vp, i64, vp, vp, vp]
+    L.nb_sync_status.argtypes = [vp]
+    L.nb_get_stats.argtypes = [vp, C.POINTER(nb_stats)]
+    L.nb_copy_tree.argtypes = [vp] * 14
+    L.nb_copy_groups.argtypes = [vp] * 6
+    L.nb_copy_lists.argtypes = [vp] * 5
+    L.nb_set_timing.argtypes = [vp, i32]
+    L.nb_get_timing.argtypes = [vp, vp, vp, vp]
+    L.nb_error_string.argtypes = [i32]
+    L.nb_error_string.restype = C.c_char_p
+    return L
+
+
+_lib = _load()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(rc, where):
+    if rc != NB_OK:
+        raise NBError(rc, where)
+
+
+def _dptr(t, dtype, shape_last=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor of the given dtype."""
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError(f"{name} must have shape (n, {shape_last})")
+    return t.data_ptr()
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class NBody:
+    """One libnb context: storage for up to max_n particles on one GPU."""
+
+    def __init__(self, max_n, *, eps=0.01, theta=0.6, n_crit=64,
+                 precision="fp32", list_capacity=0, sync_checks=True,
+                 stream=None, device=None):
+        import torch
+        dev = torch.cuda.current_device() if device is None else int(device)
+        cfg = nb_config()
+        _lib.nb_config_default(C.byref(cfg), int(max_n))
+        cfg.list_capacity = int(list_capacity)
+        cfg.stream = _stream_handle(stream)
+        cfg.sync_checks = 1 if sync_checks else 0
+        cfg.device = dev
+        cfg.eps = float(eps)
+        cfg.theta = float(theta)
+        cfg.n_crit = int(n_crit)
+        cfg.precision = PRECISION.get(precision, precision)
+        self.cfg = cfg
+        self.max_n = int(max_n)
+        h = C.c_void_p()
+        _check(_lib.nb_create(C.byref(h), C.byref(cfg)), "nb_create")
+        self._h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- the path ---------------------------------------------------------
+    def set_sync_checks(self, on: bool):
+        _check(_lib.nb_set_sync_checks(self._h, 1 if on else 0), "nb_set_sync_checks")
+
+    def build_tree(self, pos, mass):
+        import torch
+        n = int(pos.shape[0])
+        _check(_lib.nb_build_tree(self._h, _dptr(pos, torch.float64, 3, "pos"),
+                                  _dptr(mass, torch.float32, None, "mass"), n),
+               "nb_build_tree")
+        self.n = n
+
+    def walk_groups(self, theta, n_crit, theta_per_group=None):
+        import torch
+        _check(_lib.nb_walk_groups(self._h, float(theta), int(n_crit),
+                                   _dptr(theta_per_group, torch.float32, None,
+                                         "theta_per_group")),
+               "nb_walk_groups")
+
+    def forces(self, eps, acc, pot=None, precision="fp32"):
+        import torch
+        _check(_lib.nb_forces(self._h, float(eps), _dptr(acc, torch.float32, 3, "acc"),
+                              _dptr(pot, torch.float32, None, "pot"),
+                              PRECISION.get(precision, precision)), "nb_forces")
+
+    def leapfrog_step(self, pos, vel, mass, dt):
+        import torch
+        _check(_lib.nb_leapfrog_step(self._h, _dptr(pos, torch.float64, 3, "pos"),
+                                     _dptr(vel, torch.float64, 3, "vel"),
+                                     _dptr(mass, torch.float32, None, "mass"),
+                                     int(pos.shape[0]), float(dt)), "nb_leapfrog_step")
+        self.n = int(pos.shape[0])
+
+    def leapfrog_reset(self):
+        _check(_lib.nb_leapfrog_reset(self._h), "nb_leapfrog_reset")
+
+    def leapfrog_acc(self, acc):
+        import torch
+        _check(_lib.nb_leapfrog_acc(self._h, _dptr(acc, torch.float32, 3, "acc")),
+               "nb_leapfrog_acc")
+
+    def set_timing(self, on: bool):
+        _check(_lib.nb_set_timing(self._h, 1 if on else 0), "nb_set_timing")
+
+    def get_timing(self) -> dict:
+        """Per-phase device milliseconds and call counts since the last call,
+        and the number of libnb kernel launches in that time."""
+        ms = np.zeros(4)
+        calls = np.zeros(4, np.int64)
+        launches = np.zeros(1, np.int64)
+        _check(_lib.nb_get_timing(self._h, _hptr(ms), _hptr(calls), _hptr(launches)),
+               "nb_get_timing")
+        out = {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(PHASES)}
+        out["launches"] = int(launches[0])
+        return out
+
+    def sync_status(self):
+        _check(_lib.nb_sync_status(self._h), "nb_sync_status")
+
+    def stats(self) -> dict:
+        st = nb_stats()
+        _check(_lib.nb_get_stats(self._h, C.byref(st)), "nb_get_stats")
+        return st.as_dict()
+
+    # -- debug export -------------------------------------------------------
+    def copy_tree(self) -> dict:
+        st = self.stats()
+        n, nn = st["n"], st["n_nodes"]
+        d = dict(root=np.zeros(7), keys=np.zeros(n, np.uint64), perm=np.zeros(n, np.int32),
+                 level=np.zeros(nn, np.int32), first=np.zeros(nn, np.int32),
+                 count=np.zeros(nn, np.int32), next=np.zeros(nn, np.int32),
+                 parent=np.zeros(nn, np.int32), nchild=np.zeros(nn, np.int32),
+                 M=np.zeros(nn), com=np.zeros((nn, 3)), l=np.zeros(nn, np.float32),
+                 s=np.zeros(nn, np.float32))
+        keys = ["root", "keys", "perm", "level", "first", "count", "next", "parent",
+                "nchild", "M", "com", "l", "s"]
+        _check(_lib.nb_copy_tree(self._h, *[_hptr(d[k]) for k in keys]), "nb_copy_tree")
+        d["is_cell"] = (d["level"] >= 0).astype(np.int8)
+        return d
+
+    def copy_groups(self) -> dict:
+        G = self.stats()["n_groups"]
+        d = dict(gnode=np.zeros(G, np.int32), gfirst=np.zeros(G, np.int32),
+                 gcount=np.zeros(G, np.int32), box=np.zeros((G, 9), np.float32),
+                 invtheta=np.zeros(G, np.float32))
+        _check(_lib.nb_copy_groups(self._h, *[_hptr(d[k]) for k in
+                                              ["gnode", "gfirst", "gcount", "box", "invtheta"]]),
+               "nb_copy_groups")
+        return d
+
+    def copy_lists(self, with_xm=False) -> dict:
+        st = self.stats()
+        G, tot = st["n_groups"], st["list_entries"]
+        d = dict(offsets=np.zeros(G + 1, np.int64), entries=np.zeros(tot, np.int32),
+                 self_off=np.zeros(G, np.int32),
+                 xm=np.zeros((tot, 4), np.float32) if with_xm else None)
+        _check(_lib.nb_copy_lists(self._h, _hptr(d["offsets"]), _hptr(d["entries"]),
+                                  _hptr(d["self_off"]), _hptr(d["xm"])), "nb_copy_lists")
+        return d
+
+
+def direct_sum(pos, mass, eps, targets=None, stream=None):
+    """FP64 GPU direct sum of Eq. (gravity) for `targets` (int64 indices, all
+    when None).  Returns (acc (nt,3) float64, pot (nt,) float64) tensors."""
+    import torch
+    n = int(pos.shape[0])
+    nt = n if targets is None else int(targets.shape[0])
+    acc = torch.empty((nt, 3), dtype=torch.float64, device=pos.device)
+    pot = torch.empty(nt, dtype=torch.float64, device=pos.device)
+    _check(_lib.nb_direct_sum(_dptr(pos, torch.float64, 3, "pos"),
+                              _dptr(mass, torch.float32, None, "mass"), n, float(eps),
+                              _dptr(targets, torch.int64, None, "targets"), nt,
+                              acc.data_ptr(), pot.data_ptr(), _stream_handle(stream)),
+           "nb_direct_sum")
+    return acc, pot

@@ -1,0 +1,576 @@
+// nb_api.cu -- the C ABI declared in include/nb.h: context and storage,
+// argument checks, the order of kernel launches, status and debug export.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "nb_internal.cuh"
+
+#define CK(call)                                                            \
+    do {                                                                    \
+        if ((call) != cudaSuccess) {                                        \
+            cudaGetLastError();                                             \
+            return NB_ERR_CUDA;                                             \
+        }                                                                   \
+    } while (0)
+
+extern "C" {
+
+void nb_config_default(nb_config *cfg, int64_t max_n)
+{
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->max_n = max_n;
+    cfg->sync_checks = 1;
+    cfg->eps = 0.01f;
+    cfg->theta = 0.6f;
+    cfg->n_crit = 64;
+    cfg->precision = NB_FP32;
+}
+
+const char *nb_error_string(int code)
+{
+    switch (code) {
+    case NB_OK: return "ok";
+    case NB_ERR_INVALID_ARG: return "invalid argument";
+    case NB_ERR_CUDA: return "CUDA runtime error";
+    case NB_ERR_CAPACITY: return "interaction list capacity exceeded";
+    case NB_ERR_WALK_LIMIT: return "tree walk did not advance";
+    case NB_ERR_NONFINITE: return "non-finite position";
+    case NB_ERR_STATE: return "call order: build the tree, then walk, then force";
+    case NB_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"
+
+static void free_all(nb_ctx *c)
+{
+    void *ptrs[] = {c->keys, c->keys_alt, c->idx, c->idx_alt, c->sort_hist, c->scan_bsum,
+                    c->root, c->bbox_part, c->p_hi, c->p_lo, c->p_x64, c->perm, c->clev,
+                    c->ccount, c->cstart, c->node_a, c->node_b, c->node_c, c->n_level,
+                    c->n_first, c->n_count, c->n_parent, c->n_nchild, c->n_arrive,
+                    c->n_mass, c->n_mx, c->n_com, c->gflag, c->gnode, c->gfirst, c->gcount,
+                    c->glen, c->gself, c->gcells, c->gbox, c->items, c->item_cnt,
+                    c->list_id, c->list_xm, c->acc_cache, c->pot_cache, c->err, c->cnt};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->cnt_host) cudaFreeHost(c->cnt_host);
+    if (c->ev) {
+        for (int i = 0; i < 2 * NB_EV_POOL; i++) cudaEventDestroy(c->ev[i]);
+        free(c->ev);
+        free(c->ev_phase);
+    }
+}
+
+template <typename T>
+static bool dalloc(T **p, int64_t count)
+{
+    if (count < 1) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * (size_t)count) == cudaSuccess;
+}
+
+static int err_code(unsigned bits)
+{
+    if (bits & NB_EF_NONFINITE) return NB_ERR_NONFINITE;
+    if (bits & NB_EF_WALK) return NB_ERR_WALK_LIMIT;
+    if (bits & NB_EF_CAPACITY) return NB_ERR_CAPACITY;
+    return NB_OK;
+}
+
+// synchronise, read and clear the device error word
+static int sync_read(nb_ctx *c)
+{
+    unsigned bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (bits) CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    return err_code(bits);
+}
+
+static int read_counters(nb_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->cnt_host, c->cnt, sizeof(long long) * CNT_N_,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NB_OK;
+}
+
+static int finish(nb_ctx *c)
+{
+    if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
+    if (!c->sync_checks) return NB_OK;
+    return sync_read(c);
+}
+
+// phase timing: a pair of events on the context's stream around each phase
+static int phase_begin(nb_ctx *c)
+{
+    if (!c->timing || !c->ev || c->ev_used >= NB_EV_POOL) return -1;
+    const int k = c->ev_used++;
+    cudaEventRecord(c->ev[2 * k], c->stream);
+    return k;
+}
+
+static void phase_end(nb_ctx *c, int k, int phase)
+{
+    if (k < 0) return;
+    cudaEventRecord(c->ev[2 * k + 1], c->stream);
+    c->ev_phase[k] = phase;
+}
+
+static int ensure_lists(nb_ctx *c, int64_t groups, int64_t cap)
+{
+    const int64_t need = groups * cap;
+    if (need <= c->list_alloc && cap == c->list_cap) return NB_OK;
+    if (need > c->list_alloc) {
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->list_id) cudaFree(c->list_id);
+        if (c->list_xm) cudaFree(c->list_xm);
+        c->list_id = nullptr;
+        c->list_xm = nullptr;
+        c->list_alloc = 0;
+        const int64_t want = need + need / 8;
+        if (!dalloc(&c->list_id, want) || !dalloc(&c->list_xm, want)) {
+            cudaGetLastError();
+            if (c->list_id) cudaFree(c->list_id);
+            c->list_id = nullptr;
+            return NB_ERR_NOMEM;
+        }
+        c->list_alloc = want;
+    }
+    c->list_cap = cap;
+    return NB_OK;
+}
+
+extern "C" {
+
+int nb_create(nb_ctx **out, const nb_config *cfg)
+{
+    if (!out || !cfg) return NB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->max_n < 1 || cfg->max_n > (int64_t)150000000 || cfg->n_crit < 1 ||
+        !(cfg->theta >= 0.f) || !(cfg->eps >= 0.f) || cfg->precision < 0 ||
+        cfg->precision > 2 || cfg->list_capacity < 0)
+        return NB_ERR_INVALID_ARG;
+    nb_ctx *c = new (std::nothrow) nb_ctx();
+    if (!c) return NB_ERR_NOMEM;
+    memset(c, 0, sizeof(*c));
+    c->cfg = *cfg;
+    c->device = cfg->device;
+    c->stream = (cudaStream_t)cfg->stream;
+    c->sync_checks = cfg->sync_checks;
+    if (cudaSetDevice(c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return NB_ERR_CUDA;
+    }
+    const int64_t N = cfg->max_n;
+    const int64_t NN = 12 * N + 2;
+    c->max_n = N;
+    c->max_nodes = NN;
+    const int64_t rs_tiles = (N + 4095) / 4096;
+    c->sort_hist_len = 256 * rs_tiles + 1;
+    int64_t scan_n = NN + 1 > c->sort_hist_len ? NN + 1 : c->sort_hist_len;
+    c->scan_bsum_len = (scan_n + 2047) / 2048 + 2;
+    c->bbox_blocks = c->num_sms * 4;
+    c->max_items = N + N / 64 + 2;
+    bool ok = dalloc(&c->keys, N) && dalloc(&c->keys_alt, N) && dalloc(&c->idx, N) &&
+              dalloc(&c->idx_alt, N) && dalloc(&c->sort_hist, c->sort_hist_len) &&
+              dalloc(&c->scan_bsum, c->scan_bsum_len) && dalloc(&c->root, 8) &&
+              dalloc(&c->bbox_part, 6 * (int64_t)c->bbox_blocks) && dalloc(&c->p_hi, N) &&
+              dalloc(&c->p_lo, N) && dalloc(&c->p_x64, 3 * N) && dalloc(&c->perm, N) &&
+              dalloc(&c->clev, N) && dalloc(&c->ccount, N + 1) && dalloc(&c->cstart, N + 1) &&
+              dalloc(&c->node_a, NN) && dalloc(&c->node_b, NN) && dalloc(&c->node_c, NN) &&
+              dalloc(&c->n_level, NN) && dalloc(&c->n_first, NN) && dalloc(&c->n_count, NN) &&
+              dalloc(&c->n_parent, NN) && dalloc(&c->n_nchild, NN) &&
+              dalloc(&c->n_arrive, NN) && dalloc(&c->n_mass, NN) && dalloc(&c->n_mx, 3 * NN) &&
+              dalloc(&c->n_com, 3 * NN) && dalloc(&c->gflag, NN + 1) && dalloc(&c->gnode, N) &&
+              dalloc(&c->gfirst, N) && dalloc(&c->gcount, N) && dalloc(&c->glen, N) &&
+              dalloc(&c->gself, N) && dalloc(&c->gcells, N) && dalloc(&c->gbox, 3 * N) &&
+              dalloc(&c->items, 2 * c->max_items) && dalloc(&c->item_cnt, N + 1) &&
+              dalloc(&c->acc_cache, 3 * N) && dalloc(&c->pot_cache, N) &&
+              dalloc(&c->err, 1) && dalloc(&c->cnt, CNT_N_) &&
+              cudaMallocHost((void **)&c->cnt_host, sizeof(long long) * CNT_N_) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return NB_ERR_NOMEM;
+    }
+    if (cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_N_, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return NB_ERR_CUDA;
+    }
+    c->list_cap = cfg->list_capacity;
+    *out = c;
+    return NB_OK;
+}
+
+int nb_destroy(nb_ctx *c)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return NB_OK;
+}
+
+int nb_set_sync_checks(nb_ctx *c, int on)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    c->sync_checks = on ? 1 : 0;
+    return NB_OK;
+}
+
+int nb_build_tree(nb_ctx *c, const double *pos, const float *mass, int64_t n)
+{
+    if (!c || n < 0 || n > c->max_n || (n > 0 && (!pos || !mass))) return NB_ERR_INVALID_ARG;
+    c->has_tree = 0;
+    c->has_lists = 0;
+    c->n = n;
+    if (n == 0) {
+        CK(cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_PP_CUM, c->stream));
+        c->has_tree = 1;
+        return finish(c);
+    }
+    const int tk = phase_begin(c);
+    nb_launch_build(c, pos, mass, n);
+    phase_end(c, tk, NB_PHASE_BUILD);
+    c->has_tree = 1;
+    return finish(c);
+}
+
+int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!c->has_tree) return NB_ERR_STATE;
+    if (!(theta >= 0.f) || n_crit < 1) return NB_ERR_INVALID_ARG;
+    c->has_lists = 0;
+    c->n_crit_cur = n_crit;
+    if (c->n == 0) {
+        c->groups_host = 0;
+        c->has_lists = 1;
+        return NB_OK;
+    }
+    const int tk = phase_begin(c);
+    nb_launch_groups(c, theta, n_crit, theta_g);
+    if (c->sync_checks) {
+        int rc = read_counters(c);
+        if (rc) return rc;
+        const int64_t G = c->cnt_host[CNT_GROUPS];
+        c->groups_host = G;
+        int64_t cap = c->list_cap > 0 ? c->list_cap : 4096;
+        for (int attempt = 0; attempt < 2; attempt++) {
+            rc = ensure_lists(c, G, cap);
+            if (rc) return rc;
+            nb_launch_walk(c);
+            rc = finish(c);
+            if (rc != NB_ERR_CAPACITY || c->cfg.list_capacity > 0) break;
+            rc = read_counters(c);
+            if (rc) return rc;
+            const int64_t need = c->cnt_host[CNT_LIST_MAX];
+            cap = ((need + need / 4 + 255) / 256) * 256;
+            rc = NB_ERR_CAPACITY;
+        }
+        phase_end(c, tk, NB_PHASE_WALK);
+        if (rc) return rc;
+    } else {
+        if (c->list_cap < 1 || !c->list_id) return NB_ERR_CAPACITY;
+        nb_launch_walk(c);
+        phase_end(c, tk, NB_PHASE_WALK);
+        int rc = finish(c);
+        if (rc) return rc;
+    }
+    c->has_lists = 1;
+    return NB_OK;
+}
+
+int nb_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!c->has_lists) return NB_ERR_STATE;
+    if (!(eps >= 0.f) || precision < 0 || precision > 2 || (c->n > 0 && !acc))
+        return NB_ERR_INVALID_ARG;
+    if (c->n == 0) return NB_OK;
+    const int tk = phase_begin(c);
+    nb_launch_forces(c, eps, acc, pot, precision);
+    phase_end(c, tk, NB_PHASE_FORCE);
+    return finish(c);
+}
+
+int nb_leapfrog_reset(nb_ctx *c)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    c->acc_valid = 0;
+    return NB_OK;
+}
+
+int nb_leapfrog_acc(nb_ctx *c, float *acc)
+{
+    if (!c || !acc) return NB_ERR_INVALID_ARG;
+    if (!c->acc_valid) return NB_ERR_STATE;
+    CK(cudaMemcpyAsync(acc, c->acc_cache, sizeof(float) * 3 * (size_t)c->n,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    return finish(c);
+}
+
+static int force_pass(nb_ctx *c, const double *pos, const float *mass, int64_t n)
+{
+    int rc = nb_build_tree(c, pos, mass, n);
+    if (rc) return rc;
+    rc = nb_walk_groups(c, c->cfg.theta, c->cfg.n_crit, nullptr);
+    if (rc) return rc;
+    return nb_forces(c, c->cfg.eps, c->acc_cache, c->pot_cache, c->cfg.precision);
+}
+
+int nb_leapfrog_step(nb_ctx *c, double *pos, double *vel, const float *mass, int64_t n,
+                     double dt)
+{
+    if (!c || n < 0 || n > c->max_n || (n > 0 && (!pos || !vel || !mass)) || !isfinite(dt))
+        return NB_ERR_INVALID_ARG;
+    if (n == 0) return NB_OK;
+    int rc;
+    if (!c->acc_valid || c->n != n) {
+        rc = force_pass(c, pos, mass, n);
+        if (rc) return rc;
+        c->acc_valid = 1;
+    }
+    const double h = 0.5 * dt;
+    int tk = phase_begin(c);
+    nb_launch_kick(c, vel, c->acc_cache, n, h);
+    nb_launch_drift(c, pos, vel, n, dt);
+    phase_end(c, tk, NB_PHASE_INTEGRATE);
+    rc = force_pass(c, pos, mass, n);
+    if (rc) {
+        c->acc_valid = 0;
+        return rc;
+    }
+    tk = phase_begin(c);
+    nb_launch_kick(c, vel, c->acc_cache, n, h);
+    phase_end(c, tk, NB_PHASE_INTEGRATE);
+    return finish(c);
+}
+
+int nb_direct_sum(const double *pos, const float *mass, int64_t n, double eps,
+                  const int64_t *targets, int64_t nt, double *acc, double *pot, void *stream)
+{
+    if (n < 0 || nt < 0 || !(eps >= 0.0) || (n > 0 && (!pos || !mass)) ||
+        (nt > 0 && (!acc || !pot)))
+        return NB_ERR_INVALID_ARG;
+    if (!targets && nt > n) return NB_ERR_INVALID_ARG;
+    if (nb_launch_direct(pos, mass, n, eps, targets, nt, acc, pot, (cudaStream_t)stream))
+        return NB_ERR_CUDA;
+    return NB_OK;
+}
+
+int nb_set_timing(nb_ctx *c, int on)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (on && !c->ev) {
+        c->ev = (cudaEvent_t *)calloc(2 * NB_EV_POOL, sizeof(cudaEvent_t));
+        c->ev_phase = (int *)calloc(NB_EV_POOL, sizeof(int));
+        if (!c->ev || !c->ev_phase) return NB_ERR_NOMEM;
+        for (int i = 0; i < 2 * NB_EV_POOL; i++) CK(cudaEventCreate(&c->ev[i]));
+    }
+    c->timing = on ? 1 : 0;
+    return NB_OK;
+}
+
+int nb_get_timing(nb_ctx *c, double *ms, int64_t *calls, int64_t *launches)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    double t[NB_NPHASE] = {0, 0, 0, 0};
+    int64_t k[NB_NPHASE] = {0, 0, 0, 0};
+    for (int i = 0; i < c->ev_used; i++) {
+        float e = 0.f;
+        CK(cudaEventElapsedTime(&e, c->ev[2 * i], c->ev[2 * i + 1]));
+        t[c->ev_phase[i]] += e;
+        k[c->ev_phase[i]]++;
+    }
+    c->ev_used = 0;
+    for (int p = 0; p < NB_NPHASE; p++) {
+        if (ms) ms[p] = t[p];
+        if (calls) calls[p] = k[p];
+    }
+    if (launches) *launches = c->launches;
+    c->launches = 0;
+    return NB_OK;
+}
+
+int nb_sync_status(nb_ctx *c)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
+    return sync_read(c);
+}
+
+int nb_get_stats(nb_ctx *c, nb_stats *st)
+{
+    if (!c || !st) return NB_ERR_INVALID_ARG;
+    int rc = read_counters(c);
+    if (rc) return rc;
+    const long long *h = c->cnt_host;
+    memset(st, 0, sizeof(*st));
+    st->n = c->n;
+    st->n_cells = c->n > 0 ? h[CNT_CELLS] : 0;
+    st->n_nodes = c->n > 0 ? h[CNT_NODES] : 0;
+    st->n_groups = c->has_lists && c->n > 0 ? h[CNT_GROUPS] : 0;
+    st->list_entries = h[CNT_LIST_TOT];
+    st->max_list = h[CNT_LIST_MAX];
+    st->list_capacity = c->list_cap;
+    st->n_pp = h[CNT_PP];
+    st->n_pc = h[CNT_PC];
+    st->max_level = (int32_t)h[CNT_MAXLEVEL];
+    st->n_pp_total = h[CNT_PP_CUM];
+    st->n_pc_total = h[CNT_PC_CUM];
+    return NB_OK;
+}
+
+#define D2H(dst, src, count)                                                              \
+    do {                                                                                  \
+        if (dst) CK(cudaMemcpyAsync(dst, src, sizeof(*(dst)) * (size_t)(count),           \
+                                    cudaMemcpyDeviceToHost, c->stream));                  \
+    } while (0)
+
+int nb_copy_tree(nb_ctx *c, double *root, uint64_t *keys, int32_t *perm, int32_t *level,
+                 int32_t *first, int32_t *count, int32_t *next, int32_t *parent,
+                 int32_t *nchild, double *mass, double *com, float *l, float *s)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!c->has_tree) return NB_ERR_STATE;
+    int rc = read_counters(c);
+    if (rc) return rc;
+    const int64_t nn = c->n > 0 ? c->cnt_host[CNT_NODES] : 0;
+    const int64_t n = c->n;
+    if (n > 0) D2H(root, c->root, 7);
+    D2H(keys, c->keys, n);
+    D2H(perm, c->perm, n);
+    D2H(level, c->n_level, nn);
+    D2H(first, c->n_first, nn);
+    D2H(count, c->n_count, nn);
+    D2H(parent, c->n_parent, nn);
+    D2H(nchild, c->n_nchild, nn);
+    D2H(mass, c->n_mass, nn);
+    D2H(com, c->n_com, 3 * nn);
+    int4 *nc = nullptr;
+    if ((next || l || s) && nn > 0) {
+        nc = (int4 *)malloc(sizeof(int4) * (size_t)nn);
+        if (!nc) return NB_ERR_NOMEM;
+        if (cudaMemcpyAsync(nc, c->node_c, sizeof(int4) * (size_t)nn, cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess) {
+            free(nc);
+            return NB_ERR_CUDA;
+        }
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        free(nc);
+        return NB_ERR_CUDA;
+    }
+    for (int64_t u = 0; nc && u < nn; u++) {
+        if (next) next[u] = nc[u].x >= nn ? -1 : nc[u].x;
+        float lf, sf;
+        memcpy(&lf, &nc[u].y, 4);
+        memcpy(&sf, &nc[u].z, 4);
+        if (l) l[u] = lf;
+        if (s) s[u] = sf;
+    }
+    free(nc);
+    return NB_OK;
+}
+
+int nb_copy_groups(nb_ctx *c, int32_t *gnode, int32_t *gfirst, int32_t *gcount, float *box,
+                   float *invtheta)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!c->has_lists) return NB_ERR_STATE;
+    int rc = read_counters(c);
+    if (rc) return rc;
+    const int64_t G = c->n > 0 ? c->cnt_host[CNT_GROUPS] : 0;
+    D2H(gnode, c->gnode, G);
+    D2H(gfirst, c->gfirst, G);
+    D2H(gcount, c->gcount, G);
+    float4 *b = nullptr;
+    if ((box || invtheta) && G > 0) {
+        b = (float4 *)malloc(sizeof(float4) * 3 * (size_t)G);
+        if (!b) return NB_ERR_NOMEM;
+        if (cudaMemcpyAsync(b, c->gbox, sizeof(float4) * 3 * (size_t)G, cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess) {
+            free(b);
+            return NB_ERR_CUDA;
+        }
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        free(b);
+        return NB_ERR_CUDA;
+    }
+    for (int64_t g = 0; b && g < G; g++) {
+        const float4 lo = b[3 * g], hi = b[3 * g + 1], ct = b[3 * g + 2];
+        if (box) {
+            float *o = box + 9 * g;
+            o[0] = lo.x; o[1] = lo.y; o[2] = lo.z;
+            o[3] = hi.x; o[4] = hi.y; o[5] = hi.z;
+            o[6] = ct.x; o[7] = ct.y; o[8] = ct.z;
+        }
+        if (invtheta) invtheta[g] = ct.w;
+    }
+    free(b);
+    return NB_OK;
+}
+
+int nb_copy_lists(nb_ctx *c, int64_t *offsets, int32_t *entries, int32_t *self_off,
+                  float *xm)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!c->has_lists) return NB_ERR_STATE;
+    int rc = read_counters(c);
+    if (rc) return rc;
+    const int64_t G = c->n > 0 ? c->cnt_host[CNT_GROUPS] : 0;
+    if (G == 0) {
+        if (offsets) offsets[0] = 0;
+        return NB_OK;
+    }
+    int32_t *len = (int32_t *)malloc(sizeof(int32_t) * (size_t)G);
+    if (!len) return NB_ERR_NOMEM;
+    if (cudaMemcpyAsync(len, c->glen, sizeof(int32_t) * (size_t)G, cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess ||
+        (self_off && cudaMemcpyAsync(self_off, c->gself, sizeof(int32_t) * (size_t)G,
+                                     cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        free(len);
+        return NB_ERR_CUDA;
+    }
+    int64_t off = 0;
+    for (int64_t g = 0; g < G; g++) {
+        if (offsets) offsets[g] = off;
+        const int64_t L = len[g] < c->list_cap ? len[g] : c->list_cap;
+        if (entries && L > 0 &&
+            cudaMemcpyAsync(entries + off, c->list_id + g * c->list_cap, sizeof(int32_t) * L,
+                            cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+            free(len);
+            return NB_ERR_CUDA;
+        }
+        if (xm && L > 0 &&
+            cudaMemcpyAsync(xm + 4 * off, c->list_xm + g * c->list_cap, sizeof(float4) * L,
+                            cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+            free(len);
+            return NB_ERR_CUDA;
+        }
+        off += len[g];
+    }
+    if (offsets) offsets[G] = off;
+    free(len);
+    CK(cudaStreamSynchronize(c->stream));
+    return NB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// nb_sort.cu -- device-wide exclusive scan and the stable LSD radix sort of
+// (63-bit Morton key, particle index) pairs that puts particles in Morton
+// order (Sec. "Test and Optimization": depth-first leaf order of the tree).
+//
+// Radix sort: 8 passes of 8-bit digits.  Each pass = per-tile digit
+// histograms (tile 4096 keys) -> exclusive scan of the digit-major
+// histogram table -> stable scatter.  Stability inside a tile comes from
+// warp-level match/rank over 32 consecutive keys at a time with per-warp
+// running digit counts, then a scan of those counts across the 8 warps.
+// No step waits on another block, so nothing can spin.
+#include "nb_internal.cuh"
+
+#define SCAN_T 256
+#define SCAN_I 8
+#define SCAN_TILE (SCAN_T * SCAN_I)
+
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *total)
+{
+    __shared__ int32_t wsum[SCAN_T / NB_WARP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int32_t s = lane < SCAN_T / NB_WARP ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < SCAN_T / NB_WARP) wsum[lane] = s;
+    }
+    __syncthreads();
+    const int32_t before = (w > 0 ? wsum[w - 1] : 0) + x - v;
+    if (total) *total = wsum[SCAN_T / NB_WARP - 1];
+    __syncthreads();
+    return before;
+}
+
+__device__ __forceinline__ int64_t eff_n(int64_t n_max, const long long *n_dev)
+{
+    if (!n_dev) return n_max;
+    const long long v = *n_dev;
+    return v < n_max ? (int64_t)v : n_max;
+}
+
+__global__ void __launch_bounds__(SCAN_T)
+k_scan_reduce(const int32_t *__restrict__ in, int64_t n_max,
+              const long long *__restrict__ n_dev, int32_t *__restrict__ bsum)
+{
+    const int64_t n = eff_n(n_max, n_dev);
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int32_t s = 0;
+    if (base < n) {
+#pragma unroll
+        for (int k = 0; k < SCAN_I; k++) {
+            const int64_t i = base + k * SCAN_T + threadIdx.x;
+            if (i < n) s += in[i];
+        }
+    }
+    int32_t tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = base < n ? tot : 0;
+}
+
+// one block: exclusive scan of the tile sums; writes out[n] and the total
+__global__ void __launch_bounds__(1024)
+k_scan_bsum(int32_t *__restrict__ bsum, int nb, int32_t *__restrict__ out,
+            int64_t n_max, const long long *__restrict__ n_dev,
+            long long *__restrict__ total_dev)
+{
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x;
+    const int per = (nb + 1023) / 1024;
+    const int lo = t * per, hi = min(nb, lo + per);
+    int32_t s = 0;
+    for (int i = lo; i < hi; i++) s += bsum[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int32_t y = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += y;
+        __syncthreads();
+    }
+    int32_t run = t > 0 ? part[t - 1] : 0;
+    for (int i = lo; i < hi; i++) {
+        const int32_t v = bsum[i];
+        bsum[i] = run;
+        run += v;
+    }
+    if (t == 1023) {
+        const int64_t n = eff_n(n_max, n_dev);
+        out[n] = part[1023];
+        if (total_dev) *total_dev = part[1023];
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_T)
+k_scan_apply(const int32_t *__restrict__ in, int32_t *__restrict__ out,
+             int64_t n_max, const long long *__restrict__ n_dev,
+             const int32_t *__restrict__ bsum)
+{
+    const int64_t n = eff_n(n_max, n_dev);
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    if (base >= n) return;
+    int32_t v[SCAN_I];
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        const int64_t i = base + threadIdx.x * SCAN_I + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    int32_t run = block_excl_scan(s, nullptr) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        const int64_t i = base + threadIdx.x * SCAN_I + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+}
+
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total.  n is
+// min(*n_dev, n_max) when n_dev is given (device-resident count), else
+// n_max.  In-place (in == out) is allowed.
+void nb_exclusive_scan(nb_ctx *c, const int32_t *in, int32_t *out, int64_t n_max,
+                       const long long *n_dev, long long *total_dev)
+{
+    const int nb = (int)((n_max + SCAN_TILE - 1) / SCAN_TILE);
+    const int g = nb > 0 ? nb : 1;
+    k_scan_reduce<<<g, SCAN_T, 0, c->stream>>>(in, n_max, n_dev, c->scan_bsum);
+    c->launches++;
+    k_scan_bsum<<<1, 1024, 0, c->stream>>>(c->scan_bsum, g, out, n_max, n_dev,
+                                           total_dev);
+    c->launches++;
+    k_scan_apply<<<g, SCAN_T, 0, c->stream>>>(in, out, n_max, n_dev, c->scan_bsum);
+    c->launches++;
+}
+
+// ------------------------------------------------------------ radix sort
+#define RS_T 256
+#define RS_I 16
+#define RS_TILE (RS_T * RS_I)
+#define RS_WARPS (RS_T / NB_WARP)
+
+__global__ void __launch_bounds__(RS_T)
+k_rs_hist(const uint64_t *__restrict__ key, int64_t n, int shift,
+          uint32_t *__restrict__ hist, int nb)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int k = 0; k < RS_I; k++) {
+        const int64_t i = base + k * RS_T + threadIdx.x;
+        if (i < n) atomicAdd(&h[(key[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_T)
+k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+             const uint32_t *__restrict__ offs, int64_t n, int shift, int nb)
+{
+    __shared__ uint32_t whist[RS_WARPS][256];
+    __shared__ uint32_t boff[256];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    for (int i = t; i < RS_WARPS * 256; i += RS_T) (&whist[0][0])[i] = 0u;
+    boff[t] = offs[(int64_t)t * nb + blockIdx.x];
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (RS_TILE / RS_WARPS);
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t key[RS_I];
+    uint32_t val[RS_I], rnk[RS_I];
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        const int64_t i = base + r * NB_WARP + lane;
+        const bool ok = i < n;
+        key[r] = ok ? kin[i] : 0ull;
+        val[r] = ok ? vin[i] : 0u;
+        const int d = ok ? (int)((key[r] >> shift) & 255u) : 256 + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned before = __popc(peers & lt);
+        const uint32_t pre = ok ? whist[w][d] : 0u;
+        __syncwarp();
+        if (ok && before == 0) whist[w][d] = pre + __popc(peers);
+        __syncwarp();
+        rnk[r] = pre + before;
+    }
+    __syncthreads();
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < RS_WARPS; ww++) {
+        const uint32_t v = whist[ww][t];
+        whist[ww][t] = run;
+        run += v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        const int64_t i = base + r * NB_WARP + lane;
+        if (i < n) {
+            const int d = (int)((key[r] >> shift) & 255u);
+            const uint32_t pos = boff[d] + whist[w][d] + rnk[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// Sort (c->keys, c->idx)[0..n) by key, stably.  Result in c->keys / c->idx.
+void nb_radix_sort(nb_ctx *c, int64_t n)
+{
+    if (n <= 1) return;
+    const int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    uint64_t *ka = c->keys, *kb = c->keys_alt;
+    uint32_t *va = c->idx, *vb = c->idx_alt;
+    for (int pass = 0; pass < 8; pass++) {
+        const int shift = 8 * pass;
+        k_rs_hist<<<nb, RS_T, 0, c->stream>>>(ka, n, shift, c->sort_hist, nb);
+        c->launches++;
+        nb_exclusive_scan(c, (const int32_t *)c->sort_hist, (int32_t *)c->sort_hist,
+                          (int64_t)256 * nb, nullptr, nullptr);
+        k_rs_scatter<<<nb, RS_T, 0, c->stream>>>(ka, va, kb, vb, c->sort_hist, n,
+                                                 shift, nb);
+        c->launches++;
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    // 8 passes: the result is back in c->keys / c->idx
+}

@@ -1,0 +1,217 @@
+"""CUDA path vs the CPU oracle on the same seeded inputs.
+
+Bit-exact: sorted order, tree topology, FP64 moments, l, s, groups, group
+boxes and every interaction list (node ids, in depth-first order).
+Tolerance: accelerations and potentials against the oracle's FP64 sums over
+the same lists, for every particle.  The bar is 1e-5 relative for plain FP32
+sums and 1e-6 for compensated (or FP64-accumulated) sums.  A rounded sum's
+error scales with the sum of its terms' magnitudes, A_i = sum_j |a_ij|, not
+with |a_i| (which cancellation can make arbitrarily small), so the bound is
+|a_i(gpu) - a_i(oracle)| <= tol * A_i for every i; in addition the median of
+|a_i(gpu) - a_i(oracle)| / |a_i(oracle)| must be a tenth of tol, and every
+potential (a sum of same-signed terms) must be within tol relative.
+"""
+import numpy as np
+import pytest
+
+import nbsynth
+from tests.gpu_common import gpu_run, oracle_tree_arrays, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def clump_set(n=6000, seed=3):
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(-1, 1, (n, 3))
+    pos[: n // 10] = 0.3 + 1e-5 * rng.normal(size=(n // 10, 3))
+    pos[n // 10: n // 10 + 7] = pos[n // 10 + 7]
+    pos[-3:] = pos[-4]
+    mass = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    return pos, mass
+
+
+CASES = {
+    "plummer16k": lambda: (nbsynth.plummer(16384, nbsynth.BASE_SEED + 1), 0.75, 64, 1 / 64),
+    "cube4097": lambda: (nbsynth.uniform_cube(4097, 11), 0.6, 32, 1e-3),
+    "cosmo12345": lambda: (nbsynth.clustered_cosmo(12345, 13, n_halos=20,
+                                                   mlo=1e-3, mhi=1e-2), 0.75, 256, 1e-3),
+    "halomix20000": lambda: (nbsynth.halo_mix(20000, 14, n_halos=50), 0.6, 128, 5e-4),
+}
+
+
+def assert_tree_equal(g, T):
+    o = oracle_tree_arrays(T)
+    t = g["tree"]
+    assert np.array_equal(t["perm"], o["perm"])
+    for k in ("level", "first", "count", "next", "parent", "nchild"):
+        assert np.array_equal(t[k], o[k]), k
+    cell = o["is_cell"] == 1
+    assert np.array_equal(t["M"], o["M"])
+    assert np.array_equal(t["com"], o["com"])
+    assert np.array_equal(t["l"][cell], o["l"][cell])
+    assert np.array_equal(t["s"][cell], o["s"][cell])
+    assert np.array_equal(t["root"][:3], T.centre) and t["root"][3] == T.L
+    assert np.array_equal(t["root"][4:], T.corner)
+
+
+def assert_lists_equal(g, T, theta, n_crit):
+    gnode, box, off, ent = T.all_lists(n_crit, theta)
+    gg = g["groups"]
+    assert np.array_equal(gg["gnode"], gnode)
+    assert np.array_equal(gg["box"], box)
+    e = T.export()
+    assert np.array_equal(gg["gfirst"], e["first"][gnode])
+    assert np.array_equal(gg["gcount"], e["count"][gnode])
+    assert np.all(gg["invtheta"] == np.float32(1.0 / theta) if theta > 0 else np.isinf(gg["invtheta"]))
+    L = g["lists"]
+    assert np.array_equal(L["offsets"], off)
+    assert np.array_equal(L["entries"], ent)
+    # the group's own particles start at self_off
+    leaf_of_slot = np.flatnonzero(e["is_cell"] == 0)
+    for k in range(len(gnode)):
+        lst = ent[off[k]:off[k + 1]]
+        first_leaf = leaf_of_slot[e["first"][gnode[k]]]
+        assert L["self_off"][k] == np.flatnonzero(lst == first_leaf)[0]
+    # FP32 source records: group-relative position within 2 ulp, exact mass
+    gid = np.repeat(np.arange(len(gnode)), np.diff(off))
+    rel = e["com"][ent] - box[gid, 6:9].astype(np.float64)
+    xm = L["xm"]
+    assert np.all(np.abs(xm[:, :3] - rel) <= 2.0 ** -22 * np.abs(rel) + 1e-45)
+    assert np.array_equal(xm[:, 3], e["M"][ent].astype(np.float32))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tree_groups_lists_bit_exact(oracle_lib, name):
+    ps, theta, n_crit, eps = CASES[name]()
+    g = gpu_run(ps.pos, ps.mass, theta=theta, n_crit=n_crit, eps=eps)
+    T = oracle_lib.Tree(ps.pos, ps.mass)
+    assert_tree_equal(g, T)
+    assert_lists_equal(g, T, theta, n_crit)
+    st = g["stats"]
+    _, _, npp, npc = T.forces(n_crit, theta, eps, gsel=np.zeros(0, np.int64))
+    a, p, npp, npc = T.forces(n_crit, theta, eps)
+    assert st["n_pp"] == npp and st["n_pc"] == npc
+    assert st["n_cells"] == T.ncells and st["n_nodes"] == T.nnodes
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp32_comp", 1e-6),
+                                           ("fp64acc", 1e-6)])
+def test_forces_within_tolerance(oracle_lib, name, precision, tol):
+    ps, theta, n_crit, eps = CASES[name]()
+    g = gpu_run(ps.pos, ps.mass, theta=theta, n_crit=n_crit, eps=eps,
+                precision=precision, lists=False)
+    T = oracle_lib.Tree(ps.pos, ps.mass)
+    a, p, _, _, amag = T.forces(n_crit, theta, eps, with_amag=True)
+    d = np.linalg.norm(g["acc"].astype(np.float64) - a, axis=1)
+    ea = rel_err(g["acc"], a)
+    ep = np.abs(g["pot"] - p) / np.abs(p)
+    print(f"{name} {precision}: |da|/|a| median {np.median(ea):.2e} p99.9 "
+          f"{np.percentile(ea, 99.9):.2e} max {ea.max():.2e}; |da|/A max "
+          f"{(d / amag).max():.2e}; pot max {ep.max():.2e}")
+    assert np.all(d <= tol * amag)
+    assert np.median(ea) <= tol / 10
+    assert np.all(ep <= tol)
+
+
+def test_edge_sizes(oracle_lib):
+    rng = np.random.default_rng(8)
+    for n in (1, 2, 3, 31, 33, 64, 65, 4095, 4096):
+        pos = rng.normal(size=(n, 3))
+        mass = rng.uniform(0.5, 2, n).astype(np.float32)
+        for n_crit in (1, 8, 4096):
+            g = gpu_run(pos, mass, theta=0.7, n_crit=n_crit, eps=0.05, max_n=5000)
+            T = oracle_lib.Tree(pos, mass)
+            assert_tree_equal(g, T)
+            assert_lists_equal(g, T, 0.7, n_crit)
+            a, p, _, _, am = T.forces(n_crit, 0.7, 0.05, with_amag=True)
+            if n == 1:
+                assert np.all(g["acc"] == 0) and g["pot"][0] == 0
+            else:
+                d = np.linalg.norm(g["acc"].astype(np.float64) - a, axis=1)
+                assert np.all(d <= 1e-5 * am)
+
+
+def test_coincident_particles_and_zero_softening(oracle_lib):
+    pos, mass = clump_set()
+    for eps in (0.0, 1e-4):
+        g = gpu_run(pos, mass, theta=0.6, n_crit=16, eps=eps)
+        T = oracle_lib.Tree(pos, mass)
+        assert_tree_equal(g, T)
+        assert_lists_equal(g, T, 0.6, 16)
+        a, p, _, _, am = T.forces(16, 0.6, eps, with_amag=True)
+        assert np.all(np.isfinite(g["acc"])) and np.all(np.isfinite(g["pot"]))
+        d = np.linalg.norm(g["acc"].astype(np.float64) - a, axis=1)
+        assert np.all(d <= 1e-5 * am)
+        assert np.all(np.abs(g["pot"] - p) <= 1e-5 * np.abs(p))
+
+
+def test_theta_zero_is_direct_sum(oracle_lib):
+    ps = nbsynth.plummer(3000, 4)
+    eps = 1 / 64
+    g = gpu_run(ps.pos, ps.mass, theta=0.0, n_crit=64, eps=eps, precision="fp32_comp")
+    ad, pd, am = oracle_lib.direct(ps.pos, ps.mass, eps, with_amag=True)
+    assert g["stats"]["n_pc"] == 0 and g["stats"]["n_pp"] == ps.n * (ps.n - 1)
+    d = np.linalg.norm(g["acc"].astype(np.float64) - ad, axis=1)
+    assert np.all(d <= 1e-6 * am)
+    assert np.all(np.abs(g["pot"] - pd) <= 1e-6 * np.abs(pd))
+
+
+def test_ncrit_one_is_per_particle_walk(oracle_lib):
+    ps = nbsynth.plummer(2000, 5)
+    g = gpu_run(ps.pos, ps.mass, theta=0.8, n_crit=1, eps=1 / 64)
+    T = oracle_lib.Tree(ps.pos, ps.mass)
+    L = g["lists"]
+    e = T.export()
+    gn = g["groups"]["gnode"]
+    for k in range(0, ps.n, 97):
+        slot = e["first"][gn[k]]
+        assert np.array_equal(L["entries"][L["offsets"][k]:L["offsets"][k + 1]],
+                              T.walk_particle(slot, 0.8))
+
+
+def test_direct_sum_judge(oracle_lib):
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.halo_mix(30000, 21, n_halos=40)
+    eps = 5e-4
+    tg = np.random.default_rng(1).choice(ps.n, 300, replace=False)
+    ad, pd = oracle_lib.direct(ps.pos, ps.mass, eps, targets=tg)
+    dev = torch.device("cuda")
+    acc, pot = nb.direct_sum(torch.from_numpy(ps.pos).to(dev),
+                             torch.from_numpy(ps.mass).to(dev), eps,
+                             torch.from_numpy(tg).to(dev))
+    assert np.max(rel_err(acc.cpu().numpy(), ad)) < 1e-12
+    assert np.max(np.abs(pot.cpu().numpy() - pd) / np.abs(pd)) < 1e-12
+
+
+def test_nonfinite_position_is_reported():
+    import paper_0909_0541_gb300 as nb
+    pos = np.random.default_rng(0).normal(size=(100, 3))
+    pos[17, 1] = np.nan
+    dev = torch.device("cuda")
+    ctx = nb.NBody(100)
+    with pytest.raises(nb.NBError) as ei:
+        ctx.build_tree(torch.from_numpy(pos).to(dev),
+                       torch.ones(100, dtype=torch.float32, device=dev))
+    assert ei.value.code == -5
+
+
+def test_call_order_and_arguments():
+    import paper_0909_0541_gb300 as nb
+    dev = torch.device("cuda")
+    ctx = nb.NBody(10)
+    acc = torch.zeros((10, 3), dtype=torch.float32, device=dev)
+    with pytest.raises(nb.NBError) as ei:
+        ctx.walk_groups(0.5, 8)
+    assert ei.value.code == -6
+    with pytest.raises(nb.NBError) as ei:
+        ctx.forces(0.1, acc)
+    assert ei.value.code == -6
+    pos = torch.zeros((11, 3), dtype=torch.float64, device=dev)
+    with pytest.raises(nb.NBError) as ei:
+        ctx.build_tree(pos, torch.ones(11, dtype=torch.float32, device=dev))
+    assert ei.value.code == -1

@@ -54,6 +54,16 @@ def test_long_double_brute_force(oracle_lib):
         assert np.max(np.abs(p1 - p2) / np.abs(p2)) < 1e-14
 
 
+def test_magnitude_sum_bounds_the_acceleration(oracle_lib):
+    # sum_j |a_ij| >= |sum_j a_ij| (triangle inequality), equal for two bodies
+    ps = nbsynth.plummer(500, 12)
+    acc, _, am = oracle_lib.direct(ps.pos, ps.mass, 0.01, with_amag=True)
+    assert np.all(am >= np.linalg.norm(acc, axis=1) * (1 - 1e-14))
+    tb = nbsynth.two_body(0.7, 0.4, 0.6, circular=False)
+    acc, _, am = oracle_lib.direct(tb.pos, tb.mass, 0.1, with_amag=True)
+    assert np.allclose(am, np.linalg.norm(acc, axis=1), rtol=1e-15)
+
+
 def test_targets_subset(oracle_lib):
     ps = nbsynth.uniform_sphere(500, 3)
     a, p = oracle_lib.direct(ps.pos, ps.mass, 0.01)
