@@ -187,6 +187,26 @@ int nb_copy_groups(nb_ctx *ctx, int32_t *gnode_host, int32_t *gfirst_host,
 int nb_copy_lists(nb_ctx *ctx, int64_t *offsets_host, int32_t *entries_host,
                   int32_t *self_off_host, float *xm_host);
 
+/* Morton order without any device allocation, for callers that cannot call
+ * cudaMalloc: it synchronises the device and is not allowed during stream
+ * capture, and where another allocator already holds most of the device
+ * memory it can fail.  The paper has no counterpart; this is the first part
+ * of nb_build_tree (root cube, 63-bit Morton keys, stable radix sort) run on
+ * caller buffers, with its scratch in one static device array of about
+ * 12.9 MB that every GPU loading the library keeps until the process exits.
+ * pos_dev: n x 3 FP64 (caller order).  keys_dev: n uint64, receives the
+ * sorted keys.  perm_dev: n int32, receives sorted slot -> caller index.
+ * n <= NB_NOALLOC_MAX_N (1,048,576), else NB_ERR_INVALID_ARG with nothing
+ * done.  The first call on each device looks up the scratch address on the
+ * current device; make that first call before any stream capture.  The call
+ * queues its work on `stream` and synchronises it before returning; it
+ * returns NB_ERR_NONFINITE for a NaN or infinite coordinate.  All calls
+ * share the scratch array and it keeps the last call's contents (each call
+ * clears what it needs cleared); calls that overlap on the GPU race. */
+#define NB_NOALLOC_MAX_N (1 << 20)
+int nb_morton_order_noalloc(const double *pos_dev, int64_t n, uint64_t *keys_dev,
+                            int32_t *perm_dev, void *stream);
+
 const char *nb_error_string(int code);
 
 #ifdef __cplusplus

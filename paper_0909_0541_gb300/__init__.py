@@ -32,8 +32,9 @@ EXPORTED = [
     "nb_build_tree", "nb_walk_groups", "nb_forces", "nb_leapfrog_step",
     "nb_leapfrog_reset", "nb_leapfrog_acc", "nb_direct_sum", "nb_sync_status",
     "nb_get_stats", "nb_copy_tree", "nb_copy_groups", "nb_copy_lists",
-    "nb_error_string", "nb_set_timing", "nb_get_timing",
+    "nb_error_string", "nb_set_timing", "nb_get_timing", "nb_morton_order_noalloc",
 ]
+NOALLOC_MAX_N = 1 << 20
 PHASES = ("build", "walk", "force", "integrate")
 
 
@@ -86,6 +87,7 @@ def _load():
     L.nb_copy_lists.argtypes = [vp] * 5
     L.nb_set_timing.argtypes = [vp, i32]
     L.nb_get_timing.argtypes = [vp, vp, vp, vp]
+    L.nb_morton_order_noalloc.argtypes = [vp, i64, vp, vp, vp]
     L.nb_error_string.argtypes = [i32]
     L.nb_error_string.restype = C.c_char_p
     return L
@@ -286,3 +288,16 @@ def direct_sum(pos, mass, eps, targets=None, stream=None):
                               acc.data_ptr(), pot.data_ptr(), _stream_handle(stream)),
            "nb_direct_sum")
     return acc, pot
+
+
+def morton_order_noalloc(pos, keys_out, perm_out, stream=None):
+    """Sorted Morton keys and sorted slot -> caller index for n <= NOALLOC_MAX_N
+    particles, computed without any device allocation (the library's static
+    scratch); keys_out (n,) int64 holding uint64 bits, perm_out (n,) int32."""
+    import torch
+    n = int(pos.shape[0])
+    _check(_lib.nb_morton_order_noalloc(_dptr(pos, torch.float64, 3, "pos"), n,
+                                        _dptr(keys_out, torch.int64, None, "keys_out"),
+                                        _dptr(perm_out, torch.int32, None, "perm_out"),
+                                        _stream_handle(stream)),
+           "nb_morton_order_noalloc")

@@ -126,7 +126,14 @@ void nb_exclusive_scan(nb_ctx *c, const int32_t *in, int32_t *out,
                        int64_t n_max, const long long *n_dev, long long *total_dev);
 void nb_radix_sort(nb_ctx *c, int64_t n);
 
+void nb_exclusive_scan_raw(const int32_t *in, int32_t *out, int64_t n_max, int32_t *bsum,
+                           cudaStream_t s);
+void nb_radix_sort_raw(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uint32_t *idx_alt,
+                       uint32_t *hist, int32_t *bsum, int64_t n, cudaStream_t s);
+
 // nb_tree.cu
+void nb_launch_keys_raw(const double *pos, int64_t n, double *part, int nblk, double *root,
+                        uint64_t *keys, uint32_t *idx, unsigned *err, cudaStream_t s);
 void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n);
 void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g);
 

@@ -238,3 +238,34 @@ void nb_radix_sort(nb_ctx *c, int64_t n)
     }
     // 8 passes: the result is back in c->keys / c->idx
 }
+
+// ------------------------------------------------------- explicit buffers
+// The same scan and sort, on buffers the caller supplies (no context).
+void nb_exclusive_scan_raw(const int32_t *in, int32_t *out, int64_t n_max, int32_t *bsum,
+                           cudaStream_t s)
+{
+    const int nb = (int)((n_max + SCAN_TILE - 1) / SCAN_TILE);
+    const int g = nb > 0 ? nb : 1;
+    k_scan_reduce<<<g, SCAN_T, 0, s>>>(in, n_max, nullptr, bsum);
+    k_scan_bsum<<<1, 1024, 0, s>>>(bsum, g, out, n_max, nullptr, nullptr);
+    k_scan_apply<<<g, SCAN_T, 0, s>>>(in, out, n_max, nullptr, bsum);
+}
+
+// keys/idx hold the input and, after the 8 passes, the sorted output;
+// hist needs 256 * ceil(n / 4096) + 1 entries, bsum the scan's tile sums.
+void nb_radix_sort_raw(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uint32_t *idx_alt,
+                       uint32_t *hist, int32_t *bsum, int64_t n, cudaStream_t s)
+{
+    if (n <= 1) return;
+    const int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    uint64_t *ka = keys, *kb = keys_alt;
+    uint32_t *va = idx, *vb = idx_alt;
+    for (int pass = 0; pass < 8; pass++) {
+        const int shift = 8 * pass;
+        k_rs_hist<<<nb, RS_T, 0, s>>>(ka, n, shift, hist, nb);
+        nb_exclusive_scan_raw((const int32_t *)hist, (int32_t *)hist, (int64_t)256 * nb, bsum, s);
+        k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, hist, n, shift, nb);
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+}

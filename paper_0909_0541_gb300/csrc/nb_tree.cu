@@ -458,3 +458,13 @@ void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
                                                           c->items);
     c->launches++;
 }
+
+// Root cube and Morton keys on buffers the caller supplies (no context):
+// part holds 6 * nblk doubles, root 7; idx receives 0..n-1.
+void nb_launch_keys_raw(const double *pos, int64_t n, double *part, int nblk, double *root,
+                        uint64_t *keys, uint32_t *idx, unsigned *err, cudaStream_t s)
+{
+    k_bbox<<<nblk, 256, 0, s>>>(pos, n, part, err);
+    k_root<<<1, 32, 0, s>>>(part, nblk, root);
+    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, root, keys, idx);
+}
