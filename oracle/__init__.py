@@ -77,7 +77,7 @@ def lib():
             L.or_all_lists.restype = i64
             L.or_all_lists.argtypes = [vp, i64, vp, vp, f64, vp, vp, i64]
             L.or_tree_forces.argtypes = [vp, i64, f64, vp, f64, i64, vp, vp,
-                                         vp, vp, vp, vp]
+                                         vp, vp, vp, vp, C.c_int]
             L.or_leapfrog.argtypes = [i64, vp, vp, vp, f64, f64, i64, C.c_int,
                                       f64, i64, vp, C.c_int]
             _lib = L
@@ -235,10 +235,13 @@ class Tree:
                            _ptr(off), _ptr(ent), tot)
         return gnode, box, off, ent[:tot]
 
-    def forces(self, n_crit, theta, eps, gsel=None, theta_g=None, with_amag=False):
+    def forces(self, n_crit, theta, eps, gsel=None, theta_g=None, with_amag=False,
+               coords32=False):
         """FP64 forces over the group lists.  Returns (acc, pot, npp, npc),
         and sum_j |a_ij| per particle last when with_amag; rows of particles
-        outside the selected groups stay NaN."""
+        outside the selected groups stay NaN.  coords32: sum over the
+        group-relative FP32 coordinates and FP32 masses instead of the FP64
+        positions (isolates arithmetic from representation error)."""
         acc = np.full((self.n, 3), np.nan)
         pot = np.full(self.n, np.nan)
         am = np.full(self.n, np.nan) if with_amag else None
@@ -248,7 +251,7 @@ class Tree:
         rc = lib().or_tree_forces(self._h, int(n_crit), float(theta), _ptr(tg),
                                   float(eps), 0 if gs is None else gs.shape[0],
                                   _ptr(gs), _ptr(acc), _ptr(pot), _ptr(am),
-                                  C.byref(npp), C.byref(npc))
+                                  C.byref(npp), C.byref(npc), 1 if coords32 else 0)
         assert rc == 0
         out = (acc, pot, int(npp.value), int(npc.value))
         return out + (am,) if with_amag else out

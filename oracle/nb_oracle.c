@@ -28,7 +28,8 @@
  * Readings where the paper is silent (the same ones the CUDA path follows):
  *   root cube   centre = bounding-box centre, side L = max extent * (1 + 2^-20)
  *               (L = 1 when every particle coincides);
- *   grid        q = clamp(floor((x - (centre - L/2)) / L * 2^21), 0, 2^21 - 1);
+ *   grid        q = clamp(floor((x - (centre - L/2)) * S), 0, 2^21 - 1), with
+ *               the scale S = 2^21 / L rounded once in FP64;
  *               depth is capped at 21 levels: a level-21 cell holding several
  *               particles keeps them as particle children, in input order;
  *   octant      digit = 4*bit_x + 2*bit_y + bit_z, children in digit order;
@@ -179,9 +180,9 @@ void or_root_cube(int64_t n, const double *pos, double *out)
         out[4 + k] = out[k] - 0.5 * L;
 }
 
-static int32_t grid_coord(double x, double corner, double L)
+static int32_t grid_coord(double x, double corner, double scale)
 {
-    const double f = floor((x - corner) / L * (double)OR_GRID);
+    const double f = floor((x - corner) * scale);
     if (f < 0.0)
         return 0;
     if (f > (double)(OR_GRID - 1))
@@ -191,9 +192,10 @@ static int32_t grid_coord(double x, double corner, double L)
 
 void or_quantize(int64_t n, const double *pos, const double *root, int32_t *q)
 {
+    const double scale = (double)OR_GRID / root[3];
     for (int64_t i = 0; i < n; i++)
         for (int k = 0; k < 3; k++)
-            q[3 * i + k] = grid_coord(pos[3 * i + k], root[4 + k], root[3]);
+            q[3 * i + k] = grid_coord(pos[3 * i + k], root[4 + k], scale);
 }
 
 /* Morton key by brute-force bit interleaving: for each level from the top,
@@ -712,11 +714,24 @@ int64_t or_all_lists(const or_tree *t, int64_t G, const int64_t *gnode,
  * own opening angle.  npp / npc receive the particle-particle and
  * particle-cell interaction counts (self pairs not counted).  amag
  * (nullable) receives sum_j |a_ij|, the scale of the rounding error of the
- * summed acceleration.                                                     */
+ * summed acceleration.
+ * coords32 != 0 first rounds every position and centre of mass to the
+ * group-relative FP32 coordinate the force sum is defined on (rel32 below:
+ * the FP64 value carried as two floats, differenced from the group's FP32
+ * box centre in FP32) and cells' masses to FP32, then sums in FP64: the
+ * result differs from the FP32 sums of the same lists only by arithmetic. */
+static float rel32(double x, float c)
+{
+    const float hi = (float)x;
+    const float lo = (float)(x - (double)hi);
+    const float d = hi - c;
+    return d + lo;
+}
+
 int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
                    const float *theta_g, double eps, int64_t nsel,
                    const int64_t *gsel, double *acc, double *pot,
-                   double *amag, int64_t *npp, int64_t *npc)
+                   double *amag, int64_t *npp, int64_t *npc, int coords32)
 {
     const int64_t G = or_groups(t, n_crit, NULL);
     int64_t *gnode = (int64_t *)malloc((size_t)(G > 0 ? G : 1) * sizeof(int64_t));
@@ -759,29 +774,43 @@ int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
             for (int64_t e = 0; e < len; e++)
                 ncell += t->is_cell[lst[e]];
             const int64_t u = gnode[g];
+            const float *cg = box + 9 * g + 6;
             for (int64_t m = 0; m < t->count[u]; m++) {
                 const int64_t slot = t->first[u] + m;
                 const int64_t i = t->order[slot];
                 const int64_t self = t->leaf[slot];
-                const double xi = t->pos[3 * i], yi = t->pos[3 * i + 1],
-                             zi = t->pos[3 * i + 2];
+                double xi = t->pos[3 * i], yi = t->pos[3 * i + 1],
+                       zi = t->pos[3 * i + 2];
+                if (coords32) {
+                    xi = rel32(xi, cg[0]);
+                    yi = rel32(yi, cg[1]);
+                    zi = rel32(zi, cg[2]);
+                }
                 double ax = 0.0, ay = 0.0, az = 0.0, p = 0.0, am = 0.0;
                 for (int64_t e = 0; e < len; e++) {
                     const int64_t v = lst[e];
                     if (v == self)
                         continue;
-                    const double dx = t->com[3 * v] - xi;
-                    const double dy = t->com[3 * v + 1] - yi;
-                    const double dz = t->com[3 * v + 2] - zi;
+                    double xv = t->com[3 * v], yv = t->com[3 * v + 1],
+                           zv = t->com[3 * v + 2], mv = t->M[v];
+                    if (coords32) {
+                        xv = rel32(xv, cg[0]);
+                        yv = rel32(yv, cg[1]);
+                        zv = rel32(zv, cg[2]);
+                        mv = (double)(float)mv;
+                    }
+                    const double dx = xv - xi;
+                    const double dy = yv - yi;
+                    const double dz = zv - zi;
                     const double r2 = dx * dx + dy * dy + dz * dz + e2;
                     if (r2 == 0.0)
                         continue;
                     const double rinv = 1.0 / sqrt(r2);
-                    const double mr3 = t->M[v] * rinv * rinv * rinv;
+                    const double mr3 = mv * rinv * rinv * rinv;
                     ax += mr3 * dx;
                     ay += mr3 * dy;
                     az += mr3 * dz;
-                    p -= t->M[v] * rinv;
+                    p -= mv * rinv;
                     am += mr3 * sqrt(dx * dx + dy * dy + dz * dz);
                 }
                 if (amag)
@@ -821,7 +850,7 @@ static int accel(int64_t n, const double *pos, const float *mass, double eps,
     if (!t)
         return -1;
     const int rc = or_tree_forces(t, n_crit, theta, NULL, eps, 0, NULL, acc,
-                                  pot, NULL, NULL, NULL);
+                                  pot, NULL, NULL, NULL, 0);
     or_tree_free(t);
     return rc;
 }

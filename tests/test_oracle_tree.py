@@ -313,3 +313,21 @@ def test_tiny_and_degenerate_inputs(oracle_lib):
     assert T.ncells == LEVELS + 1 and e["level"][T.ncells - 1] == LEVELS
     a, p, _, _ = T.forces(2, 0.6, 0.5)
     assert np.allclose(a, 0) and np.allclose(p, -4 / 0.5)
+
+
+def test_coords32_mode(oracle_lib):
+    # dyadic positions, theta 0: the group-relative FP32 coordinates are exact,
+    # so the sum equals the FP64-position sum bit for bit
+    pos, mass = dyadic_set(2048)
+    T = oracle_lib.Tree(pos, mass)
+    a64, p64, _, _ = T.forces(32, 0.0, 0.01)
+    a32, p32, _, _ = T.forces(32, 0.0, 0.01, coords32=True)
+    assert np.array_equal(a64, a32) and np.array_equal(p64, p32)
+    # general input: differs only by FP32 representation of the coordinates
+    ps = nbsynth.plummer(4000, 3)
+    T = oracle_lib.Tree(ps.pos, ps.mass)
+    a64, _, _, _, am = T.forces(64, 0.75, 1 / 64, with_amag=True)
+    a32, _, _, _ = T.forces(64, 0.75, 1 / 64, coords32=True)
+    d = np.linalg.norm(a64 - a32, axis=1)
+    assert np.all(d <= 1e-5 * am) and np.median(d / am) < 1e-7
+    assert not np.array_equal(a64, a32)
