@@ -107,21 +107,23 @@ int nb_build_tree(nb_ctx *ctx, const double *pos_dev, const float *mass_dev,
                   int64_t n);
 
 /* Form groups (each node with count <= n_crit whose parent holds more) and
- * walk the tree once per group (Fig. "treewalk_iterative" driven by the
- * next/more pointers), writing each group's interaction list of particles
- * and accepted cells to device memory in depth-first order.  A cell is
- * accepted when the squared FP32 distance from its centre of mass to the
- * group's bounding box exceeds (l/theta + s)^2 (Eq. mac; l = cell side,
- * s = |centre of mass - geometric centre|); a cell that contains the group
- * is always opened.  theta = 0 accepts no cell (direct summation).
+ * walk the tree once per group (the walk of Fig. "treewalk_iterative" in
+ * group form, breadth-first over a level-ordered copy of the tree), writing
+ * each group's interaction list of particles and accepted cells to device
+ * memory.  A cell is accepted when the squared FP32 distance from its centre
+ * of mass to the group's bounding box exceeds (l/theta + s)^2 (Eq. mac; l =
+ * cell side, s = |centre of mass - geometric centre|); a cell that contains
+ * the group is always opened.  The group's own particles are not listed:
+ * nb_forces sums them directly.  theta = 0 accepts no cell (direct sum).
  * theta_per_group_dev (nullable): one theta per group, in group order, for
  * the groups of a previous call with the same n_crit on the same tree.
  * Errors: STATE (no tree), INVALID_ARG, CAPACITY (sync_checks == 0 and a
- * list outgrew cfg.list_capacity), WALK_LIMIT, CUDA, NOMEM. */
+ * list or a walk frontier outgrew its storage), WALK_LIMIT, CUDA, NOMEM. */
 int nb_walk_groups(nb_ctx *ctx, float theta, int n_crit,
                    const float *theta_per_group_dev);
 
-/* Sum Eq. (gravity) over every group's list for every particle of the group:
+/* Sum Eq. (gravity) over every group's list and the group's own members for
+ * every particle of the group:
  * a_i = sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^{3/2},
  * phi_i = -sum_{j != i} m_j / (|x_j - x_i|^2 + eps^2)^{1/2}, cells entering as
  * point masses at their centre of mass.  Coordinates are FP32 relative to
@@ -181,11 +183,12 @@ int nb_copy_tree(nb_ctx *ctx, double *root_host, uint64_t *keys_host,
  * lo[3], hi[3], centre[3]) and the FP32 1/theta used. */
 int nb_copy_groups(nb_ctx *ctx, int32_t *gnode_host, int32_t *gfirst_host,
                    int32_t *gcount_host, float *box_host, float *invtheta_host);
-/* Lists of the last walk, packed: offsets (G+1), node ids, the position of
- * the group's own first particle in its list, and the FP32 source records
- * the force kernel reads (x, y, z relative to the group centre, mass). */
+/* Lists of the last walk, packed: offsets (G+1), preorder node ids in walk
+ * (breadth-first) order, and the FP32 source records the force kernel reads
+ * (x, y, z relative to the group centre, mass).  The group's own particles
+ * are not in its list. */
 int nb_copy_lists(nb_ctx *ctx, int64_t *offsets_host, int32_t *entries_host,
-                  int32_t *self_off_host, float *xm_host);
+                  float *xm_host);
 
 /* Morton order without any device allocation, for callers that cannot call
  * cudaMalloc: it synchronises the device and is not allowed during stream

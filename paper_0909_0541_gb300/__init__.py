@@ -84,7 +84,7 @@ def _load():
     L.nb_get_stats.argtypes = [vp, C.POINTER(nb_stats)]
     L.nb_copy_tree.argtypes = [vp] * 14
     L.nb_copy_groups.argtypes = [vp] * 6
-    L.nb_copy_lists.argtypes = [vp] * 5
+    L.nb_copy_lists.argtypes = [vp] * 4
     L.nb_set_timing.argtypes = [vp, i32]
     L.nb_get_timing.argtypes = [vp, vp, vp, vp]
     L.nb_morton_order_noalloc.argtypes = [vp, i64, vp, vp, vp]
@@ -267,10 +267,9 @@ class NBody:
         st = self.stats()
         G, tot = st["n_groups"], st["list_entries"]
         d = dict(offsets=np.zeros(G + 1, np.int64), entries=np.zeros(tot, np.int32),
-                 self_off=np.zeros(G, np.int32),
                  xm=np.zeros((tot, 4), np.float32) if with_xm else None)
         _check(_lib.nb_copy_lists(self._h, _hptr(d["offsets"]), _hptr(d["entries"]),
-                                  _hptr(d["self_off"]), _hptr(d["xm"])), "nb_copy_lists")
+                                  _hptr(d["xm"])), "nb_copy_lists")
         return d
 
 

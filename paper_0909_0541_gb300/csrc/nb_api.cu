@@ -50,11 +50,12 @@ static void free_all(nb_ctx *c)
 {
     void *ptrs[] = {c->keys, c->keys_alt, c->idx, c->idx_alt, c->sort_hist, c->scan_bsum,
                     c->root, c->bbox_part, c->p_hi, c->p_lo, c->p_x64, c->perm, c->clev,
-                    c->ccount, c->cstart, c->node_a, c->node_b, c->node_c, c->n_level,
-                    c->n_first, c->n_count, c->n_parent, c->n_nchild, c->n_arrive,
-                    c->n_mass, c->n_mx, c->n_com, c->gflag, c->gnode, c->gfirst, c->gcount,
-                    c->glen, c->gself, c->gcells, c->gbox, c->items, c->item_cnt,
-                    c->list_id, c->list_xm, c->acc_cache, c->pot_cache, c->err, c->cnt};
+                    c->ccount, c->cstart, c->node_c, c->n_level, c->n_first, c->n_count,
+                    c->n_parent, c->n_nchild, c->n_depth, c->bfs2pid, c->pid2bfs, c->dhist,
+                    c->level_start, c->w_a, c->w_d, c->w_b, c->w_c, c->b_mass, c->b_mx,
+                    c->b_com, c->gflag, c->gnode, c->gfirst, c->gcount, c->glen, c->gcells,
+                    c->gbox, c->items, c->item_cnt, c->list_id, c->list_xm, c->wq,
+                    c->acc_cache, c->pot_cache, c->err, c->cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cnt_host) cudaFreeHost(c->cnt_host);
@@ -76,18 +77,25 @@ static int err_code(unsigned bits)
 {
     if (bits & NB_EF_NONFINITE) return NB_ERR_NONFINITE;
     if (bits & NB_EF_WALK) return NB_ERR_WALK_LIMIT;
-    if (bits & NB_EF_CAPACITY) return NB_ERR_CAPACITY;
+    if (bits & (NB_EF_CAPACITY | NB_EF_QUEUE)) return NB_ERR_CAPACITY;
     return NB_OK;
 }
 
 // synchronise, read and clear the device error word
+static int sync_read_bits(nb_ctx *c, unsigned *bits)
+{
+    *bits = 0;
+    CK(cudaMemcpyAsync(bits, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (*bits) CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    return NB_OK;
+}
+
 static int sync_read(nb_ctx *c)
 {
     unsigned bits = 0;
-    CK(cudaMemcpyAsync(&bits, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (bits) CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
-    return err_code(bits);
+    const int rc = sync_read_bits(c, &bits);
+    return rc ? rc : err_code(bits);
 }
 
 static int read_counters(nb_ctx *c)
@@ -175,7 +183,10 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
     c->max_nodes = NN;
     const int64_t rs_tiles = (N + 4095) / 4096;
     c->sort_hist_len = 256 * rs_tiles + 1;
+    c->dtiles = (NN + 4095) / 4096;
+    const int64_t dhist_len = NB_DEPTHS * c->dtiles + 1;
     int64_t scan_n = NN + 1 > c->sort_hist_len ? NN + 1 : c->sort_hist_len;
+    if (dhist_len > scan_n) scan_n = dhist_len;
     c->scan_bsum_len = (scan_n + 2047) / 2048 + 2;
     c->bbox_blocks = c->num_sms * 4;
     c->max_items = N + N / 64 + 2;
@@ -185,13 +196,15 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
               dalloc(&c->bbox_part, 6 * (int64_t)c->bbox_blocks) && dalloc(&c->p_hi, N) &&
               dalloc(&c->p_lo, N) && dalloc(&c->p_x64, 3 * N) && dalloc(&c->perm, N) &&
               dalloc(&c->clev, N) && dalloc(&c->ccount, N + 1) && dalloc(&c->cstart, N + 1) &&
-              dalloc(&c->node_a, NN) && dalloc(&c->node_b, NN) && dalloc(&c->node_c, NN) &&
-              dalloc(&c->n_level, NN) && dalloc(&c->n_first, NN) && dalloc(&c->n_count, NN) &&
-              dalloc(&c->n_parent, NN) && dalloc(&c->n_nchild, NN) &&
-              dalloc(&c->n_arrive, NN) && dalloc(&c->n_mass, NN) && dalloc(&c->n_mx, 3 * NN) &&
-              dalloc(&c->n_com, 3 * NN) && dalloc(&c->gflag, NN + 1) && dalloc(&c->gnode, N) &&
+              dalloc(&c->node_c, NN) && dalloc(&c->n_level, NN) && dalloc(&c->n_first, NN) &&
+              dalloc(&c->n_count, NN) && dalloc(&c->n_parent, NN) && dalloc(&c->n_nchild, NN) &&
+              dalloc(&c->n_depth, NN) && dalloc(&c->bfs2pid, NN) && dalloc(&c->pid2bfs, NN) &&
+              dalloc(&c->dhist, dhist_len) && dalloc(&c->level_start, NB_DEPTHS + 1) &&
+              dalloc(&c->w_a, NN) && dalloc(&c->w_d, NN) && dalloc(&c->w_b, NN) &&
+              dalloc(&c->w_c, NN) && dalloc(&c->b_mass, NN) && dalloc(&c->b_mx, 3 * NN) &&
+              dalloc(&c->b_com, 3 * NN) && dalloc(&c->gflag, NN + 1) && dalloc(&c->gnode, N) &&
               dalloc(&c->gfirst, N) && dalloc(&c->gcount, N) && dalloc(&c->glen, N) &&
-              dalloc(&c->gself, N) && dalloc(&c->gcells, N) && dalloc(&c->gbox, 3 * N) &&
+              dalloc(&c->gcells, N) && dalloc(&c->gbox, 3 * N) &&
               dalloc(&c->items, 2 * c->max_items) && dalloc(&c->item_cnt, N + 1) &&
               dalloc(&c->acc_cache, 3 * N) && dalloc(&c->pot_cache, N) &&
               dalloc(&c->err, 1) && dalloc(&c->cnt, CNT_N_) &&
@@ -211,6 +224,14 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
         return NB_ERR_CUDA;
     }
     c->list_cap = cfg->list_capacity;
+    c->walk_warps = nb_walk_warps(c);
+    c->wq_cap = 4096;
+    if (!dalloc(&c->wq, 2 * c->wq_cap * c->walk_warps)) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return NB_ERR_NOMEM;
+    }
     *out = c;
     return NB_OK;
 }
@@ -269,22 +290,42 @@ int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
         const int64_t G = c->cnt_host[CNT_GROUPS];
         c->groups_host = G;
         int64_t cap = c->list_cap > 0 ? c->list_cap : 4096;
-        for (int attempt = 0; attempt < 2; attempt++) {
+        for (int attempt = 0; attempt < 4; attempt++) {
             rc = ensure_lists(c, G, cap);
             if (rc) return rc;
             nb_launch_walk(c);
-            rc = finish(c);
-            if (rc != NB_ERR_CAPACITY || c->cfg.list_capacity > 0) break;
+            if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
+            unsigned bits = 0;
+            rc = sync_read_bits(c, &bits);
+            if (rc) return rc;
+            rc = err_code(bits);
+            if (rc != NB_ERR_CAPACITY) break;
             rc = read_counters(c);
             if (rc) return rc;
-            const int64_t need = c->cnt_host[CNT_LIST_MAX];
-            cap = ((need + need / 4 + 255) / 256) * 256;
+            if (bits & NB_EF_QUEUE) {   // a frontier outgrew the walk queues
+                const int64_t want = 2 * (c->cnt_host[CNT_QMAX] > c->wq_cap ? c->cnt_host[CNT_QMAX]
+                                                                            : c->wq_cap);
+                CK(cudaStreamSynchronize(c->stream));
+                cudaFree(c->wq);
+                c->wq = nullptr;
+                if (!dalloc(&c->wq, 2 * want * c->walk_warps)) {
+                    cudaGetLastError();
+                    c->wq_cap = 0;
+                    return NB_ERR_NOMEM;
+                }
+                c->wq_cap = want;
+            }
+            if (bits & NB_EF_CAPACITY) {
+                if (c->cfg.list_capacity > 0) return NB_ERR_CAPACITY;
+                const int64_t need = c->cnt_host[CNT_LIST_MAX];
+                cap = ((need + need / 4 + 255) / 256) * 256;
+            }
             rc = NB_ERR_CAPACITY;
         }
         phase_end(c, tk, NB_PHASE_WALK);
         if (rc) return rc;
     } else {
-        if (c->list_cap < 1 || !c->list_id) return NB_ERR_CAPACITY;
+        if (c->list_cap < 1 || !c->list_id || !c->wq) return NB_ERR_CAPACITY;
         nb_launch_walk(c);
         phase_end(c, tk, NB_PHASE_WALK);
         int rc = finish(c);
@@ -460,32 +501,46 @@ int nb_copy_tree(nb_ctx *c, double *root, uint64_t *keys, int32_t *perm, int32_t
     D2H(count, c->n_count, nn);
     D2H(parent, c->n_parent, nn);
     D2H(nchild, c->n_nchild, nn);
-    D2H(mass, c->n_mass, nn);
-    D2H(com, c->n_com, 3 * nn);
-    int4 *nc = nullptr;
-    if ((next || l || s) && nn > 0) {
-        nc = (int4 *)malloc(sizeof(int4) * (size_t)nn);
-        if (!nc) return NB_ERR_NOMEM;
-        if (cudaMemcpyAsync(nc, c->node_c, sizeof(int4) * (size_t)nn, cudaMemcpyDeviceToHost,
-                            c->stream) != cudaSuccess) {
-            free(nc);
-            return NB_ERR_CUDA;
-        }
+    if (nn == 0) {
+        CK(cudaStreamSynchronize(c->stream));
+        return NB_OK;
     }
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
-        free(nc);
-        return NB_ERR_CUDA;
-    }
-    for (int64_t u = 0; nc && u < nn; u++) {
+    // preorder views of the level-order moment arrays
+    int4 *nc = (int4 *)malloc(sizeof(int4) * (size_t)nn);
+    int32_t *p2b = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
+    double *bm = (double *)malloc(sizeof(double) * (size_t)nn);
+    double *bc = (double *)malloc(sizeof(double) * 3 * (size_t)nn);
+    float2 *wc = (float2 *)malloc(sizeof(float2) * (size_t)nn);
+    rc = NB_OK;
+    if (!nc || !p2b || !bm || !bc || !wc) rc = NB_ERR_NOMEM;
+    if (!rc && (cudaMemcpyAsync(nc, c->node_c, sizeof(int4) * nn, cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(p2b, c->pid2bfs, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(bm, c->b_mass, sizeof(double) * nn, cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(bc, c->b_com, sizeof(double) * 3 * nn, cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(wc, c->w_c, sizeof(float2) * nn, cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess))
+        rc = NB_ERR_CUDA;
+    for (int64_t u = 0; !rc && u < nn; u++) {
+        const int64_t b = p2b[u];
         if (next) next[u] = nc[u].x >= nn ? -1 : nc[u].x;
-        float lf, sf;
-        memcpy(&lf, &nc[u].y, 4);
-        memcpy(&sf, &nc[u].z, 4);
-        if (l) l[u] = lf;
-        if (s) s[u] = sf;
+        if (mass) mass[u] = bm[b];
+        if (com)
+            for (int d = 0; d < 3; d++) com[3 * u + d] = bc[3 * b + d];
+        if (l) l[u] = wc[b].x;
+        if (s) s[u] = wc[b].y;
     }
     free(nc);
-    return NB_OK;
+    free(p2b);
+    free(bm);
+    free(bc);
+    free(wc);
+    if (rc == NB_ERR_CUDA) cudaGetLastError();
+    return rc;
 }
 
 int nb_copy_groups(nb_ctx *c, int32_t *gnode, int32_t *gfirst, int32_t *gcount, float *box,
@@ -527,8 +582,7 @@ int nb_copy_groups(nb_ctx *c, int32_t *gnode, int32_t *gfirst, int32_t *gcount, 
     return NB_OK;
 }
 
-int nb_copy_lists(nb_ctx *c, int64_t *offsets, int32_t *entries, int32_t *self_off,
-                  float *xm)
+int nb_copy_lists(nb_ctx *c, int64_t *offsets, int32_t *entries, float *xm)
 {
     if (!c) return NB_ERR_INVALID_ARG;
     if (!c->has_lists) return NB_ERR_STATE;
@@ -543,8 +597,6 @@ int nb_copy_lists(nb_ctx *c, int64_t *offsets, int32_t *entries, int32_t *self_o
     if (!len) return NB_ERR_NOMEM;
     if (cudaMemcpyAsync(len, c->glen, sizeof(int32_t) * (size_t)G, cudaMemcpyDeviceToHost,
                         c->stream) != cudaSuccess ||
-        (self_off && cudaMemcpyAsync(self_off, c->gself, sizeof(int32_t) * (size_t)G,
-                                     cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
         free(len);
         return NB_ERR_CUDA;

@@ -1,28 +1,28 @@
 // nb_force.cu -- Eq. (gravity) summed over each group's interaction list.
 //
-// Work item = (group, 64 consecutive members).  One warp takes one item from
-// a global queue; each lane owns FR = 2 target particles (FP32 coordinates
-// relative to the group centre) and the warp streams the group's list in
-// tiles of 32 source records: one coalesced 16-byte load per lane into a
-// per-warp shared-memory tile, then every lane reads each record by
-// broadcast and applies it to its FR targets.  The interaction is
+// Work item = (group, up to 64 consecutive members).  One warp takes one
+// item from a global queue; each lane owns R target particles (R = 2, or 1
+// when the item's targets fit one 32-wide row) as FP32 coordinates relative
+// to the group centre.  The warp streams sources in tiles of 32 records: one
+// coalesced 16-byte load per lane into a per-warp shared-memory tile, then
+// every lane reads each record by broadcast and applies it to its R targets:
 //   dx = xj - xi (3 FADD); r2 = eps^2 + dx.dx (3 FFMA); ri = rsqrt(r2) (MUFU);
 //   mr = mj ri; mr3 = mr ri ri (3 FMUL); a += mr3 dx (3 FFMA); phi -= mr (FADD)
-// i.e. 13 FP32-pipe instructions and one MUFU.  This stays on the CUDA
-// cores: there is no dense contraction to hand to the tensor cores.
+// i.e. 13 FP32-pipe instructions and one MUFU per interaction.  This stays on
+// the CUDA cores: there is no dense contraction to hand to the tensor cores.
 //
-// The group's own particles sit contiguously in its list (they are emitted
-// when the walk descends through the group's node), starting at gself[g];
-// only tiles overlapping that run take the masked path that drops j == i.
-// Padding records beyond the list end are massless and far away.
+// Two phases per item: (1) the group's list (particles and accepted cells
+// outside the group), unmasked; (2) the group's own members, read from the
+// sorted particle arrays and converted to the same group-relative FP32
+// coordinates, with the j == i term dropped by index.  Padding records are
+// massless and far away.
 #include <float.h>
 
 #include "nb_internal.cuh"
 
-#define NB_IBLOCK 64
-#define FR 2
 #define F_T 256
 #define F_WARPS (F_T / NB_WARP)
+#define ITEM_ONE_ROW (1 << 30)
 
 enum { MODE_FP32 = 0, MODE_COMP = 1, MODE_F64 = 2 };
 
@@ -36,7 +36,7 @@ __device__ __forceinline__ float mufu_rsqrt(float x)
 template <int MODE>
 struct Acc {
     float x, y, z, p;        // running (or per-tile) sums
-    float cx, cy, cz, cp;    // compensation (MODE_COMP) / unused
+    float cx, cy, cz, cp;    // Kahan compensation (MODE_COMP)
     double dx, dy, dz, dp;   // FP64 sums (MODE_F64)
     __device__ __forceinline__ void init()
     {
@@ -84,17 +84,121 @@ __device__ __forceinline__ void interact(const float4 q, float xi, float yi, flo
     }
 }
 
+// one 32-record tile against the lane's R targets
+template <int MODE, bool GUARD, bool MASK, int R>
+__device__ __forceinline__ void tile_pass(const float4 *tile, int32_t j0, const float *xi,
+                                          const float *yi, const float *zi, const int32_t *kk,
+                                          float eps2, Acc<MODE> *A, Acc<MODE> *T)
+{
+#pragma unroll 8
+    for (int j = 0; j < NB_WARP; j++) {
+        const float4 q = tile[j];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const bool me = MASK && (j0 + j == kk[r]);
+            if constexpr (MODE == MODE_COMP)
+                interact<MODE, GUARD, MASK>(q, xi[r], yi[r], zi[r], eps2, me, T[r]);
+            else
+                interact<MODE, GUARD, MASK>(q, xi[r], yi[r], zi[r], eps2, me, A[r]);
+        }
+    }
+    if constexpr (MODE == MODE_COMP) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            kahan(A[r].x, A[r].cx, T[r].x);
+            kahan(A[r].y, A[r].cy, T[r].y);
+            kahan(A[r].z, A[r].cz, T[r].z);
+            kahan(A[r].p, A[r].cp, T[r].p);
+            T[r].x = T[r].y = T[r].z = T[r].p = 0.f;
+        }
+    }
+}
+
+template <int MODE, bool GUARD, int R>
+__device__ __forceinline__ void force_item(
+    int32_t g, int32_t i0, float4 *tile, const int32_t *__restrict__ gfirst,
+    const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
+    const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
+    const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
+    const float4 *__restrict__ list_xm, int64_t cap, float eps2, float *__restrict__ acc,
+    float *__restrict__ pot)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t f = gfirst[g], ng = gcount[g];
+    // a list that outgrew its slot was reported by the walk; never read past the slot
+    const int32_t len = glen[g] < cap ? glen[g] : (int32_t)cap;
+    const float4 bc = gbox[3 * (int64_t)g + 2];
+    const float4 pad = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+    float xi[R], yi[R], zi[R];
+    int32_t kk[R], slot[R];
+    bool ok[R];
+    Acc<MODE> A[R], T[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int32_t k = i0 + r * NB_WARP + lane;
+        ok[r] = k < ng;
+        kk[r] = k;
+        slot[r] = f + (ok[r] ? k : ng - 1);
+        const float4 h = p_hi[slot[r]], lo = p_lo[slot[r]];
+        xi[r] = nb_rel(h.x, lo.x, bc.x);
+        yi[r] = nb_rel(h.y, lo.y, bc.y);
+        zi[r] = nb_rel(h.z, lo.z, bc.z);
+        A[r].init();
+        T[r].init();
+    }
+    // (1) the list: sources outside the group
+    const float4 *__restrict__ src = list_xm + (int64_t)g * cap;
+    for (int32_t j0 = 0; j0 < len; j0 += NB_WARP) {
+        const int32_t jj = j0 + lane;
+        tile[lane] = jj < len ? src[jj] : pad;
+        __syncwarp();
+        tile_pass<MODE, GUARD, false, R>(tile, j0, xi, yi, zi, kk, eps2, A, T);
+        __syncwarp();
+    }
+    // (2) the group's own members, j != i
+    for (int32_t j0 = 0; j0 < ng; j0 += NB_WARP) {
+        const int32_t jj = j0 + lane;
+        if (jj < ng) {
+            const float4 h = p_hi[f + jj], lo = p_lo[f + jj];
+            tile[lane] = make_float4(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y),
+                                     nb_rel(h.z, lo.z, bc.z), h.w);
+        } else {
+            tile[lane] = pad;
+        }
+        __syncwarp();
+        tile_pass<MODE, GUARD, true, R>(tile, j0, xi, yi, zi, kk, eps2, A, T);
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        if (!ok[r]) continue;
+        const int64_t o = perm[slot[r]];
+        float ax, ay, az, ph;
+        if (MODE == MODE_F64) {
+            ax = (float)A[r].dx; ay = (float)A[r].dy; az = (float)A[r].dz; ph = (float)A[r].dp;
+        } else if (MODE == MODE_COMP) {
+            ax = A[r].x - A[r].cx; ay = A[r].y - A[r].cy;
+            az = A[r].z - A[r].cz; ph = A[r].p - A[r].cp;
+        } else {
+            ax = A[r].x; ay = A[r].y; az = A[r].z; ph = A[r].p;
+        }
+        acc[3 * o] = ax;
+        acc[3 * o + 1] = ay;
+        acc[3 * o + 2] = az;
+        if (pot) pot[o] = ph;
+    }
+}
+
 template <int MODE, bool GUARD>
 __global__ void __launch_bounds__(F_T)
 k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ gfirst,
         const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
-        const int32_t *__restrict__ gself, const float4 *__restrict__ gbox,
-        const float4 *__restrict__ p_hi, const float4 *__restrict__ p_lo,
-        const int32_t *__restrict__ perm, const float4 *__restrict__ list_xm, int64_t cap,
-        long long *__restrict__ cnt, float eps2, float *__restrict__ acc,
-        float *__restrict__ pot)
+        const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
+        const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
+        const float4 *__restrict__ list_xm, int64_t cap, long long *__restrict__ cnt,
+        float eps2, float *__restrict__ acc, float *__restrict__ pot)
 {
-    __shared__ float4 tile[F_WARPS][NB_WARP];
+    __shared__ float4 tiles[F_WARPS][NB_WARP];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int32_t nitems = (int32_t)cnt[CNT_ITEMS];
@@ -103,90 +207,14 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ gfirst,
         if (lane == 0) it = (int)nb_atomic_add(&cnt[CNT_FORCE_Q], 1LL);
         it = __shfl_sync(FULL, it, 0);
         if (it >= nitems) break;
-        const int32_t g = items[2 * (int64_t)it], i0 = items[2 * (int64_t)it + 1];
-        const int32_t f = gfirst[g], ng = gcount[g], self = gself[g];
-        // a list that outgrew its slot was reported by the walk; never read past the slot
-        const int32_t len = glen[g] < cap ? glen[g] : (int32_t)cap;
-        const float4 bc = gbox[3 * (int64_t)g + 2];
-        const float4 *__restrict__ src = list_xm + (int64_t)g * cap;
-        float xi[FR], yi[FR], zi[FR];
-        int32_t kk[FR], slot[FR];
-        bool ok[FR];
-        Acc<MODE> A[FR], T[FR];
-#pragma unroll
-        for (int r = 0; r < FR; r++) {
-            const int32_t k = i0 + r * NB_WARP + lane;
-            ok[r] = k < ng;
-            slot[r] = f + (ok[r] ? k : ng - 1);
-            const float4 h = p_hi[slot[r]], lo = p_lo[slot[r]];
-            xi[r] = __fadd_rn(__fsub_rn(h.x, bc.x), lo.x);
-            yi[r] = __fadd_rn(__fsub_rn(h.y, bc.y), lo.y);
-            zi[r] = __fadd_rn(__fsub_rn(h.z, bc.z), lo.z);
-            kk[r] = self + k;
-            A[r].init();
-            T[r].init();
-        }
-        for (int32_t j0 = 0; j0 < len; j0 += NB_WARP) {
-            const int32_t jj = j0 + lane;
-            tile[w][lane] = jj < len ? src[jj] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-            __syncwarp();
-            const bool st = (self < j0 + NB_WARP) && (self + ng > j0);
-            if (!st) {
-#pragma unroll 8
-                for (int j = 0; j < NB_WARP; j++) {
-                    const float4 q = tile[w][j];
-#pragma unroll
-                    for (int r = 0; r < FR; r++) {
-                        if constexpr (MODE == MODE_COMP)
-                            interact<MODE, GUARD, false>(q, xi[r], yi[r], zi[r], eps2, false, T[r]);
-                        else
-                            interact<MODE, GUARD, false>(q, xi[r], yi[r], zi[r], eps2, false, A[r]);
-                    }
-                }
-            } else {
-#pragma unroll 4
-                for (int j = 0; j < NB_WARP; j++) {
-                    const float4 q = tile[w][j];
-#pragma unroll
-                    for (int r = 0; r < FR; r++) {
-                        const bool me = j0 + j == kk[r];
-                        if constexpr (MODE == MODE_COMP)
-                            interact<MODE, GUARD, true>(q, xi[r], yi[r], zi[r], eps2, me, T[r]);
-                        else
-                            interact<MODE, GUARD, true>(q, xi[r], yi[r], zi[r], eps2, me, A[r]);
-                    }
-                }
-            }
-            __syncwarp();
-            if constexpr (MODE == MODE_COMP) {
-#pragma unroll
-                for (int r = 0; r < FR; r++) {
-                    kahan(A[r].x, A[r].cx, T[r].x);
-                    kahan(A[r].y, A[r].cy, T[r].y);
-                    kahan(A[r].z, A[r].cz, T[r].z);
-                    kahan(A[r].p, A[r].cp, T[r].p);
-                    T[r].x = T[r].y = T[r].z = T[r].p = 0.f;
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < FR; r++) {
-            if (!ok[r]) continue;
-            const int64_t o = perm[slot[r]];
-            float ax, ay, az, ph;
-            if (MODE == MODE_F64) {
-                ax = (float)A[r].dx; ay = (float)A[r].dy; az = (float)A[r].dz; ph = (float)A[r].dp;
-            } else if (MODE == MODE_COMP) {
-                ax = A[r].x - A[r].cx; ay = A[r].y - A[r].cy;
-                az = A[r].z - A[r].cz; ph = A[r].p - A[r].cp;
-            } else {
-                ax = A[r].x; ay = A[r].y; az = A[r].z; ph = A[r].p;
-            }
-            acc[3 * o] = ax;
-            acc[3 * o + 1] = ay;
-            acc[3 * o + 2] = az;
-            if (pot) pot[o] = ph;
-        }
+        const int32_t g = items[2 * (int64_t)it], word = items[2 * (int64_t)it + 1];
+        const int32_t i0 = word & ~ITEM_ONE_ROW;
+        if (word & ITEM_ONE_ROW)
+            force_item<MODE, GUARD, 1>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo,
+                                       perm, list_xm, cap, eps2, acc, pot);
+        else
+            force_item<MODE, GUARD, 2>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo,
+                                       perm, list_xm, cap, eps2, acc, pot);
     }
 }
 
@@ -199,8 +227,8 @@ static void launch_force(nb_ctx *c, float eps2, float *acc, float *pot)
         if (blocks < 1) blocks = 1;
     }
     k_force<MODE, GUARD><<<c->num_sms * blocks, F_T, 0, c->stream>>>(
-        c->items, c->gfirst, c->gcount, c->glen, c->gself, c->gbox, c->p_hi, c->p_lo,
-        c->perm, c->list_xm, c->list_cap, c->cnt, eps2, acc, pot);
+        c->items, c->gfirst, c->gcount, c->glen, c->gbox, c->p_hi, c->p_lo, c->perm,
+        c->list_xm, c->list_cap, c->cnt, eps2, acc, pot);
     c->launches++;
 }
 

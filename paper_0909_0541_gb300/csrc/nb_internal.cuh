@@ -1,18 +1,27 @@
 // nb_internal.cuh -- device-side layout shared by the libnb translation units.
 //
-// HBM layout (all per context, allocated once for max_n particles):
+// HBM layout (all per context, allocated once for max_n particles; NN = 12N+2
+// node slots bound the cells + particle leaves of any input):
 //   sorted particles  p_hi[N] float4 (x,y,z as the FP32 nearest to the FP64
 //                     position, mass), p_lo[N] float4 (FP32 remainders),
 //                     p_x64[3N] FP64 positions, perm[N] sorted slot -> caller
-//   tree nodes        depth-first preorder over cells and particle leaves:
-//                     node_a[NN] float4 (centre of mass hi part, mass)
-//                     node_b[NN] float4 (centre of mass lo part, 0)
-//                     node_c[NN] int4   (next, l bits, s bits, is_particle)
-//                     plus FP64 moments and integer topology for export
-//   groups            gnode/gfirst/gcount, gbox[3G] float4 (lo, hi,
-//                     centre + 1/theta), list length / self offset
-//   lists             list_id[G * cap] int32, list_xm[G * cap] float4
-//                     (group-relative position, mass), slot g at g * cap
+//   topology          depth-first preorder ("pid"): node_c int4 (next, -, -,
+//                     is_particle), level, first particle, count, parent,
+//                     number of children, depth
+//   walk records      level order ("bfs": nodes sorted by depth, preorder
+//                     inside a depth), so the children of a cell are one
+//                     contiguous run:
+//                       w_a float4 (centre of mass hi part, FP32 mass)
+//                       w_b int4   (pid, preorder next, first child, children)
+//                       w_c float2 (l, s)
+//                       w_d float4 (centre of mass lo part, 0)
+//                     and FP64 mass, first moment and centre of mass
+//   groups            gnode (pid), first slot, size, box 3 x float4 (lo, hi,
+//                     centre + 1/theta), list length, cell entries
+//   lists             slot g at g * cap: list_id int32 (pid), list_xm float4
+//                     (group-relative x, y, z, mass); the group's own
+//                     particles are not listed (the force kernel sums them)
+//   walk queues       two frontier queues of wq_cap node indices per warp
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,13 +30,16 @@
 #include "../../include/nb.h"
 
 #define NB_LEVELS 21
-#define NB_EV_POOL 2048
+#define NB_DEPTHS 23   // tree depths 0..22 (level-21 buckets hold depth-22 leaves)
 #define NB_WARP 32
+#define NB_EV_POOL 2048
+#define NB_IBLOCK 64   // targets per force work item (two per lane)
 
 // bits of the device error word
 #define NB_EF_NONFINITE 1u
 #define NB_EF_CAPACITY 2u
 #define NB_EF_WALK 4u
+#define NB_EF_QUEUE 8u
 
 // device counters (int64 slots of ctx->cnt)
 enum {
@@ -42,6 +54,7 @@ enum {
     CNT_FORCE_Q,     // force work queue head
     CNT_ITEMS,       // force work items
     CNT_MAXLEVEL,
+    CNT_QMAX,        // widest walk frontier
     CNT_PP_CUM,      // n_pp over every walk (never reset)
     CNT_PC_CUM,
     CNT_N_
@@ -71,7 +84,7 @@ struct nb_ctx {
     int32_t *scan_bsum;
     int64_t scan_bsum_len;
 
-    // root: centre[3], L, corner[3]; bbox partials
+    // root: centre[3], L, corner[3], 2^21 / L; bbox partials
     double *root;
     double *bbox_part;
     int bbox_blocks;
@@ -84,17 +97,26 @@ struct nb_ctx {
     int32_t *ccount;  // cells starting at each particle
     int32_t *cstart;  // exclusive scan of ccount (N + 1)
 
-    // nodes
-    float4 *node_a, *node_b;
+    // topology, preorder
     int4 *node_c;
-    int32_t *n_level, *n_first, *n_count, *n_parent, *n_nchild, *n_arrive;
-    double *n_mass, *n_mx, *n_com;  // FP64 moments (mx, com: 3 per node)
+    int32_t *n_level, *n_first, *n_count, *n_parent, *n_nchild;
+    int8_t *n_depth;
+
+    // level order
+    int32_t *bfs2pid, *pid2bfs;
+    uint32_t *dhist;       // depth histogram per tile, scanned (NB_DEPTHS x tiles + 1)
+    int64_t dtiles;
+    int32_t *level_start;  // NB_DEPTHS + 1
+    float4 *w_a, *w_d;
+    int4 *w_b;
+    float2 *w_c;
+    double *b_mass, *b_mx, *b_com;  // FP64 moments in level order (mx, com: 3 per node)
 
     // groups
     int32_t *gflag;   // per node flag, scanned in place to group ids (NN + 1)
-    int32_t *gnode, *gfirst, *gcount, *glen, *gself, *gcells;
+    int32_t *gnode, *gfirst, *gcount, *glen, *gcells;
     float4 *gbox;     // 3 per group
-    int32_t *items;   // force work items: (group, first member) pairs
+    int32_t *items;   // force work items: (group, first member | one-warp-row flag)
     int32_t *item_cnt;
     int64_t max_items;
 
@@ -103,6 +125,11 @@ struct nb_ctx {
     int64_t list_alloc;   // entries allocated
     int32_t *list_id;
     float4 *list_xm;
+
+    // walk frontier queues
+    int32_t *wq;
+    int64_t wq_cap;       // entries per queue
+    int walk_warps;       // warps the queues were sized for
 
     // leapfrog
     float *acc_cache, *pot_cache;
@@ -125,7 +152,6 @@ struct nb_ctx {
 void nb_exclusive_scan(nb_ctx *c, const int32_t *in, int32_t *out,
                        int64_t n_max, const long long *n_dev, long long *total_dev);
 void nb_radix_sort(nb_ctx *c, int64_t n);
-
 void nb_exclusive_scan_raw(const int32_t *in, int32_t *out, int64_t n_max, int32_t *bsum,
                            cudaStream_t s);
 void nb_radix_sort_raw(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uint32_t *idx_alt,
@@ -138,6 +164,7 @@ void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
 void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g);
 
 // nb_walk.cu
+int nb_walk_warps(nb_ctx *c);
 void nb_launch_walk(nb_ctx *c);
 
 // nb_force.cu
@@ -153,6 +180,13 @@ void nb_launch_drift(nb_ctx *c, double *pos, const double *vel, int64_t n, doubl
 __device__ __forceinline__ long long nb_atomic_add(long long *p, long long v)
 {
     return (long long)atomicAdd((unsigned long long *)p, (unsigned long long)v);
+}
+
+// group-relative FP32 coordinate of a value carried as two floats (hi, lo):
+// fl32(fl32(hi - c) + lo)
+__device__ __forceinline__ float nb_rel(float hi, float lo, float c)
+{
+    return __fadd_rn(__fsub_rn(hi, c), lo);
 }
 
 static inline int nb_grid(int64_t n, int block, int cap = 1 << 20)

@@ -15,7 +15,6 @@
 // is written with explicit round-to-nearest intrinsics, never contracted.
 #include "nb_internal.cuh"
 
-#define NB_IBLOCK 64
 
 // ------------------------------------------------------------ bbox, root
 __global__ void __launch_bounds__(256)
@@ -58,27 +57,45 @@ k_bbox(const double *__restrict__ pos, int64_t n, double *__restrict__ part,
 }
 
 // Root cube: centre = bbox centre, side = max extent * (1 + 2^-20), 1 when
-// every particle coincides; corner = centre - side/2.
-__global__ void k_root(const double *__restrict__ part, int nblk, double *__restrict__ root)
+// every particle coincides; corner = centre - side/2; grid scale 2^21 / side.
+__global__ void __launch_bounds__(256)
+k_root(const double *__restrict__ part, int nblk, double *__restrict__ root)
 {
-    if (threadIdx.x != 0) return;
-    double lo[3], hi[3];
-    for (int k = 0; k < 3; k++) { lo[k] = part[k]; hi[k] = part[3 + k]; }
-    for (int b = 1; b < nblk; b++)
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
         for (int k = 0; k < 3; k++) {
             lo[k] = fmin(lo[k], part[6 * b + k]);
             hi[k] = fmax(hi[k], part[6 * b + 3 + k]);
         }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            lo[k] = fmin(lo[k], __shfl_down_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_down_sync(0xffffffffu, hi[k], o));
+        }
+    __shared__ double s[8][6];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; k++) { s[w][k] = lo[k]; s[w][3 + k] = hi[k]; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int ww = 1; ww < (int)(blockDim.x >> 5); ww++)
+        for (int k = 0; k < 3; k++) {
+            s[0][k] = fmin(s[0][k], s[ww][k]);
+            s[0][3 + k] = fmax(s[0][3 + k], s[ww][3 + k]);
+        }
     double ext = 0.0;
     for (int k = 0; k < 3; k++) {
-        root[k] = __dmul_rn(0.5, __dadd_rn(lo[k], hi[k]));
-        const double e = __dsub_rn(hi[k], lo[k]);
+        root[k] = __dmul_rn(0.5, __dadd_rn(s[0][k], s[0][3 + k]));
+        const double e = __dsub_rn(s[0][3 + k], s[0][k]);
         if (e > ext) ext = e;
     }
     double L = __dmul_rn(ext, 1.0 + 0x1p-20);
     if (!(L > 0.0)) L = 1.0;
     root[3] = L;
     for (int k = 0; k < 3; k++) root[4 + k] = __dsub_rn(root[k], __dmul_rn(0.5, L));
+    root[7] = __ddiv_rn(2097152.0, L);
 }
 
 // ------------------------------------------------------------ Morton keys
@@ -104,9 +121,9 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x)
     return (uint32_t)x;
 }
 
-__device__ __forceinline__ uint32_t grid_coord(double x, double corner, double L)
+__device__ __forceinline__ uint32_t grid_coord(double x, double corner, double scale)
 {
-    const double f = floor(__dmul_rn(__ddiv_rn(__dsub_rn(x, corner), L), 2097152.0));
+    const double f = floor(__dmul_rn(__dsub_rn(x, corner), scale));
     if (f < 0.0) return 0u;
     if (f > 2097151.0) return 2097151u;
     return (uint32_t)f;
@@ -118,10 +135,10 @@ k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ roo
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double L = root[3];
-    const uint32_t qx = grid_coord(pos[3 * i], root[4], L);
-    const uint32_t qy = grid_coord(pos[3 * i + 1], root[5], L);
-    const uint32_t qz = grid_coord(pos[3 * i + 2], root[6], L);
+    const double sc = root[7];
+    const uint32_t qx = grid_coord(pos[3 * i], root[4], sc);
+    const uint32_t qy = grid_coord(pos[3 * i + 1], root[5], sc);
+    const uint32_t qz = grid_coord(pos[3 * i + 2], root[6], sc);
     key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     idx[i] = (uint32_t)i;
 }
@@ -171,13 +188,10 @@ k_levels(const uint64_t *__restrict__ key, int64_t n, int8_t *__restrict__ clev,
 
 __global__ void __launch_bounds__(256)
 k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ clev,
-        const int32_t *__restrict__ cstart, const float4 *__restrict__ p_hi,
-        const float4 *__restrict__ p_lo, const double *__restrict__ x64,
-        float4 *__restrict__ node_a, float4 *__restrict__ node_b, int4 *__restrict__ node_c,
+        const int32_t *__restrict__ cstart, int4 *__restrict__ node_c,
         int32_t *__restrict__ n_level, int32_t *__restrict__ n_first,
         int32_t *__restrict__ n_count, int32_t *__restrict__ n_parent,
-        int32_t *__restrict__ n_nchild, int32_t *__restrict__ n_arrive,
-        double *__restrict__ n_mass, double *__restrict__ n_mx, double *__restrict__ n_com,
+        int32_t *__restrict__ n_nchild, int8_t *__restrict__ n_depth,
         long long *__restrict__ cnt)
 {
     const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -191,23 +205,13 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
     const int32_t base = cstart[a] + (int32_t)a;
     const int32_t leaf = base + k;
 
-    // particle leaf
-    const float4 h = p_hi[a];
-    node_a[leaf] = h;
-    node_b[leaf] = p_lo[a];
+    // particle leaf: one below the deepest cell that holds it
     node_c[leaf] = make_int4(leaf + 1, 0, 0, 1);
     n_level[leaf] = -1;
     n_first[leaf] = (int32_t)a;
     n_count[leaf] = 1;
     n_nchild[leaf] = 0;
-    const double m = (double)h.w;
-    n_mass[leaf] = m;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const double x = x64[3 * a + d];
-        n_com[3 * (int64_t)leaf + d] = x;
-        n_mx[3 * (int64_t)leaf + d] = __dmul_rn(m, x);
-    }
+    n_depth[leaf] = (int8_t)((ca > cp ? ca : cp) + 1);
     if (k > 0) n_parent[leaf] = leaf - 1;
     else if (leaf == 0) n_parent[leaf] = -1;
 
@@ -235,7 +239,7 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
         n_level[id] = lev;
         n_first[id] = (int32_t)a;
         n_count[id] = (int32_t)(b - a + 1);
-        n_arrive[id] = 0;
+        n_depth[id] = (int8_t)lev;
         if (lev > cp + 1) n_parent[id] = id - 1;
         else if (id == 0) n_parent[id] = -1;
         if (lev > maxlev) maxlev = lev;
@@ -265,67 +269,172 @@ k_parents(const int4 *__restrict__ node_c, const long long *__restrict__ cnt,
     }
 }
 
-// FP64 moments bottom-up: the last child to finish folds its parent's
-// children in octant order (mass, sum of m x), then COM = sum(m x) / M,
+// ------------------------------------------------------------ level order
+// Stable counting sort of the preorder node ids by depth: per-tile depth
+// histograms, one scan of the depth-major table, then a stable scatter with
+// warp match/rank (the same scheme as the radix sort's scatter).
+#define DS_T 256
+#define DS_I 16
+#define DS_TILE (DS_T * DS_I)
+
+__global__ void __launch_bounds__(DS_T)
+k_depth_hist(const int8_t *__restrict__ depth, const long long *__restrict__ cnt,
+             uint32_t *__restrict__ hist, int ntiles)
+{
+    __shared__ uint32_t h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t total = cnt[CNT_NODES];
+    const int64_t base = (int64_t)blockIdx.x * DS_TILE;
+    for (int k = 0; k < DS_I; k++) {
+        const int64_t i = base + k * DS_T + threadIdx.x;
+        if (i < total) atomicAdd(&h[depth[i]], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < NB_DEPTHS) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(DS_T)
+k_depth_scatter(const int8_t *__restrict__ depth, const long long *__restrict__ cnt,
+                const uint32_t *__restrict__ offs, int ntiles, int32_t *__restrict__ bfs2pid,
+                int32_t *__restrict__ pid2bfs)
+{
+    __shared__ uint32_t whist[DS_T / NB_WARP][32];
+    __shared__ uint32_t boff[32];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    for (int i = t; i < (DS_T / NB_WARP) * 32; i += DS_T) (&whist[0][0])[i] = 0u;
+    if (t < NB_DEPTHS) boff[t] = offs[(int64_t)t * ntiles + blockIdx.x];
+    __syncthreads();
+    const int64_t total = cnt[CNT_NODES];
+    const int64_t base = (int64_t)blockIdx.x * DS_TILE + (int64_t)w * (DS_TILE / (DS_T / NB_WARP));
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t rnk[DS_I];
+#pragma unroll
+    for (int r = 0; r < DS_I; r++) {
+        const int64_t i = base + r * NB_WARP + lane;
+        const bool ok = i < total;
+        const int d = ok ? (int)depth[i] : 32 + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned before = __popc(peers & lt);
+        const uint32_t pre = ok ? whist[w][d] : 0u;
+        __syncwarp();
+        if (ok && before == 0) whist[w][d] = pre + __popc(peers);
+        __syncwarp();
+        rnk[r] = pre + before;
+    }
+    __syncthreads();
+    if (t < 32) {
+        uint32_t run = 0;
+        for (int ww = 0; ww < DS_T / NB_WARP; ww++) {
+            const uint32_t v = whist[ww][t];
+            whist[ww][t] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < DS_I; r++) {
+        const int64_t i = base + r * NB_WARP + lane;
+        if (i < total) {
+            const int d = depth[i];
+            const uint32_t pos = boff[d] + whist[w][d] + rnk[r];
+            bfs2pid[pos] = (int32_t)i;
+            pid2bfs[i] = (int32_t)pos;
+        }
+    }
+}
+
+// level_start[d] = first level-order index of depth d (d = 0 .. NB_DEPTHS)
+__global__ void k_level_start(const uint32_t *__restrict__ hist, int ntiles,
+                              int32_t *__restrict__ level_start)
+{
+    const int d = threadIdx.x;
+    if (d <= NB_DEPTHS) level_start[d] = (int32_t)hist[(int64_t)d * ntiles];
+}
+
+// level-order records: particle leaves get their position and FP64 moments,
+// cells their topology (moments follow level by level)
+__global__ void __launch_bounds__(256)
+k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ pid2bfs,
+              const int4 *__restrict__ node_c, const int32_t *__restrict__ n_first,
+              const int32_t *__restrict__ n_nchild, const float4 *__restrict__ p_hi,
+              const float4 *__restrict__ p_lo, const double *__restrict__ x64,
+              const long long *__restrict__ cnt, float4 *__restrict__ w_a,
+              float4 *__restrict__ w_d, int4 *__restrict__ w_b, float2 *__restrict__ w_c,
+              double *__restrict__ b_mass, double *__restrict__ b_mx, double *__restrict__ b_com)
+{
+    const int32_t total = (int32_t)cnt[CNT_NODES];
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < total;
+         b += gridDim.x * blockDim.x) {
+        const int32_t u = bfs2pid[b];
+        const int4 c = node_c[u];
+        if (c.w) {
+            const int32_t slot = n_first[u];
+            const float4 h = p_hi[slot];
+            w_a[b] = h;
+            w_d[b] = p_lo[slot];
+            w_b[b] = make_int4(u, c.x, -1, 0);
+            w_c[b] = make_float2(0.0f, 0.0f);
+            const double m = (double)h.w;
+            b_mass[b] = m;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const double x = x64[3 * (int64_t)slot + d];
+                b_com[3 * (int64_t)b + d] = x;
+                b_mx[3 * (int64_t)b + d] = __dmul_rn(m, x);
+            }
+        } else {
+            w_b[b] = make_int4(u, c.x, pid2bfs[u + 1], n_nchild[u]);
+        }
+    }
+}
+
+// FP64 moments of the cells at one depth (= level): fold the children, which
+// are contiguous one level down and in octant order, then COM = sum(m x) / M,
 // l = L / 2^level, s = |COM - geometric centre|.
 __global__ void __launch_bounds__(256)
-k_moments(int64_t n, const uint64_t *__restrict__ key, const int32_t *__restrict__ cstart,
-          const double *__restrict__ root, const int32_t *__restrict__ n_parent,
-          const int32_t *__restrict__ n_nchild, const int32_t *__restrict__ n_level,
-          const int32_t *__restrict__ n_first, int32_t *__restrict__ n_arrive,
-          double *__restrict__ n_mass, double *__restrict__ n_mx, double *__restrict__ n_com,
-          float4 *__restrict__ node_a, float4 *__restrict__ node_b, int4 *__restrict__ node_c)
+k_moments_level(int depth, const int32_t *__restrict__ level_start,
+                const uint64_t *__restrict__ key, const int32_t *__restrict__ n_first,
+                const double *__restrict__ root, const int4 *__restrict__ w_b,
+                float4 *__restrict__ w_a, float4 *__restrict__ w_d, float2 *__restrict__ w_c,
+                double *__restrict__ b_mass, double *__restrict__ b_mx,
+                double *__restrict__ b_com)
 {
-    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    int32_t u = cstart[a + 1] + (int32_t)a;   // particle leaf
-    __threadfence();
-    int32_t p = n_parent[u];
+    const int32_t lo_b = level_start[depth], hi_b = level_start[depth + 1];
     const double L = root[3];
-    while (p >= 0) {
-        const int old = atomicAdd(&n_arrive[p], 1);
-        if (old != n_nchild[p] - 1) return;
-        __threadfence();
-        const int32_t end = node_c[p].x;
+    const double lc = ldexp(L, -depth);
+    for (int32_t b = lo_b + blockIdx.x * blockDim.x + threadIdx.x; b < hi_b;
+         b += gridDim.x * blockDim.x) {
+        const int4 wb = w_b[b];
+        if (wb.z < 0) continue;
         double M = 0.0, mx[3] = {0.0, 0.0, 0.0};
-        for (int32_t ch = p + 1; ch < end;) {
-            M = __dadd_rn(M, __ldcg(&n_mass[ch]));
+        for (int32_t k = 0; k < wb.w; k++) {
+            const int64_t ch = wb.z + k;
+            M = __dadd_rn(M, b_mass[ch]);
 #pragma unroll
-            for (int d = 0; d < 3; d++)
-                mx[d] = __dadd_rn(mx[d], __ldcg(&n_mx[3 * (int64_t)ch + d]));
-            const int32_t nx = node_c[ch].x;
-            ch = nx > ch ? nx : end;
+            for (int d = 0; d < 3; d++) mx[d] = __dadd_rn(mx[d], b_mx[3 * ch + d]);
         }
-        const int lev = n_level[p];
-        const double lc = ldexp(L, -lev);
-        const uint64_t kf = key[n_first[p]];
-        const int sh = 3 * (NB_LEVELS - lev);
-        const uint32_t cq[3] = {compact3(kf >> 2) >> (NB_LEVELS - lev),
-                                compact3(kf >> 1) >> (NB_LEVELS - lev),
-                                compact3(kf) >> (NB_LEVELS - lev)};
-        (void)sh;
-        double com[3], d2 = 0.0;
+        const uint64_t kf = key[n_first[wb.x]];
+        const uint32_t cq[3] = {compact3(kf >> 2) >> (NB_LEVELS - depth),
+                                compact3(kf >> 1) >> (NB_LEVELS - depth),
+                                compact3(kf) >> (NB_LEVELS - depth)};
+        double d2 = 0.0;
         float hi[3], lo[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const double g = __dadd_rn(root[4 + d], __dmul_rn(__dadd_rn((double)cq[d], 0.5), lc));
-            com[d] = M > 0.0 ? __ddiv_rn(mx[d], M) : g;
-            const double dd = __dsub_rn(com[d], g);
+            const double com = M > 0.0 ? __ddiv_rn(mx[d], M) : g;
+            const double dd = __dsub_rn(com, g);
             d2 = __dadd_rn(d2, __dmul_rn(dd, dd));
-            hi[d] = __double2float_rn(com[d]);
-            lo[d] = __double2float_rn(__dsub_rn(com[d], (double)hi[d]));
-            n_mx[3 * (int64_t)p + d] = mx[d];
-            n_com[3 * (int64_t)p + d] = com[d];
+            hi[d] = __double2float_rn(com);
+            lo[d] = __double2float_rn(__dsub_rn(com, (double)hi[d]));
+            b_mx[3 * (int64_t)b + d] = mx[d];
+            b_com[3 * (int64_t)b + d] = com;
         }
-        n_mass[p] = M;
-        const float lf = __double2float_rn(lc);
-        const float sf = __double2float_rn(__dsqrt_rn(d2));
-        node_a[p] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(M));
-        node_b[p] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-        node_c[p] = make_int4(end, __float_as_int(lf), __float_as_int(sf), 0);
-        __threadfence();
-        u = p;
-        p = n_parent[u];
+        b_mass[b] = M;
+        w_a[b] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(M));
+        w_d[b] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        w_c[b] = make_float2(__double2float_rn(lc), __double2float_rn(__dsqrt_rn(d2)));
     }
 }
 
@@ -335,7 +444,7 @@ void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_PP_CUM, s);
     k_bbox<<<c->bbox_blocks, 256, 0, s>>>(pos, n, c->bbox_part, c->err);
     c->launches++;
-    k_root<<<1, 32, 0, s>>>(c->bbox_part, c->bbox_blocks, c->root);
+    k_root<<<1, 256, 0, s>>>(c->bbox_part, c->bbox_blocks, c->root);
     c->launches++;
     k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, c->keys, c->idx);
     c->launches++;
@@ -346,18 +455,35 @@ void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     k_levels<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, n, c->clev, c->ccount);
     c->launches++;
     nb_exclusive_scan(c, c->ccount, c->cstart, n, nullptr, &c->cnt[CNT_CELLS]);
-    k_cells<<<nb_grid(n, 256), 256, 0, s>>>(
-        c->keys, n, c->clev, c->cstart, c->p_hi, c->p_lo, c->p_x64, c->node_a, c->node_b,
-        c->node_c, c->n_level, c->n_first, c->n_count, c->n_parent, c->n_nchild,
-        c->n_arrive, c->n_mass, c->n_mx, c->n_com, c->cnt);
+    k_cells<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, n, c->clev, c->cstart, c->node_c,
+                                            c->n_level, c->n_first, c->n_count, c->n_parent,
+                                            c->n_nchild, c->n_depth, c->cnt);
     c->launches++;
-    k_parents<<<nb_grid(c->max_nodes, 256, c->num_sms * 16), 256, 0, s>>>(
-        c->node_c, c->cnt, c->n_parent, c->n_nchild);
+    const int gcap = c->num_sms * 16;
+    k_parents<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(c->node_c, c->cnt, c->n_parent,
+                                                               c->n_nchild);
     c->launches++;
-    k_moments<<<nb_grid(n, 256), 256, 0, s>>>(
-        n, c->keys, c->cstart, c->root, c->n_parent, c->n_nchild, c->n_level, c->n_first,
-        c->n_arrive, c->n_mass, c->n_mx, c->n_com, c->node_a, c->node_b, c->node_c);
+    // level order
+    const int nt = (int)c->dtiles;
+    k_depth_hist<<<nt, DS_T, 0, s>>>(c->n_depth, c->cnt, c->dhist, nt);
     c->launches++;
+    nb_exclusive_scan(c, (const int32_t *)c->dhist, (int32_t *)c->dhist,
+                      (int64_t)NB_DEPTHS * nt, nullptr, nullptr);
+    k_depth_scatter<<<nt, DS_T, 0, s>>>(c->n_depth, c->cnt, c->dhist, nt, c->bfs2pid, c->pid2bfs);
+    c->launches++;
+    k_level_start<<<1, 32, 0, s>>>(c->dhist, nt, c->level_start);
+    c->launches++;
+    k_bfs_records<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
+        c->bfs2pid, c->pid2bfs, c->node_c, c->n_first, c->n_nchild, c->p_hi, c->p_lo, c->p_x64,
+        c->cnt, c->w_a, c->w_d, c->w_b, c->w_c, c->b_mass, c->b_mx, c->b_com);
+    c->launches++;
+    const int gl = c->num_sms * 8;
+    for (int d = NB_LEVELS; d >= 0; d--) {
+        k_moments_level<<<gl, 256, 0, s>>>(d, c->level_start, c->keys, c->n_first, c->root,
+                                           c->w_b, c->w_a, c->w_d, c->w_c, c->b_mass, c->b_mx,
+                                           c->b_com);
+        c->launches++;
+    }
 }
 
 // ------------------------------------------------------------ groups
@@ -432,7 +558,8 @@ k_items(const int32_t *__restrict__ item_off, const int32_t *__restrict__ gcount
         const int32_t o = item_off[g], m = gcount[g];
         for (int32_t i0 = 0, k = 0; i0 < m; i0 += NB_IBLOCK, k++) {
             items[2 * (int64_t)(o + k)] = g;
-            items[2 * (int64_t)(o + k) + 1] = i0;
+            // bit 30: the item's targets fit one 32-wide row
+            items[2 * (int64_t)(o + k) + 1] = i0 | (m - i0 <= NB_WARP ? (1 << 30) : 0);
         }
     }
 }
@@ -465,6 +592,6 @@ void nb_launch_keys_raw(const double *pos, int64_t n, double *part, int nblk, do
                         uint64_t *keys, uint32_t *idx, unsigned *err, cudaStream_t s)
 {
     k_bbox<<<nblk, 256, 0, s>>>(pos, n, part, err);
-    k_root<<<1, 32, 0, s>>>(part, nblk, root);
+    k_root<<<1, 256, 0, s>>>(part, nblk, root);
     k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, root, keys, idx);
 }

@@ -1,23 +1,31 @@
-// nb_walk.cu -- the group tree walk (Fig. "treewalk_iterative" in group form).
+// nb_walk.cu -- the group tree walk: the iterative walk of Fig.
+// "treewalk_iterative" in group form, done breadth-first by one warp.
 //
-// One warp walks one group.  Nodes are stored in depth-first preorder, so the
-// iterative walk only ever moves forward: to id + 1 when a cell is opened
-// ("more"), to next(id) when a particle or an accepted cell is taken.  The
-// warp evaluates the 32 consecutive nodes cur .. cur+31 at once (coalesced
-// 32-byte records, opening tests in parallel), then follows the chain of
-// successors from cur inside that window with register shuffles to find
-// which of the 32 were actually visited, appends the visited particles and
-// accepted cells to the group's list in walk order, and continues at the
-// first successor beyond the window.  Each window advances cur by >= 1, so
-// the loop ends after at most (number of nodes) windows; a successor that
-// does not advance raises NB_EF_WALK instead of looping.
+// Nodes are stored in level order, so the children of a cell are one
+// contiguous run one level down.  The warp keeps the current level's
+// frontier (node indices) in a queue in global memory and takes it 32 nodes
+// at a time: each lane loads one node's record (coalesced, L2-resident) and
+// applies the opening test.  Particles and accepted cells are appended to
+// the group's list (ballot + popc compaction); opened cells append their
+// children to the next level's queue (warp prefix sum over the child
+// counts).  Every lane of every step holds a node the walk visits, and the
+// loop ends after at most one pass per tree level.
 //
-// List records: node id (int32) and the FP32 source the force kernel reads:
-// position relative to the group's box centre, computed from the two-float
-// split of the FP64 centre of mass as (hi - c) + lo, and the mass.
+// The group's own node is skipped: its particles are exactly the group's
+// members, which the force kernel sums directly (with j != i by index).  A
+// cell that contains the group (preorder id <= group id < preorder next) is
+// always opened.  The list therefore holds, in breadth-first order, the
+// same entries as the depth-first list of the paper's walk minus the group's
+// own particles.
+//
+// List records: preorder node id (int32) and the FP32 source the force
+// kernel reads: position relative to the group's box centre from the
+// two-float split of the FP64 centre of mass, fl32(fl32(hi - c) + lo), and
+// the FP32 mass.
 #include "nb_internal.cuh"
 
 #define WALK_T 256
+#define WALK_WARPS (WALK_T / NB_WARP)
 
 // Eq. (mac) for a group: squared FP32 distance from the cell's centre of
 // mass to the group box against (l / theta + s)^2, every operation rounded
@@ -37,21 +45,23 @@ __device__ __forceinline__ bool far_enough(const float4 &a, float l, float s,
 }
 
 __global__ void __launch_bounds__(WALK_T)
-k_walk(const float4 *__restrict__ node_a, const float4 *__restrict__ node_b,
-       const int4 *__restrict__ node_c, const int32_t *__restrict__ gnode,
+k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
+       const int4 *__restrict__ w_b, const float2 *__restrict__ w_c,
+       const int32_t *__restrict__ pid2bfs, const int32_t *__restrict__ gnode,
        const int32_t *__restrict__ gcount, const float4 *__restrict__ gbox,
-       long long *__restrict__ cnt, int32_t *__restrict__ glen,
-       int32_t *__restrict__ gself, int32_t *__restrict__ gcells,
-       int32_t *__restrict__ list_id, float4 *__restrict__ list_xm, int64_t cap,
-       int64_t alloc, unsigned *__restrict__ err)
+       long long *__restrict__ cnt, int32_t *__restrict__ glen, int32_t *__restrict__ gcells,
+       int32_t *__restrict__ list_id, float4 *__restrict__ list_xm, int64_t cap, int64_t alloc,
+       int32_t *__restrict__ wq, int64_t wq_cap, unsigned *__restrict__ err)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int32_t total = (int32_t)cnt[CNT_NODES];
+    const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + (threadIdx.x >> 5);
+    int32_t *const qa = wq + gw * 2 * wq_cap;
+    int32_t *const qb = qa + wq_cap;
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     long long pp = 0, pc = 0, tot = 0;
-    int32_t mx = 0;
+    int32_t mx = 0, qmax = 0;
     unsigned bad = 0;
     for (;;) {
         int g = 0;
@@ -62,77 +72,86 @@ k_walk(const float4 *__restrict__ node_a, const float4 *__restrict__ node_b,
         const float4 bhi = gbox[3 * (int64_t)g + 1];
         const float4 bc = gbox[3 * (int64_t)g + 2];
         const float invth = bc.w;
-        const int32_t gn = gnode[g];
-        const int32_t gend = node_c[gn].x;
+        const int32_t gpid = gnode[g];
+        const int32_t gb = pid2bfs[gpid];
         const int64_t base = (int64_t)g * cap;
         const int64_t room = alloc - base < cap ? (alloc - base > 0 ? alloc - base : 0) : cap;
-        int32_t len = 0, ncell = 0, self_off = -1;
-        int32_t cur = 0;
-        int32_t guard = 0;
-        while (cur < total) {
-            const int32_t u = cur + lane;
-            bool emit = false, cell_emit = false, own = false;
-            int32_t succ = total;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (u < total) {
-                const int4 c = node_c[u];
-                a = node_a[u];
-                if (c.w) {
-                    emit = true;
-                } else {
-                    const bool holds = (u <= gn) && (gn < c.x);
-                    emit = !holds && far_enough(a, __int_as_float(c.y), __int_as_float(c.z),
-                                                blo, bhi, invth);
-                    cell_emit = emit;
+        int32_t len = 0, ncell = 0;
+        int32_t *qin = qa, *qout = qb;
+        if (lane == 0) qin[0] = 0;   // the root
+        __syncwarp();
+        int32_t na = 1;
+        int depth_guard = 0;
+        while (na > 0) {
+            int32_t nb = 0;
+            for (int32_t i0 = 0; i0 < na; i0 += NB_WARP) {
+                const int32_t i = i0 + lane;
+                bool emit = false, cell_emit = false, open = false;
+                int32_t b = 0, pid = 0, fc = 0, nch = 0;
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < na) {
+                    b = qin[i];
+                    const int4 wb = w_b[b];
+                    a = w_a[b];
+                    pid = wb.x;
+                    fc = wb.z;
+                    if (b != gb) {
+                        if (fc < 0) {
+                            emit = true;
+                        } else {
+                            const bool holds = (wb.x <= gpid) && (gpid < wb.y);
+                            const float2 wc = w_c[b];
+                            if (!holds && far_enough(a, wc.x, wc.y, blo, bhi, invth)) {
+                                emit = true;
+                                cell_emit = true;
+                            } else {
+                                open = true;
+                                nch = wb.w;
+                            }
+                        }
+                    }
                 }
-                succ = emit ? c.x : u + 1;
-                own = (u >= gn) && (u < gend);
-            }
-            // chain of visited nodes inside the window, starting at cur
-            unsigned vis = 0u;
-            int l = 0;
-            int32_t nxt = total;
-            for (;;) {
-                vis |= 1u << l;
-                const int32_t sl = __shfl_sync(FULL, succ, l);
-                const int32_t off = sl - cur;
-                if (sl >= total || off >= 32) { nxt = sl; break; }
-                if (off <= l) { bad |= NB_EF_WALK; nxt = total; break; }
-                l = off;
-            }
-            const unsigned em = __ballot_sync(FULL, emit) & vis;
-            const unsigned cm = __ballot_sync(FULL, cell_emit) & vis;
-            if ((em >> lane) & 1u) {
-                const int32_t pos = len + __popc(em & lt);
-                if (pos < room) {
-                    const float4 b = node_b[u];
-                    list_id[base + pos] = u;
-                    list_xm[base + pos] =
-                        make_float4(__fadd_rn(__fsub_rn(a.x, bc.x), b.x),
-                                    __fadd_rn(__fsub_rn(a.y, bc.y), b.y),
-                                    __fadd_rn(__fsub_rn(a.z, bc.z), b.z), a.w);
+                const unsigned em = __ballot_sync(FULL, emit);
+                if (emit) {
+                    const int32_t pos = len + __popc(em & lt);
+                    if (pos < room) {
+                        const float4 d = w_d[b];
+                        list_id[base + pos] = pid;
+                        list_xm[base + pos] = make_float4(nb_rel(a.x, d.x, bc.x), nb_rel(a.y, d.y, bc.y),
+                                                          nb_rel(a.z, d.z, bc.z), a.w);
+                    }
                 }
+                len += __popc(em);
+                ncell += __popc(__ballot_sync(FULL, cell_emit));
+                // children of opened cells go to the next level's queue
+                int32_t incl = nch;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int32_t start = nb + incl - nch;
+                if (open)
+                    for (int32_t k = 0; k < nch; k++)
+                        if (start + k < wq_cap) qout[start + k] = fc + k;
+                nb += __shfl_sync(FULL, incl, 31);
             }
-            if (self_off < 0) {
-                const unsigned sm = em & __ballot_sync(FULL, own);
-                if (sm) self_off = len + __popc(em & ((1u << (__ffs(sm) - 1)) - 1u));
-            }
-            len += __popc(em);
-            ncell += __popc(cm);
-            cur = nxt;
-            if (++guard > total) { bad |= NB_EF_WALK; break; }
+            if (nb > qmax) qmax = nb;
+            if (nb > wq_cap) { bad |= NB_EF_QUEUE; break; }
+            __syncwarp();
+            int32_t *t = qin; qin = qout; qout = t;
+            na = nb;
+            if (++depth_guard > NB_DEPTHS + 1) { bad |= NB_EF_WALK; break; }
         }
         if (lane == 0) {
             glen[g] = len;
-            gself[g] = self_off;
             gcells[g] = ncell;
             const long long m = gcount[g];
-            pp += m * (long long)(len - ncell - 1);
+            pp += m * (long long)(len - ncell) + m * (m - 1);
             pc += m * (long long)ncell;
             tot += len;
             if (len > mx) mx = len;
             if (len > room) bad |= NB_EF_CAPACITY;
-            if (self_off < 0) bad |= NB_EF_WALK;
         }
     }
     if (lane == 0) {
@@ -142,19 +161,29 @@ k_walk(const float4 *__restrict__ node_a, const float4 *__restrict__ node_b,
         nb_atomic_add(&cnt[CNT_PC_CUM], pc);
         nb_atomic_add(&cnt[CNT_LIST_TOT], tot);
         atomicMax(&cnt[CNT_LIST_MAX], (long long)mx);
+        atomicMax(&cnt[CNT_QMAX], (long long)qmax);
         if (bad) atomicOr(err, bad);
     }
+}
+
+// warps of one walk launch (the frontier queues are sized for them)
+int nb_walk_warps(nb_ctx *c)
+{
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_walk, WALK_T, 0);
+    if (blocks < 1) blocks = 1;
+    return c->num_sms * blocks * WALK_WARPS;
 }
 
 void nb_launch_walk(nb_ctx *c)
 {
     cudaMemsetAsync(&c->cnt[CNT_LIST_TOT], 0, sizeof(long long) * 5, c->stream);
     static_assert(CNT_LIST_TOT + 4 == CNT_WALK_Q, "counter layout");
-    int blocks = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_walk, WALK_T, 0);
-    if (blocks < 1) blocks = 1;
-    k_walk<<<c->num_sms * blocks, WALK_T, 0, c->stream>>>(
-        c->node_a, c->node_b, c->node_c, c->gnode, c->gcount, c->gbox, c->cnt, c->glen,
-        c->gself, c->gcells, c->list_id, c->list_xm, c->list_cap, c->list_alloc, c->err);
+    cudaMemsetAsync(&c->cnt[CNT_QMAX], 0, sizeof(long long), c->stream);
+    const int blocks = c->walk_warps / WALK_WARPS;
+    k_walk<<<blocks, WALK_T, 0, c->stream>>>(
+        c->w_a, c->w_d, c->w_b, c->w_c, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
+        c->glen, c->gcells, c->list_id, c->list_xm, c->list_cap, c->list_alloc, c->wq,
+        c->wq_cap, c->err);
     c->launches++;
 }

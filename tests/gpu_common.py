@@ -40,6 +40,26 @@ def oracle_tree_arrays(T):
         s=np.where(cell, e["s"], 0), is_cell=e["is_cell"])
 
 
+def oracle_external_lists(T, n_crit, theta):
+    """The oracle's depth-first lists with each group's own particles removed
+    (the CUDA walk lists sources outside the group; the force kernel sums the
+    group's members directly).  Returns (gnode, box, offsets, entries, own)
+    where own[k] is the number of own particles found in group k's list."""
+    gnode, box, off, ent = T.all_lists(n_crit, theta)
+    e = T.export()
+    leaf_of_slot = np.flatnonzero(e["is_cell"] == 0)
+    out, offs, own = [], [0], []
+    for k in range(len(gnode)):
+        lst = ent[off[k]:off[k + 1]]
+        f, c = e["first"][gnode[k]], e["count"][gnode[k]]
+        mine = np.isin(lst, leaf_of_slot[f:f + c])
+        own.append(int(mine.sum()))
+        out.append(lst[~mine])
+        offs.append(offs[-1] + int((~mine).sum()))
+    ent2 = np.concatenate(out) if out else np.zeros(0, np.int64)
+    return gnode, box, np.array(offs, np.int64), ent2, np.array(own)
+
+
 def rel_err(a, ref):
     """Per-particle |a - ref| / |ref| (rows of ref with zero norm use 1)."""
     d = np.linalg.norm(np.asarray(a, np.float64) - ref, axis=1)

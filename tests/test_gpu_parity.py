@@ -1,21 +1,29 @@
 """CUDA path vs the CPU oracle on the same seeded inputs.
 
 Bit-exact: sorted order, tree topology, FP64 moments, l, s, groups, group
-boxes and every interaction list (node ids, in depth-first order).
-Tolerance: accelerations and potentials against the oracle's FP64 sums over
-the same lists, for every particle.  The bar is 1e-5 relative for plain FP32
-sums and 1e-6 for compensated (or FP64-accumulated) sums.  A rounded sum's
-error scales with the sum of its terms' magnitudes, A_i = sum_j |a_ij|, not
-with |a_i| (which cancellation can make arbitrarily small), so the bound is
-|a_i(gpu) - a_i(oracle)| <= tol * A_i for every i; in addition the median of
-|a_i(gpu) - a_i(oracle)| / |a_i(oracle)| must be a tenth of tol, and every
-potential (a sum of same-signed terms) must be within tol relative.
+boxes and every interaction list.  The CUDA walk is breadth-first and leaves
+the group's own particles to the force kernel, so each GPU list, sorted, must
+equal the oracle's depth-first list (ascending node ids) minus the group's
+own particles, which must all be in the oracle's list.
+
+Forces, for every particle:
+* arithmetic parity against the oracle's FP64 sum over the same lists and the
+  same group-relative FP32 coordinates and FP32 masses (oracle coords32
+  mode): the bar is 1e-5 relative for plain FP32 sums and 1e-6 for
+  compensated (or FP64-accumulated) sums.  A rounded sum's error scales with
+  the sum of its terms' magnitudes, A_i = sum_j |a_ij|, not with |a_i|
+  (which cancellation can make arbitrarily small), so the bound is
+  |a_i(gpu) - a_i(oracle)| <= tol * A_i; every potential (a sum of
+  same-signed terms) must be within tol relative;
+* against the oracle's FP64 sum over the exact FP64 positions, which adds
+  the FP32 coordinate representation: the median of |da|/|a| is at most a
+  tenth of tol and the potential within 10 tol.
 """
 import numpy as np
 import pytest
 
 import nbsynth
-from tests.gpu_common import gpu_run, oracle_tree_arrays, rel_err
+from tests.gpu_common import gpu_run, oracle_external_lists, oracle_tree_arrays, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -59,27 +67,29 @@ def assert_tree_equal(g, T):
 
 
 def assert_lists_equal(g, T, theta, n_crit):
-    gnode, box, off, ent = T.all_lists(n_crit, theta)
+    gnode, box, off, ent, own = oracle_external_lists(T, n_crit, theta)
     gg = g["groups"]
     assert np.array_equal(gg["gnode"], gnode)
     assert np.array_equal(gg["box"], box)
     e = T.export()
     assert np.array_equal(gg["gfirst"], e["first"][gnode])
     assert np.array_equal(gg["gcount"], e["count"][gnode])
-    assert np.all(gg["invtheta"] == np.float32(1.0 / theta) if theta > 0 else np.isinf(gg["invtheta"]))
+    assert np.array_equal(own, e["count"][gnode])      # own particles all in the list
+    if theta > 0:
+        assert np.all(gg["invtheta"] == np.float32(1.0 / theta))
+    else:
+        assert np.all(np.isinf(gg["invtheta"]))
     L = g["lists"]
     assert np.array_equal(L["offsets"], off)
-    assert np.array_equal(L["entries"], ent)
-    # the group's own particles start at self_off
-    leaf_of_slot = np.flatnonzero(e["is_cell"] == 0)
+    xm = L["xm"]
     for k in range(len(gnode)):
-        lst = ent[off[k]:off[k + 1]]
-        first_leaf = leaf_of_slot[e["first"][gnode[k]]]
-        assert L["self_off"][k] == np.flatnonzero(lst == first_leaf)[0]
+        a, b = off[k], off[k + 1]
+        order = np.argsort(L["entries"][a:b], kind="stable")
+        assert np.array_equal(L["entries"][a:b][order], ent[a:b])
+        xm[a:b] = xm[a:b][order]
     # FP32 source records: group-relative position within 2 ulp, exact mass
     gid = np.repeat(np.arange(len(gnode)), np.diff(off))
     rel = e["com"][ent] - box[gid, 6:9].astype(np.float64)
-    xm = L["xm"]
     assert np.all(np.abs(xm[:, :3] - rel) <= 2.0 ** -22 * np.abs(rel) + 1e-45)
     assert np.array_equal(xm[:, 3], e["M"][ent].astype(np.float32))
 
@@ -106,16 +116,19 @@ def test_forces_within_tolerance(oracle_lib, name, precision, tol):
     g = gpu_run(ps.pos, ps.mass, theta=theta, n_crit=n_crit, eps=eps,
                 precision=precision, lists=False)
     T = oracle_lib.Tree(ps.pos, ps.mass)
-    a, p, _, _, amag = T.forces(n_crit, theta, eps, with_amag=True)
-    d = np.linalg.norm(g["acc"].astype(np.float64) - a, axis=1)
-    ea = rel_err(g["acc"], a)
-    ep = np.abs(g["pot"] - p) / np.abs(p)
-    print(f"{name} {precision}: |da|/|a| median {np.median(ea):.2e} p99.9 "
-          f"{np.percentile(ea, 99.9):.2e} max {ea.max():.2e}; |da|/A max "
-          f"{(d / amag).max():.2e}; pot max {ep.max():.2e}")
+    a32, p32, _, _, amag = T.forces(n_crit, theta, eps, with_amag=True, coords32=True)
+    a64, p64, _, _ = T.forces(n_crit, theta, eps)
+    d = np.linalg.norm(g["acc"].astype(np.float64) - a32, axis=1)
+    ep = np.abs(g["pot"] - p32) / np.abs(p32)
+    ea = rel_err(g["acc"], a64)
+    ep64 = np.abs(g["pot"] - p64) / np.abs(p64)
+    print(f"{name} {precision}: |da|/A max {(d / amag).max():.2e}, pot max {ep.max():.2e}; "
+          f"vs FP64 positions |da|/|a| median {np.median(ea):.2e} p99.9 "
+          f"{np.percentile(ea, 99.9):.2e}, pot max {ep64.max():.2e}")
     assert np.all(d <= tol * amag)
-    assert np.median(ea) <= tol / 10
     assert np.all(ep <= tol)
+    assert np.median(ea) <= tol / 10
+    assert np.all(ep64 <= 10 * tol)
 
 
 def test_edge_sizes(oracle_lib):
@@ -128,7 +141,7 @@ def test_edge_sizes(oracle_lib):
             T = oracle_lib.Tree(pos, mass)
             assert_tree_equal(g, T)
             assert_lists_equal(g, T, 0.7, n_crit)
-            a, p, _, _, am = T.forces(n_crit, 0.7, 0.05, with_amag=True)
+            a, p, _, _, am = T.forces(n_crit, 0.7, 0.05, with_amag=True, coords32=True)
             if n == 1:
                 assert np.all(g["acc"] == 0) and g["pot"][0] == 0
             else:
@@ -143,7 +156,7 @@ def test_coincident_particles_and_zero_softening(oracle_lib):
         T = oracle_lib.Tree(pos, mass)
         assert_tree_equal(g, T)
         assert_lists_equal(g, T, 0.6, 16)
-        a, p, _, _, am = T.forces(16, 0.6, eps, with_amag=True)
+        a, p, _, _, am = T.forces(16, 0.6, eps, with_amag=True, coords32=True)
         assert np.all(np.isfinite(g["acc"])) and np.all(np.isfinite(g["pot"]))
         d = np.linalg.norm(g["acc"].astype(np.float64) - a, axis=1)
         assert np.all(d <= 1e-5 * am)
@@ -154,11 +167,14 @@ def test_theta_zero_is_direct_sum(oracle_lib):
     ps = nbsynth.plummer(3000, 4)
     eps = 1 / 64
     g = gpu_run(ps.pos, ps.mass, theta=0.0, n_crit=64, eps=eps, precision="fp32_comp")
-    ad, pd, am = oracle_lib.direct(ps.pos, ps.mass, eps, with_amag=True)
+    T = oracle_lib.Tree(ps.pos, ps.mass)
+    a32, p32, _, _, am = T.forces(64, 0.0, eps, with_amag=True, coords32=True)
+    ad, pd = oracle_lib.direct(ps.pos, ps.mass, eps)
     assert g["stats"]["n_pc"] == 0 and g["stats"]["n_pp"] == ps.n * (ps.n - 1)
-    d = np.linalg.norm(g["acc"].astype(np.float64) - ad, axis=1)
+    d = np.linalg.norm(g["acc"].astype(np.float64) - a32, axis=1)
     assert np.all(d <= 1e-6 * am)
-    assert np.all(np.abs(g["pot"] - pd) <= 1e-6 * np.abs(pd))
+    assert np.all(np.abs(g["pot"] - p32) <= 1e-6 * np.abs(p32))
+    assert np.median(rel_err(g["acc"], ad)) < 1e-7
 
 
 def test_ncrit_one_is_per_particle_walk(oracle_lib):
@@ -170,8 +186,10 @@ def test_ncrit_one_is_per_particle_walk(oracle_lib):
     gn = g["groups"]["gnode"]
     for k in range(0, ps.n, 97):
         slot = e["first"][gn[k]]
-        assert np.array_equal(L["entries"][L["offsets"][k]:L["offsets"][k + 1]],
-                              T.walk_particle(slot, 0.8))
+        ref = T.walk_particle(slot, 0.8)
+        ref = ref[ref != gn[k]]           # the group's own particle
+        got = np.sort(L["entries"][L["offsets"][k]:L["offsets"][k + 1]])
+        assert np.array_equal(got, ref)
 
 
 def test_direct_sum_judge(oracle_lib):
