@@ -190,6 +190,12 @@ int nb_copy_groups(nb_ctx *ctx, int32_t *gnode_host, int32_t *gfirst_host,
 int nb_copy_lists(nb_ctx *ctx, int64_t *offsets_host, int32_t *entries_host,
                   float *xm_host);
 
+/* One group's list of the last walk: up to cap node ids and FP32 source
+ * records; *len_host receives the full length (copy again with a larger cap
+ * when it exceeds cap). */
+int nb_copy_list(nb_ctx *ctx, int64_t group, int32_t *entries_host, float *xm_host,
+                 int64_t cap, int64_t *len_host);
+
 /* Morton order without any device allocation, for callers that cannot call
  * cudaMalloc: it synchronises the device and is not allowed during stream
  * capture, and where another allocator already holds most of the device

@@ -176,7 +176,7 @@ def _grf_displacement(rng: np.random.Generator, pts: np.ndarray, rms: float,
     disp = []
     for kc in (kx, ky, kz):
         psi_k = 1j * kc / k2 * delta
-        disp.append(np.fft.irfftn(psi_k, s=(ngrid, ngrid, ngrid)))
+        disp.append(np.fft.irfftn(psi_k, s=(ngrid, ngrid, ngrid), axes=(0, 1, 2)))
     disp = np.stack(disp, axis=-1)               # (g, g, g, 3)
     # trilinear interpolation, periodic
     f = (pts / box + 0.5) * ngrid

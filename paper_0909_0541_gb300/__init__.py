@@ -32,7 +32,7 @@ EXPORTED = [
     "nb_build_tree", "nb_walk_groups", "nb_forces", "nb_leapfrog_step",
     "nb_leapfrog_reset", "nb_leapfrog_acc", "nb_direct_sum", "nb_sync_status",
     "nb_get_stats", "nb_copy_tree", "nb_copy_groups", "nb_copy_lists",
-    "nb_error_string", "nb_set_timing", "nb_get_timing", "nb_morton_order_noalloc",
+    "nb_error_string", "nb_set_timing", "nb_get_timing", "nb_morton_order_noalloc", "nb_copy_list",
 ]
 NOALLOC_MAX_N = 1 << 20
 PHASES = ("build", "walk", "force", "integrate")
@@ -85,6 +85,7 @@ def _load():
     L.nb_copy_tree.argtypes = [vp] * 14
     L.nb_copy_groups.argtypes = [vp] * 6
     L.nb_copy_lists.argtypes = [vp] * 4
+    L.nb_copy_list.argtypes = [vp, i64, vp, vp, i64, vp]
     L.nb_set_timing.argtypes = [vp, i32]
     L.nb_get_timing.argtypes = [vp, vp, vp, vp]
     L.nb_morton_order_noalloc.argtypes = [vp, i64, vp, vp, vp]
@@ -262,6 +263,16 @@ class NBody:
                                               ["gnode", "gfirst", "gcount", "box", "invtheta"]]),
                "nb_copy_groups")
         return d
+
+    def copy_list(self, group, with_xm=False):
+        """(node ids, FP32 records or None) of one group's list."""
+        n = C.c_int64(0)
+        _check(_lib.nb_copy_list(self._h, int(group), None, None, 0, C.byref(n)), "nb_copy_list")
+        ids = np.zeros(n.value, np.int32)
+        xm = np.zeros((n.value, 4), np.float32) if with_xm else None
+        _check(_lib.nb_copy_list(self._h, int(group), _hptr(ids), _hptr(xm), n.value,
+                                 C.byref(n)), "nb_copy_list")
+        return ids, xm
 
     def copy_lists(self, with_xm=False) -> dict:
         st = self.stats()

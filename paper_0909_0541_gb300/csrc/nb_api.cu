@@ -582,6 +582,31 @@ int nb_copy_groups(nb_ctx *c, int32_t *gnode, int32_t *gfirst, int32_t *gcount, 
     return NB_OK;
 }
 
+int nb_copy_list(nb_ctx *c, int64_t g, int32_t *entries, float *xm, int64_t cap,
+                 int64_t *len_out)
+{
+    if (!c || cap < 0 || !len_out) return NB_ERR_INVALID_ARG;
+    if (!c->has_lists) return NB_ERR_STATE;
+    int rc = read_counters(c);
+    if (rc) return rc;
+    const int64_t G = c->n > 0 ? c->cnt_host[CNT_GROUPS] : 0;
+    if (g < 0 || g >= G) return NB_ERR_INVALID_ARG;
+    int32_t len = 0;
+    CK(cudaMemcpyAsync(&len, c->glen + g, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *len_out = len;
+    int64_t L = len < c->list_cap ? len : c->list_cap;
+    if (L > cap) L = cap;
+    if (entries && L > 0)
+        CK(cudaMemcpyAsync(entries, c->list_id + g * c->list_cap, sizeof(int32_t) * L,
+                           cudaMemcpyDeviceToHost, c->stream));
+    if (xm && L > 0)
+        CK(cudaMemcpyAsync(xm, c->list_xm + g * c->list_cap, sizeof(float4) * L,
+                           cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NB_OK;
+}
+
 int nb_copy_lists(nb_ctx *c, int64_t *offsets, int32_t *entries, float *xm)
 {
     if (!c) return NB_ERR_INVALID_ARG;

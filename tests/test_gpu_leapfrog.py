@@ -1,0 +1,70 @@
+"""nb_leapfrog_step against the oracle's FP64 KDK leapfrog with tree forces,
+and against the FP64 direct-sum leapfrog on the Plummer 16k configuration
+(eps 1/64, theta 0.75, n_crit 64, dt 1/128)."""
+import numpy as np
+import pytest
+
+import nbsynth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def test_one_step_plummer16k(oracle_lib):
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(16384, nbsynth.BASE_SEED + 1)
+    eps, theta, n_crit, dt = 1.0 / 64, 0.75, 64, 1.0 / 128
+    dev = torch.device("cuda")
+    pos = torch.from_numpy(ps.pos).to(dev)
+    vel = torch.from_numpy(ps.vel).to(dev)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    ctx = nb.NBody(ps.n, eps=eps, theta=theta, n_crit=n_crit)
+    ctx.leapfrog_step(pos, vel, mass, dt)
+    acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
+    ctx.leapfrog_acc(acc)
+    x1, v1, a1 = pos.cpu().numpy(), vel.cpu().numpy(), acc.cpu().numpy()
+    xo, vo, ao = oracle_lib.leapfrog(ps.pos, ps.vel, ps.mass, eps, dt, 1, use_tree=True,
+                                     theta=theta, n_crit=n_crit)
+    amax = np.abs(ao).max()
+    # kicks carry the force error (<= 1e-5 relative of the summed magnitudes)
+    assert np.max(np.abs(v1 - vo)) <= dt * 1e-5 * 10 * amax
+    assert np.max(np.abs(x1 - xo)) <= dt * dt * 1e-5 * 10 * amax
+    # accelerations at the new positions
+    assert np.median(np.linalg.norm(a1 - ao, axis=1) / np.linalg.norm(ao, axis=1)) < 1e-6
+    # against the FP64 direct-sum step: the tree's own error at theta 0.75
+    xd, vd, ad = oracle_lib.leapfrog(ps.pos, ps.vel, ps.mass, eps, dt, 1)
+    err = np.linalg.norm(a1 - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    assert 1e-4 < np.median(err) < 5e-3
+    ctx.close()
+
+
+def test_many_steps_conserve_energy(oracle_lib):
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(4096, 77)
+    eps, theta, n_crit, dt = 1.0 / 64, 0.6, 64, 1.0 / 128
+    dev = torch.device("cuda")
+    pos = torch.from_numpy(ps.pos).to(dev)
+    vel = torch.from_numpy(ps.vel).to(dev)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    ctx = nb.NBody(ps.n, eps=eps, theta=theta, n_crit=n_crit, sync_checks=True)
+
+    def energy(p, v):
+        _, pot = oracle_lib.direct(p, ps.mass, eps)
+        m = ps.mass.astype(np.float64)
+        return 0.5 * (m * (v ** 2).sum(1)).sum() + 0.5 * (m * pot).sum()
+
+    e0 = energy(ps.pos, ps.vel)
+    for _ in range(64):
+        ctx.leapfrog_step(pos, vel, mass, dt)
+    e1 = energy(pos.cpu().numpy(), vel.cpu().numpy())
+    assert abs(e1 - e0) < 2e-3 * abs(e0)
+    # reversibility: 64 steps back with negated velocities
+    vel.neg_()
+    ctx.leapfrog_reset()
+    for _ in range(64):
+        ctx.leapfrog_step(pos, vel, mass, dt)
+    assert np.max(np.abs(pos.cpu().numpy() - ps.pos)) < 1e-4
+    ctx.close()
