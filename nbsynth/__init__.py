@@ -300,6 +300,18 @@ def two_body(sep: float, m1: float = 0.5, m2: float = 0.5,
     return ParticleSet(pos, vel, np.array([m1, m2], dtype=np.float32), "twobody")
 
 
+def mlp_initial_weights(seed: int, n_in: int = 12, hidden: int = 64) -> dict:
+    """Seeded random draws for the learned-theta network's initial weights
+    (He-style normal draws; zero biases): W1 (hidden, n_in), W2, W3 (hidden,
+    hidden), w4 (hidden,).  Only random numbers: the network is elsewhere."""
+    rng = _rng(seed)
+    return dict(W1=rng.normal(0.0, math.sqrt(2.0 / n_in), (hidden, n_in)),
+                W2=rng.normal(0.0, math.sqrt(2.0 / hidden), (hidden, hidden)),
+                W3=rng.normal(0.0, math.sqrt(2.0 / hidden), (hidden, hidden)),
+                w4=rng.normal(0.0, math.sqrt(1.0 / hidden), hidden),
+                b1=np.zeros(hidden), b2=np.zeros(hidden), b3=np.zeros(hidden), b4=0.0)
+
+
 # Named workloads with their method parameters (softening eps, opening angle
 # theta, group size n_crit, time step dt).
 WORKLOADS = {
