@@ -190,6 +190,40 @@ int nb_copy_groups(nb_ctx *ctx, int32_t *gnode_host, int32_t *gfirst_host,
 int nb_copy_lists(nb_ctx *ctx, int64_t *offsets_host, int32_t *entries_host,
                   float *xm_host);
 
+/* ---- learned opening angle (the paper has one global theta, Eq. mac; this
+ * per-group form is the project's addition) ---------------------------------
+ * A 12 -> 64 -> 64 -> 64 -> 1 GELU network maps a group's features to
+ * theta = 0.3 + 0.9 sigmoid(z).  Parameters: NB_MLP_NPARAM FP32 values in
+ * the flat layout W1 (64 x 16) @0, b1 @1024, W2 (64 x 64) @1088, b2 @5184,
+ * W3 @5248, b3 @9344, w4 (64) @9408, b4 @9920, mu (16) @9928, sigma (16)
+ * @9944; features are standardised as (x - mu) / sigma.  Products run on
+ * the tensor cores with BF16 operands and FP32 accumulation.  Features are
+ * rows of NB_NFEAT_STRIDE floats (12 used).  `work` is a device workspace
+ * of nb_mlp_workspace_size(batch) bytes owned by the caller.  All calls
+ * queue work on `stream` and do not synchronise. */
+#define NB_MLP_NPARAM 9960
+#define NB_NFEAT 12
+#define NB_NFEAT_STRIDE 16
+size_t nb_mlp_workspace_size(int64_t batch);
+/* theta for n feature rows; a non-finite output becomes `fallback`. */
+int nb_mlp_forward(const float *params_dev, const float *feat_dev, int64_t n,
+                   float *theta_dev, float fallback, void *work_dev, void *stream);
+/* Gradient of the summed loss over a batch of n rows, divided by n
+ * (L = mean((theta - y)^2 + 4 max(0, theta - y)^2)): grad_dev receives
+ * NB_MLP_NPARAM floats; loss_dev (nullable) the loss summed over the batch. */
+int nb_mlp_grad(const float *params_dev, const float *feat_dev, const float *labels_dev,
+                int64_t n, float *grad_dev, float *loss_dev, void *work_dev, void *stream);
+/* Adam training (beta 0.9 / 0.999, eps 1e-8, rate lr) over `epochs` passes of
+ * n samples in batches of `batch`; order_dev holds epochs x n sample indices
+ * (the shuffles, drawn by the caller); adam_m/adam_v start at zero; grad_dev
+ * is NB_MLP_NPARAM floats of scratch; loss_per_epoch_dev (nullable) receives
+ * each epoch's summed loss. */
+int nb_mlp_train(float *params_dev, float *adam_m_dev, float *adam_v_dev,
+                 const float *feat_dev, const float *labels_dev, int64_t n,
+                 const int32_t *order_dev, int epochs, int batch, float lr,
+                 float *grad_dev, float *loss_per_epoch_dev, void *work_dev,
+                 void *stream);
+
 /* One group's list of the last walk: up to cap node ids and FP32 source
  * records; *len_host receives the full length (copy again with a larger cap
  * when it exceeds cap). */

@@ -32,8 +32,11 @@ EXPORTED = [
     "nb_build_tree", "nb_walk_groups", "nb_forces", "nb_leapfrog_step",
     "nb_leapfrog_reset", "nb_leapfrog_acc", "nb_direct_sum", "nb_sync_status",
     "nb_get_stats", "nb_copy_tree", "nb_copy_groups", "nb_copy_lists",
-    "nb_error_string", "nb_set_timing", "nb_get_timing", "nb_morton_order_noalloc", "nb_copy_list",
+    "nb_error_string", "nb_set_timing", "nb_get_timing", "nb_morton_order_noalloc", "nb_copy_list", "nb_mlp_workspace_size",
+    "nb_mlp_forward", "nb_mlp_grad", "nb_mlp_train",
 ]
+MLP_NPARAM = 9960
+NFEAT_STRIDE = 16
 NOALLOC_MAX_N = 1 << 20
 PHASES = ("build", "walk", "force", "integrate")
 
@@ -89,6 +92,11 @@ def _load():
     L.nb_set_timing.argtypes = [vp, i32]
     L.nb_get_timing.argtypes = [vp, vp, vp, vp]
     L.nb_morton_order_noalloc.argtypes = [vp, i64, vp, vp, vp]
+    L.nb_mlp_workspace_size.argtypes = [i64]
+    L.nb_mlp_workspace_size.restype = C.c_size_t
+    L.nb_mlp_forward.argtypes = [vp, vp, i64, vp, C.c_float, vp, vp]
+    L.nb_mlp_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
+    L.nb_mlp_train.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, i32, C.c_float, vp, vp, vp, vp]
     L.nb_error_string.argtypes = [i32]
     L.nb_error_string.restype = C.c_char_p
     return L
@@ -311,3 +319,59 @@ def morton_order_noalloc(pos, keys_out, perm_out, stream=None):
                                         _dptr(perm_out, torch.int32, None, "perm_out"),
                                         _stream_handle(stream)),
            "nb_morton_order_noalloc")
+
+
+# ---------------------------------------------------------------- learned theta
+def _workspace(batch, device):
+    import torch
+    return torch.empty(int(_lib.nb_mlp_workspace_size(int(batch))), dtype=torch.uint8,
+                       device=device)
+
+
+def mlp_forward(params, feat, fallback=0.6, stream=None):
+    """theta (n,) for feature rows feat (n, 16) float32 with the network
+    parameters params (MLP_NPARAM,) float32."""
+    import torch
+    n = int(feat.shape[0])
+    theta = torch.empty(n, dtype=torch.float32, device=feat.device)
+    work = _workspace(max(n, 1), feat.device)
+    _check(_lib.nb_mlp_forward(_dptr(params, torch.float32, None, "params"),
+                               _dptr(feat, torch.float32, NFEAT_STRIDE, "feat"), n,
+                               theta.data_ptr(), float(fallback), work.data_ptr(),
+                               _stream_handle(stream)), "nb_mlp_forward")
+    return theta
+
+
+def mlp_grad(params, feat, labels, stream=None):
+    """(gradient (MLP_NPARAM,), summed loss) of one batch."""
+    import torch
+    n = int(feat.shape[0])
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=feat.device)
+    loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+    work = _workspace(n, feat.device)
+    _check(_lib.nb_mlp_grad(_dptr(params, torch.float32, None, "params"),
+                            _dptr(feat, torch.float32, NFEAT_STRIDE, "feat"),
+                            _dptr(labels, torch.float32, None, "labels"), n,
+                            grad.data_ptr(), loss.data_ptr(), work.data_ptr(),
+                            _stream_handle(stream)), "nb_mlp_grad")
+    return grad, loss
+
+
+def mlp_train(params, feat, labels, order, epochs, batch, lr, stream=None):
+    """Adam training in place on params; order (epochs, n) int32 shuffles.
+    Returns the per-epoch summed loss."""
+    import torch
+    n = int(feat.shape[0])
+    dev = feat.device
+    m = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=dev)
+    v = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=dev)
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=dev)
+    hist = torch.empty(int(epochs), dtype=torch.float32, device=dev)
+    work = _workspace(batch, dev)
+    _check(_lib.nb_mlp_train(_dptr(params, torch.float32, None, "params"), m.data_ptr(),
+                             v.data_ptr(), _dptr(feat, torch.float32, NFEAT_STRIDE, "feat"),
+                             _dptr(labels, torch.float32, None, "labels"), n,
+                             _dptr(order, torch.int32, None, "order"), int(epochs), int(batch),
+                             float(lr), grad.data_ptr(), hist.data_ptr(), work.data_ptr(),
+                             _stream_handle(stream)), "nb_mlp_train")
+    return hist
