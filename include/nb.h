@@ -179,7 +179,7 @@ int nb_copy_tree(nb_ctx *ctx, double *root_host, uint64_t *keys_host,
                  int32_t *count_host, int32_t *next_host, int32_t *parent_host,
                  int32_t *nchild_host, double *mass_host, double *com_host,
                  float *l_host, float *s_host);
-/* Groups of the last walk: node id, first sorted slot, size, box (G x 9:
+/* Groups of the last walk or feature probe: node id, first sorted slot, size, box (G x 9:
  * lo[3], hi[3], centre[3]) and the FP32 1/theta used. */
 int nb_copy_groups(nb_ctx *ctx, int32_t *gnode_host, int32_t *gfirst_host,
                    int32_t *gcount_host, float *box_host, float *invtheta_host);
@@ -201,6 +201,40 @@ int nb_copy_lists(nb_ctx *ctx, int64_t *offsets_host, int32_t *entries_host,
  * rows of NB_NFEAT_STRIDE floats (12 used).  `work` is a device workspace
  * of nb_mlp_workspace_size(batch) bytes owned by the caller.  All calls
  * queue work on `stream` and do not synchronise. */
+/* Features of every group for n_crit: the groups are walked once with
+ * theta = 1.2 without writing lists (the probe walk) and each gets 16
+ * floats: ln n_g; ln(box side / L + 1e-7) for x, y, z; ln n_g minus the sum
+ * of ln(side / L + 1e-4); ln(|box centre - root centre| / L + 1e-6);
+ * ln(list length + 1); accepted cells / list length; ln(min, mean, max
+ * distance from the box centre to the accepted cells' centres of mass / L +
+ * 1e-7); depth of the group node / 22; 4 zeros (L = root cube side).
+ * feat_dev (nullable) receives min(G, cap_rows) rows; n_groups_host
+ * (nullable, synchronises) receives G.  Lists are invalidated. */
+int nb_group_features(nb_ctx *ctx, int n_crit, float *feat_dev, int64_t cap_rows,
+                      int64_t *n_groups_host);
+/* Walk with a per-group theta from the network (params_dev, layout below)
+ * evaluated on the probe features; a non-finite output becomes
+ * theta_fallback.  theta_out_dev (nullable, n floats) receives the group
+ * thetas (G of them are meaningful). */
+int nb_walk_groups_learned(nb_ctx *ctx, int n_crit, const float *params_dev,
+                           float theta_fallback, float *theta_out_dev);
+/* Training data of the learned theta.  nb_group_errors: median |da|/|a| of
+ * each sampled group (rows off[k] .. off[k+1] of ref_dev, FP64 judge
+ * accelerations, belong to sample k and targets_dev gives their caller
+ * indices into acc_dev, n x 3 FP32), at most 1024 members per group.
+ * nb_theta_labels: the label of each sample from its errors at the T thetas
+ * of an ascending grid (err_dev, T x S).  With cost_dev NULL: the largest
+ * grid theta whose error is within budget (else the smallest).  With
+ * cost_dev (interactions of the group at each theta, T x S) and size_dev
+ * (group sizes, S): the grid theta minimising cost / size + lambda *
+ * ln(error), one exchange rate between interactions and error for every
+ * group. */
+int nb_group_errors(const float *acc_dev, const double *ref_dev, const int64_t *targets_dev,
+                    const int64_t *off_dev, int64_t S, float *err_dev, void *stream);
+int nb_theta_labels(const float *err_dev, const float *cost_dev, const float *size_dev,
+                    const float *grid_dev, int T, int64_t S, float budget, float lambda,
+                    float *labels_dev, void *stream);
+
 #define NB_MLP_NPARAM 9960
 #define NB_NFEAT 12
 #define NB_NFEAT_STRIDE 16
@@ -223,6 +257,9 @@ int nb_mlp_train(float *params_dev, float *adam_m_dev, float *adam_v_dev,
                  const int32_t *order_dev, int epochs, int batch, float lr,
                  float *grad_dev, float *loss_per_epoch_dev, void *work_dev,
                  void *stream);
+
+/* List length of every group of the last walk (G int32, host). */
+int nb_copy_group_lengths(nb_ctx *ctx, int32_t *len_host, int64_t cap);
 
 /* One group's list of the last walk: up to cap node ids and FP32 source
  * records; *len_host receives the full length (copy again with a larger cap

@@ -33,7 +33,9 @@ EXPORTED = [
     "nb_leapfrog_reset", "nb_leapfrog_acc", "nb_direct_sum", "nb_sync_status",
     "nb_get_stats", "nb_copy_tree", "nb_copy_groups", "nb_copy_lists",
     "nb_error_string", "nb_set_timing", "nb_get_timing", "nb_morton_order_noalloc", "nb_copy_list", "nb_mlp_workspace_size",
-    "nb_mlp_forward", "nb_mlp_grad", "nb_mlp_train",
+    "nb_mlp_forward", "nb_mlp_grad", "nb_mlp_train", "nb_group_features",
+    "nb_walk_groups_learned", "nb_group_errors", "nb_theta_labels",
+    "nb_copy_group_lengths",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -92,6 +94,11 @@ def _load():
     L.nb_set_timing.argtypes = [vp, i32]
     L.nb_get_timing.argtypes = [vp, vp, vp, vp]
     L.nb_morton_order_noalloc.argtypes = [vp, i64, vp, vp, vp]
+    L.nb_group_features.argtypes = [vp, i32, vp, i64, vp]
+    L.nb_copy_group_lengths.argtypes = [vp, vp, i64]
+    L.nb_walk_groups_learned.argtypes = [vp, i32, vp, C.c_float, vp]
+    L.nb_group_errors.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+    L.nb_theta_labels.argtypes = [vp, vp, vp, vp, i32, i64, C.c_float, C.c_float, vp, vp]
     L.nb_mlp_workspace_size.argtypes = [i64]
     L.nb_mlp_workspace_size.restype = C.c_size_t
     L.nb_mlp_forward.argtypes = [vp, vp, i64, vp, C.c_float, vp, vp]
@@ -223,6 +230,26 @@ class NBody:
         _check(_lib.nb_leapfrog_acc(self._h, _dptr(acc, torch.float32, 3, "acc")),
                "nb_leapfrog_acc")
 
+    def group_features(self, n_crit):
+        """(G, 16) float32 CUDA tensor of the probe-walk features."""
+        import torch
+        G = C.c_int64(0)
+        _check(_lib.nb_group_features(self._h, int(n_crit), None, 0, C.byref(G)),
+               "nb_group_features")
+        feat = torch.empty((max(G.value, 1), NFEAT_STRIDE), dtype=torch.float32, device="cuda")
+        _check(_lib.nb_group_features(self._h, int(n_crit), feat.data_ptr(), G.value, None),
+               "nb_group_features")
+        self.sync_status()
+        return feat[:G.value]
+
+    def walk_groups_learned(self, n_crit, params, theta_fallback=0.6, theta_out=None):
+        import torch
+        _check(_lib.nb_walk_groups_learned(self._h, int(n_crit),
+                                           _dptr(params, torch.float32, None, "params"),
+                                           float(theta_fallback),
+                                           _dptr(theta_out, torch.float32, None, "theta_out")),
+               "nb_walk_groups_learned")
+
     def set_timing(self, on: bool):
         _check(_lib.nb_set_timing(self._h, 1 if on else 0), "nb_set_timing")
 
@@ -262,6 +289,13 @@ class NBody:
         d["is_cell"] = (d["level"] >= 0).astype(np.int8)
         return d
 
+    def copy_perm(self) -> np.ndarray:
+        """Sorted slot -> caller index of the current tree."""
+        perm = np.zeros(self.stats()["n"], np.int32)
+        _check(_lib.nb_copy_tree(self._h, None, None, _hptr(perm), *([None] * 10)),
+               "nb_copy_tree")
+        return perm
+
     def copy_groups(self) -> dict:
         G = self.stats()["n_groups"]
         d = dict(gnode=np.zeros(G, np.int32), gfirst=np.zeros(G, np.int32),
@@ -271,6 +305,12 @@ class NBody:
                                               ["gnode", "gfirst", "gcount", "box", "invtheta"]]),
                "nb_copy_groups")
         return d
+
+    def copy_group_lengths(self) -> np.ndarray:
+        G = self.stats()["n_groups"]
+        out = np.zeros(G, np.int32)
+        _check(_lib.nb_copy_group_lengths(self._h, _hptr(out), G), "nb_copy_group_lengths")
+        return out
 
     def copy_list(self, group, with_xm=False):
         """(node ids, FP32 records or None) of one group's list."""
@@ -375,3 +415,32 @@ def mlp_train(params, feat, labels, order, epochs, batch, lr, stream=None):
                              float(lr), grad.data_ptr(), hist.data_ptr(), work.data_ptr(),
                              _stream_handle(stream)), "nb_mlp_train")
     return hist
+
+
+def group_errors(acc, ref, targets, off, stream=None):
+    """Median |da|/|a| per sampled group (see nb_group_errors)."""
+    import torch
+    S = int(off.shape[0]) - 1
+    err = torch.empty(S, dtype=torch.float32, device=acc.device)
+    _check(_lib.nb_group_errors(_dptr(acc, torch.float32, 3, "acc"),
+                                _dptr(ref, torch.float64, 3, "ref"),
+                                _dptr(targets, torch.int64, None, "targets"),
+                                _dptr(off, torch.int64, None, "off"), S, err.data_ptr(),
+                                _stream_handle(stream)), "nb_group_errors")
+    return err
+
+
+def theta_labels(err, grid, budget=1e-3, cost=None, size=None, lam=0.0, stream=None):
+    """Labels from errors (T, S) over a theta grid; with cost (T, S) and size
+    (S,) the cost-aware labels at exchange rate lam (see nb_theta_labels)."""
+    import torch
+    T, S = int(err.shape[0]), int(err.shape[1])
+    lab = torch.empty(S, dtype=torch.float32, device=err.device)
+    _check(_lib.nb_theta_labels(_dptr(err.contiguous(), torch.float32, None, "err"),
+                                None if cost is None else
+                                _dptr(cost.contiguous(), torch.float32, None, "cost"),
+                                None if size is None else _dptr(size, torch.float32, None, "size"),
+                                _dptr(grid, torch.float32, None, "grid"), T, S, float(budget),
+                                float(lam), lab.data_ptr(), _stream_handle(stream)),
+           "nb_theta_labels")
+    return lab

@@ -54,7 +54,7 @@ static void free_all(nb_ctx *c)
                     c->n_parent, c->n_nchild, c->n_depth, c->bfs2pid, c->pid2bfs, c->dhist,
                     c->level_start, c->w_a, c->w_d, c->w_b, c->w_c, c->b_mass, c->b_mx,
                     c->b_com, c->gflag, c->gnode, c->gfirst, c->gcount, c->glen, c->gcells,
-                    c->gbox, c->items, c->item_cnt, c->list_id, c->list_xm, c->wq,
+                    c->gbox, c->items, c->item_cnt, c->list_id, c->list_xm, c->wq, c->gfeat, c->gtheta,
                     c->acc_cache, c->pot_cache, c->err, c->cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -205,6 +205,7 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
               dalloc(&c->b_com, 3 * NN) && dalloc(&c->gflag, NN + 1) && dalloc(&c->gnode, N) &&
               dalloc(&c->gfirst, N) && dalloc(&c->gcount, N) && dalloc(&c->glen, N) &&
               dalloc(&c->gcells, N) && dalloc(&c->gbox, 3 * N) &&
+              dalloc(&c->gfeat, 16 * N) && dalloc(&c->gtheta, N) &&
               dalloc(&c->items, 2 * c->max_items) && dalloc(&c->item_cnt, N + 1) &&
               dalloc(&c->acc_cache, 3 * N) && dalloc(&c->pot_cache, N) &&
               dalloc(&c->err, 1) && dalloc(&c->cnt, CNT_N_) &&
@@ -256,6 +257,7 @@ int nb_build_tree(nb_ctx *c, const double *pos, const float *mass, int64_t n)
 {
     if (!c || n < 0 || n > c->max_n || (n > 0 && (!pos || !mass))) return NB_ERR_INVALID_ARG;
     c->has_tree = 0;
+    c->has_groups = 0;
     c->has_lists = 0;
     c->n = n;
     if (n == 0) {
@@ -284,6 +286,7 @@ int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
     }
     const int tk = phase_begin(c);
     nb_launch_groups(c, theta, n_crit, theta_g);
+    c->has_groups = 1;
     if (c->sync_checks) {
         int rc = read_counters(c);
         if (rc) return rc;
@@ -333,6 +336,77 @@ int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
     }
     c->has_lists = 1;
     return NB_OK;
+}
+
+// the probe walk over groups formed with theta = NB_PROBE_THETA; in the
+// synchronising mode a frontier that outgrows the walk queues grows them
+static int probe(nb_ctx *c, int n_crit)
+{
+    nb_launch_groups(c, NB_PROBE_THETA, n_crit, nullptr);
+    for (int attempt = 0; attempt < 4; attempt++) {
+        nb_launch_probe(c, c->gfeat);
+        if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
+        if (!c->sync_checks) return NB_OK;
+        unsigned bits = 0;
+        int rc = sync_read_bits(c, &bits);
+        if (rc) return rc;
+        if (!(bits & NB_EF_QUEUE)) return err_code(bits);
+        rc = read_counters(c);
+        if (rc) return rc;
+        const int64_t want = 2 * (c->cnt_host[CNT_QMAX] > c->wq_cap ? c->cnt_host[CNT_QMAX] : c->wq_cap);
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->wq);
+        c->wq = nullptr;
+        if (!dalloc(&c->wq, 2 * want * c->walk_warps)) {
+            cudaGetLastError();
+            c->wq_cap = 0;
+            return NB_ERR_NOMEM;
+        }
+        c->wq_cap = want;
+    }
+    return NB_ERR_CAPACITY;
+}
+
+int nb_group_features(nb_ctx *c, int n_crit, float *feat, int64_t cap_rows, int64_t *n_groups)
+{
+    if (!c || n_crit < 1 || cap_rows < 0) return NB_ERR_INVALID_ARG;
+    if (!c->has_tree) return NB_ERR_STATE;
+    c->has_lists = 0;
+    if (c->n == 0) {
+        if (n_groups) *n_groups = 0;
+        return NB_OK;
+    }
+    int rc = probe(c, n_crit);
+    if (rc) return rc;
+    c->has_groups = 1;
+    if (n_groups || (feat && cap_rows > 0)) {
+        rc = read_counters(c);
+        if (rc) return rc;
+        const int64_t G = c->cnt_host[CNT_GROUPS];
+        if (n_groups) *n_groups = G;
+        const int64_t rows = G < cap_rows ? G : cap_rows;
+        if (feat && rows > 0)
+            CK(cudaMemcpyAsync(feat, c->gfeat, sizeof(float) * 16 * rows, cudaMemcpyDeviceToDevice,
+                               c->stream));
+    }
+    return finish(c);
+}
+
+int nb_walk_groups_learned(nb_ctx *c, int n_crit, const float *params, float fallback,
+                           float *theta_out)
+{
+    if (!c || !params || n_crit < 1 || !(fallback >= 0.f)) return NB_ERR_INVALID_ARG;
+    if (!c->has_tree) return NB_ERR_STATE;
+    if (c->n == 0) return nb_walk_groups(c, fallback, n_crit, nullptr);
+    int rc = probe(c, n_crit);
+    if (rc) return rc;
+    nb_launch_mlp_infer(c, params, c->gfeat, c->gtheta, fallback);
+    if (theta_out) {
+        // group count is known on the device only; copy the whole slot range
+        CK(cudaMemcpyAsync(theta_out, c->gtheta, sizeof(float) * c->n, cudaMemcpyDeviceToDevice,
+                           c->stream));
+    }
+    return nb_walk_groups(c, fallback, n_crit, c->gtheta);
 }
 
 int nb_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision)
@@ -465,7 +539,7 @@ int nb_get_stats(nb_ctx *c, nb_stats *st)
     st->n = c->n;
     st->n_cells = c->n > 0 ? h[CNT_CELLS] : 0;
     st->n_nodes = c->n > 0 ? h[CNT_NODES] : 0;
-    st->n_groups = c->has_lists && c->n > 0 ? h[CNT_GROUPS] : 0;
+    st->n_groups = c->has_groups && c->n > 0 ? h[CNT_GROUPS] : 0;
     st->list_entries = h[CNT_LIST_TOT];
     st->max_list = h[CNT_LIST_MAX];
     st->list_capacity = c->list_cap;
@@ -547,7 +621,7 @@ int nb_copy_groups(nb_ctx *c, int32_t *gnode, int32_t *gfirst, int32_t *gcount, 
                    float *invtheta)
 {
     if (!c) return NB_ERR_INVALID_ARG;
-    if (!c->has_lists) return NB_ERR_STATE;
+    if (!c->has_groups) return NB_ERR_STATE;
     int rc = read_counters(c);
     if (rc) return rc;
     const int64_t G = c->n > 0 ? c->cnt_host[CNT_GROUPS] : 0;
@@ -579,6 +653,19 @@ int nb_copy_groups(nb_ctx *c, int32_t *gnode, int32_t *gfirst, int32_t *gcount, 
         if (invtheta) invtheta[g] = ct.w;
     }
     free(b);
+    return NB_OK;
+}
+
+int nb_copy_group_lengths(nb_ctx *c, int32_t *len, int64_t cap)
+{
+    if (!c || !len || cap < 0) return NB_ERR_INVALID_ARG;
+    if (!c->has_lists) return NB_ERR_STATE;
+    int rc = read_counters(c);
+    if (rc) return rc;
+    int64_t G = c->n > 0 ? c->cnt_host[CNT_GROUPS] : 0;
+    if (G > cap) G = cap;
+    if (G > 0) D2H(len, c->glen, G);
+    CK(cudaStreamSynchronize(c->stream));
     return NB_OK;
 }
 

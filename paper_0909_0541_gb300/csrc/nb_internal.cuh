@@ -34,6 +34,7 @@
 #define NB_WARP 32
 #define NB_EV_POOL 2048
 #define NB_IBLOCK 64   // targets per force work item (two per lane)
+#define NB_PROBE_THETA 1.2f  // opening angle of the feature probe walk
 
 // bits of the device error word
 #define NB_EF_NONFINITE 1u
@@ -70,7 +71,7 @@ struct nb_ctx {
     int64_t max_n;
     int64_t max_nodes;    // 12 * max_n + 2
     int64_t n;            // particles in the current tree
-    int has_tree, has_lists, acc_valid;
+    int has_tree, has_groups, has_lists, acc_valid;
     int n_crit_cur;
     int64_t groups_host;  // G of the last walk, when known on the host
 
@@ -120,6 +121,9 @@ struct nb_ctx {
     int32_t *item_cnt;
     int64_t max_items;
 
+    // learned opening angle: group features (16 floats) and theta per group
+    float *gfeat, *gtheta;
+
     // lists
     int64_t list_cap;     // entries per group slot
     int64_t list_alloc;   // entries allocated
@@ -166,6 +170,11 @@ void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g);
 // nb_walk.cu
 int nb_walk_warps(nb_ctx *c);
 void nb_launch_walk(nb_ctx *c);
+void nb_launch_probe(nb_ctx *c, float *feat);
+
+// nb_mlp.cu
+void nb_launch_mlp_infer(nb_ctx *c, const float *params, const float *feat, float *theta,
+                         float fallback);
 
 // nb_force.cu
 void nb_launch_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision);

@@ -129,6 +129,51 @@ __device__ __forceinline__ void frag_b_w(const float *W, int N, int k0, int n0, 
     b[1] = pack2(p[8 * N], p[9 * N]);
 }
 
+// one hidden layer for a 16-row tile: acc = A (16 x K, BF16 rows) * W^T
+template <int K>
+__device__ __forceinline__ void mma_layer(const bf16 *A, int ldA, int r0, const float *W,
+                                          float acc[8][4])
+{
+    uint32_t a[4], b[2];
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < K / 16; kt++) {
+        frag_a_rows(A, ldA, r0, kt * 16, a);
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            frag_b_wt(W, K, kt * 16, nt * 8, b);
+            mma16816(acc[nt], a, b);
+        }
+    }
+}
+
+// z = w4 . h3 + b4 for the two rows (g, g + 8) a lane holds, FP32
+__device__ __forceinline__ void out_z(const float acc[8][4], const float *P, float z[2])
+{
+    const int t = threadIdx.x & 3;
+    float zr[2] = {0.f, 0.f};
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int col = nt * 8 + 2 * t;
+            zr[h] = fmaf(acc[nt][2 * h], P[P_W4 + col], zr[h]);
+            zr[h] = fmaf(acc[nt][2 * h + 1], P[P_W4 + col + 1], zr[h]);
+        }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        zr[h] += __shfl_xor_sync(0xffffffffu, zr[h], 1);
+        zr[h] += __shfl_xor_sync(0xffffffffu, zr[h], 2);
+        z[h] = zr[h] + P[P_B4];
+    }
+}
+
+__device__ __forceinline__ float norm_feature(const float *x, const float *P, int k)
+{
+    return k < MNIN ? __fdiv_rn(__fsub_rn(x[k], P[P_MU + k]), P[P_SG + k]) : 0.0f;
+}
+
 // ------------------------------------------------------------ input
 // z0 = (x - mu) / sigma in FP32, rounded to BF16, padded to 16 columns;
 // rows >= B are zero.  x has 16-float rows; idx (nullable) gathers rows;
@@ -145,7 +190,7 @@ k_mlp_input(const float *__restrict__ x, const int32_t *__restrict__ idx, const 
     float v = 0.0f;
     if (r < B && k < MNIN) {
         const int64_t row = idx ? idx[r] : r;
-        v = __fdiv_rn(__fsub_rn(x[row * MKIN + k], P[P_MU + k]), P[P_SG + k]);
+        v = norm_feature(x + row * MKIN, P, k);
     }
     a0[i] = __float2bfloat16_rn(v);
     if (k == 0 && yout) yout[r] = (r < B && ylab) ? ylab[idx ? idx[r] : r] : 0.0f;
@@ -164,102 +209,44 @@ k_mlp_fwd(const float *__restrict__ P, int64_t Bp, MlpWork w, float *__restrict_
     if (tile * 16 >= Bp) return;
     const int r0 = (int)(tile * 16);
     float acc[8][4];
-    uint32_t a[4], b[2];
-    // layer 1: K = 16
-#pragma unroll
-    for (int nt = 0; nt < 8; nt++) {
-        acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    }
-    frag_a_rows(w.a0, MKIN, r0, 0, a);
-#pragma unroll
-    for (int nt = 0; nt < 8; nt++) {
-        frag_b_wt(P + P_W1, MKIN, 0, nt * 8, b);
-        mma16816(acc[nt], a, b);
-    }
-    // bias + GELU; layer outputs written row-major (the next layer's A)
-    auto finish = [&](const float *bias, float *Z, bf16 *act) {
+    const float *Ws[3] = {P + P_W1, P + P_W2, P + P_W3};
+    const float *bs[3] = {P + P_B1, P + P_B2, P + P_B3};
+    const bf16 *ins[3] = {w.a0, w.a1, w.a2};
+    bf16 *outs[2] = {w.a1, w.a2};
+    float *Zs[3] = {w.Z1, w.Z2, w.Z3};
+    for (int L = 0; L < 3; L++) {
+        if (L == 0) mma_layer<MKIN>(ins[0], MKIN, r0, Ws[0], acc);
+        else mma_layer<MH>(ins[L], MH, r0, Ws[L], acc);
 #pragma unroll
         for (int nt = 0; nt < 8; nt++)
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const int row = r0 + g + 8 * h, col = nt * 8 + 2 * t;
-                const float z0 = acc[nt][2 * h] + bias[col];
-                const float z1 = acc[nt][2 * h + 1] + bias[col + 1];
+                const float z0 = acc[nt][2 * h] + bs[L][col];
+                const float z1 = acc[nt][2 * h + 1] + bs[L][col + 1];
                 if (KEEP) {
-                    Z[(int64_t)row * MH + col] = z0;
-                    Z[(int64_t)row * MH + col + 1] = z1;
+                    Zs[L][(int64_t)row * MH + col] = z0;
+                    Zs[L][(int64_t)row * MH + col + 1] = z1;
                 }
                 const float g0 = gelu(z0), g1 = gelu(z1);
                 acc[nt][2 * h] = g0;
                 acc[nt][2 * h + 1] = g1;
-                *reinterpret_cast<uint32_t *>(act + (int64_t)row * MH + col) = pack2(g0, g1);
-            }
-    };
-    finish(P + P_B1, w.Z1, w.a1);
-    __syncwarp();
-    // layers 2 and 3: K = 64
-    const float *Ws[2] = {P + P_W2, P + P_W3};
-    const float *bs[2] = {P + P_B2, P + P_B3};
-    bf16 *ins[2] = {w.a1, w.a2};
-    float *Zs[2] = {w.Z2, w.Z3};
-    for (int L = 0; L < 2; L++) {
-#pragma unroll
-        for (int nt = 0; nt < 8; nt++) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-        for (int kt = 0; kt < 4; kt++) {
-            frag_a_rows(ins[L], MH, r0, kt * 16, a);
-#pragma unroll
-            for (int nt = 0; nt < 8; nt++) {
-                frag_b_wt(Ws[L], MH, kt * 16, nt * 8, b);
-                mma16816(acc[nt], a, b);
-            }
-        }
-        if (L == 0) {
-            finish(bs[L], Zs[L], w.a2);
-        } else {
-            // last hidden layer: keep FP32 h3 for the output and backward
-#pragma unroll
-            for (int nt = 0; nt < 8; nt++)
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const int row = r0 + g + 8 * h, col = nt * 8 + 2 * t;
-                    const float z0 = acc[nt][2 * h] + bs[L][col];
-                    const float z1 = acc[nt][2 * h + 1] + bs[L][col + 1];
-                    if (KEEP) {
-                        Zs[L][(int64_t)row * MH + col] = z0;
-                        Zs[L][(int64_t)row * MH + col + 1] = z1;
-                    }
-                    acc[nt][2 * h] = gelu(z0);
-                    acc[nt][2 * h + 1] = gelu(z1);
-                    if (KEEP) {
-                        w.h3[(int64_t)row * MH + col] = acc[nt][2 * h];
-                        w.h3[(int64_t)row * MH + col + 1] = acc[nt][2 * h + 1];
-                    }
+                if (L < 2) {
+                    *reinterpret_cast<uint32_t *>(outs[L] + (int64_t)row * MH + col) = pack2(g0, g1);
+                } else if (KEEP) {
+                    w.h3[(int64_t)row * MH + col] = g0;
+                    w.h3[(int64_t)row * MH + col + 1] = g1;
                 }
-        }
+            }
         __syncwarp();
     }
-    // output: z = w4 . h3 + b4 (FP32), reduced over the four lanes of a row
-    float zr[2] = {0.f, 0.f};
-#pragma unroll
-    for (int nt = 0; nt < 8; nt++)
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int col = nt * 8 + 2 * t;
-            zr[h] = fmaf(acc[nt][2 * h], P[P_W4 + col], zr[h]);
-            zr[h] = fmaf(acc[nt][2 * h + 1], P[P_W4 + col + 1], zr[h]);
-        }
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        zr[h] += __shfl_xor_sync(0xffffffffu, zr[h], 1);
-        zr[h] += __shfl_xor_sync(0xffffffffu, zr[h], 2);
-    }
+    float z[2];
+    out_z(acc, P, z);
     if (t == 0)
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int row = r0 + g + 8 * h;
-            const float z = zr[h] + P[P_B4];
-            const float s = 1.0f / (1.0f + expf(-z));
+            const float s = 1.0f / (1.0f + expf(-z[h]));
             float th = 0.3f + 0.9f * s;
             if (KEEP) {
                 w.s[row] = s;
@@ -270,6 +257,177 @@ k_mlp_fwd(const float *__restrict__ P, int64_t Bp, MlpWork w, float *__restrict_
                 theta_out[row] = th;
             }
         }
+}
+
+// Inference for every group of a context: the same arithmetic as k_mlp_fwd
+// with the layer activations in shared memory; the group count is read on
+// the device (no host synchronisation, no workspace).
+__global__ void __launch_bounds__(MLP_T)
+k_mlp_infer(const float *__restrict__ P, const float *__restrict__ feat,
+            const long long *__restrict__ cnt, float *__restrict__ theta, float fallback)
+{
+    __shared__ __align__(16) bf16 sbuf[MLP_T / 32][2][16 * MH];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t G = cnt[CNT_GROUPS];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    bf16 *b0 = sbuf[wl][0], *b1 = sbuf[wl][1];
+    for (int64_t tile = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; tile * 16 < G;
+         tile += nwarps) {
+        const int64_t r0 = tile * 16;
+        for (int e = lane; e < 16 * MKIN; e += 32) {
+            const int r = e / MKIN, k = e % MKIN;
+            const float v = r0 + r < G ? norm_feature(feat + (r0 + r) * MKIN, P, k) : 0.0f;
+            b0[r * MKIN + k] = __float2bfloat16_rn(v);
+        }
+        __syncwarp();
+        float acc[8][4];
+        const float *Ws[3] = {P + P_W1, P + P_W2, P + P_W3};
+        const float *bs[3] = {P + P_B1, P + P_B2, P + P_B3};
+        for (int L = 0; L < 3; L++) {
+            bf16 *src = (L == 1) ? b1 : b0;
+            bf16 *dst = (L == 1) ? b0 : b1;
+            if (L == 0) mma_layer<MKIN>(src, MKIN, 0, Ws[0], acc);
+            else mma_layer<MH>(src, MH, 0, Ws[L], acc);
+            __syncwarp();
+#pragma unroll
+            for (int nt = 0; nt < 8; nt++)
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int row = g + 8 * h, col = nt * 8 + 2 * t;
+                    const float g0 = gelu(acc[nt][2 * h] + bs[L][col]);
+                    const float g1 = gelu(acc[nt][2 * h + 1] + bs[L][col + 1]);
+                    acc[nt][2 * h] = g0;
+                    acc[nt][2 * h + 1] = g1;
+                    if (L < 2) *reinterpret_cast<uint32_t *>(dst + row * MH + col) = pack2(g0, g1);
+                }
+            __syncwarp();
+        }
+        float z[2];
+        out_z(acc, P, z);
+        if (t == 0)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int64_t row = r0 + g + 8 * h;
+                if (row < G) {
+                    float th = 0.3f + 0.9f * (1.0f / (1.0f + expf(-z[h])));
+                    theta[row] = isfinite(th) ? th : fallback;
+                }
+            }
+        __syncwarp();
+    }
+}
+
+void nb_launch_mlp_infer(nb_ctx *c, const float *params, const float *feat, float *theta,
+                         float fallback)
+{
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_mlp_infer, MLP_T, 0);
+    if (blocks < 1) blocks = 1;
+    k_mlp_infer<<<c->num_sms * blocks, MLP_T, 0, c->stream>>>(params, feat, c->cnt, theta, fallback);
+    c->launches++;
+}
+
+// ------------------------------------------------------------ training data
+// Median relative force error of each sampled group: rows off[k] .. off[k+1]
+// of ref (FP64 judge accelerations) belong to sampled group k, targets[]
+// gives their caller index into acc.  One warp per group, bitonic sort of up
+// to 1024 errors in shared memory; median = mean of the two middle values.
+#define GE_MAX 1024
+__global__ void __launch_bounds__(128)
+k_group_errors(const float *__restrict__ acc, const double *__restrict__ ref,
+               const int64_t *__restrict__ targets, const int64_t *__restrict__ off, int64_t S,
+               float *__restrict__ err)
+{
+    __shared__ float buf[4][GE_MAX];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (k >= S) return;
+    const int64_t a = off[k];
+    int n = (int)(off[k + 1] - a);
+    if (n > GE_MAX) n = GE_MAX;
+    int np = 1;
+    while (np < n) np <<= 1;
+    float *e = buf[wl];
+    for (int i = lane; i < np; i += 32) {
+        float v = INFINITY;
+        if (i < n) {
+            const int64_t o = targets[a + i];
+            const double rx = ref[3 * (a + i)], ry = ref[3 * (a + i) + 1], rz = ref[3 * (a + i) + 2];
+            const double dx = (double)acc[3 * o] - rx, dy = (double)acc[3 * o + 1] - ry,
+                         dz = (double)acc[3 * o + 2] - rz;
+            const double r = sqrt(rx * rx + ry * ry + rz * rz);
+            v = (float)(sqrt(dx * dx + dy * dy + dz * dz) / (r > 0.0 ? r : 1.0));
+        }
+        e[i] = v;
+    }
+    __syncwarp();
+    for (int size = 2; size <= np; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < np; i += 32) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const float x = e[i], y = e[j];
+                    if ((x > y) == up) { e[i] = y; e[j] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    if (lane == 0) err[k] = n > 0 ? 0.5f * (e[(n - 1) / 2] + e[n / 2]) : 0.0f;
+}
+
+// Label of each sample from its error curve err[t][k] (T x S, grid
+// ascending).  Without costs: the largest grid theta whose error meets the
+// budget (the smallest grid theta when none does).  With costs (interactions
+// of the group at each theta) and group sizes: the grid theta minimising
+// cost / n + lambda * ln(error), the allocation that trades interactions
+// against error at one exchange rate lambda for every group.
+__global__ void k_theta_labels(const float *__restrict__ err, const float *__restrict__ cost,
+                               const float *__restrict__ nsz, const float *__restrict__ grid,
+                               int T, int64_t S, float budget, float lambda,
+                               float *__restrict__ labels)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= S) return;
+    float lab = grid[0];
+    if (!cost) {
+        for (int t = 0; t < T; t++)
+            if (err[(int64_t)t * S + k] <= budget) lab = grid[t];
+    } else {
+        float best = INFINITY;
+        for (int t = 0; t < T; t++) {
+            const float o = cost[(int64_t)t * S + k] / nsz[k] +
+                            lambda * logf(fmaxf(err[(int64_t)t * S + k], 1e-9f));
+            if (o < best) { best = o; lab = grid[t]; }
+        }
+    }
+    labels[k] = lab;
+}
+
+extern "C" int nb_group_errors(const float *acc_dev, const double *ref_dev,
+                               const int64_t *targets_dev, const int64_t *off_dev, int64_t S,
+                               float *err_dev, void *stream)
+{
+    if (S < 0 || (S > 0 && (!acc_dev || !ref_dev || !targets_dev || !off_dev || !err_dev)))
+        return NB_ERR_INVALID_ARG;
+    if (S == 0) return NB_OK;
+    k_group_errors<<<(int)((S * 32 + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+        acc_dev, ref_dev, targets_dev, off_dev, S, err_dev);
+    return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}
+
+extern "C" int nb_theta_labels(const float *err_dev, const float *cost_dev,
+                               const float *size_dev, const float *grid_dev, int T, int64_t S,
+                               float budget, float lambda, float *labels_dev, void *stream)
+{
+    if (T < 1 || S < 0 || (S > 0 && (!err_dev || !grid_dev || !labels_dev)) ||
+        (cost_dev && !size_dev))
+        return NB_ERR_INVALID_ARG;
+    if (S == 0) return NB_OK;
+    k_theta_labels<<<nb_grid(S, 256), 256, 0, (cudaStream_t)stream>>>(
+        err_dev, cost_dev, size_dev, grid_dev, T, S, budget, lambda, labels_dev);
+    return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
 }
 
 // ------------------------------------------------------------ backward

@@ -44,6 +44,13 @@ __device__ __forceinline__ bool far_enough(const float4 &a, float l, float s,
     return d2 > __fmul_rn(w, w);
 }
 
+// PROBE: walk without writing lists and turn the list statistics into the
+// group's features for the learned opening angle (16 floats per group):
+//   0 ln n_g;  1-3 ln(box side / L + 1e-7);  4 ln n_g - sum ln(side / L + 1e-4)
+//   5 ln(|box centre - root centre| / L + 1e-6);  6 ln(list length + 1)
+//   7 accepted cells / list length;  8-10 ln(min, mean, max distance from the
+//   box centre to accepted cells' centres of mass / L + 1e-7);  11 depth / 22
+template <bool PROBE>
 __global__ void __launch_bounds__(WALK_T)
 k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
        const int4 *__restrict__ w_b, const float2 *__restrict__ w_c,
@@ -51,7 +58,8 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
        const int32_t *__restrict__ gcount, const float4 *__restrict__ gbox,
        long long *__restrict__ cnt, int32_t *__restrict__ glen, int32_t *__restrict__ gcells,
        int32_t *__restrict__ list_id, float4 *__restrict__ list_xm, int64_t cap, int64_t alloc,
-       int32_t *__restrict__ wq, int64_t wq_cap, unsigned *__restrict__ err)
+       int32_t *__restrict__ wq, int64_t wq_cap, unsigned *__restrict__ err,
+       float *__restrict__ feat, const double *__restrict__ root, const int8_t *__restrict__ n_depth)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -77,6 +85,7 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
         const int64_t base = (int64_t)g * cap;
         const int64_t room = alloc - base < cap ? (alloc - base > 0 ? alloc - base : 0) : cap;
         int32_t len = 0, ncell = 0;
+        float dmin = INFINITY, dmax = 0.0f, dsum = 0.0f;
         int32_t *qin = qa, *qout = qb;
         if (lane == 0) qin[0] = 0;   // the root
         __syncwarp();
@@ -112,7 +121,14 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
                     }
                 }
                 const unsigned em = __ballot_sync(FULL, emit);
-                if (emit) {
+                if (PROBE && cell_emit) {
+                    const float dx = a.x - bc.x, dy = a.y - bc.y, dz = a.z - bc.z;
+                    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+                    dmin = fminf(dmin, d);
+                    dmax = fmaxf(dmax, d);
+                    dsum += d;
+                }
+                if (!PROBE && emit) {
                     const int32_t pos = len + __popc(em & lt);
                     if (pos < room) {
                         const float4 d = w_d[b];
@@ -143,7 +159,41 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
             na = nb;
             if (++depth_guard > NB_DEPTHS + 1) { bad |= NB_EF_WALK; break; }
         }
-        if (lane == 0) {
+        if (PROBE) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dmin = fminf(dmin, __shfl_xor_sync(FULL, dmin, o));
+                dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o));
+                dsum += __shfl_xor_sync(FULL, dsum, o);
+            }
+            if (lane < 16) {
+                const float L = (float)root[3];
+                const float ng = (float)gcount[g];
+                const float sx = (bhi.x - blo.x) / L, sy = (bhi.y - blo.y) / L,
+                            sz = (bhi.z - blo.z) / L;
+                const float cx = bc.x - (float)root[0], cy = bc.y - (float)root[1],
+                            cz = bc.z - (float)root[2];
+                const bool any = ncell > 0;
+                float v = 0.0f;
+                switch (lane) {
+                case 0: v = logf(ng); break;
+                case 1: v = logf(sx + 1e-7f); break;
+                case 2: v = logf(sy + 1e-7f); break;
+                case 3: v = logf(sz + 1e-7f); break;
+                case 4: v = logf(ng) - logf(sx + 1e-4f) - logf(sy + 1e-4f) - logf(sz + 1e-4f); break;
+                case 5: v = logf(sqrtf(cx * cx + cy * cy + cz * cz) / L + 1e-6f); break;
+                case 6: v = logf((float)len + 1.0f); break;
+                case 7: v = len > 0 ? (float)ncell / (float)len : 0.0f; break;
+                case 8: v = logf((any ? dmin : 0.0f) / L + 1e-7f); break;
+                case 9: v = logf((any ? dsum / (float)ncell : 0.0f) / L + 1e-7f); break;
+                case 10: v = logf((any ? dmax : 0.0f) / L + 1e-7f); break;
+                case 11: v = (float)n_depth[gpid] / 22.0f; break;
+                default: v = 0.0f;
+                }
+                feat[(int64_t)g * 16 + lane] = v;
+            }
+        }
+        if (!PROBE && lane == 0) {
             glen[g] = len;
             gcells[g] = ncell;
             const long long m = gcount[g];
@@ -169,8 +219,10 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
 // warps of one walk launch (the frontier queues are sized for them)
 int nb_walk_warps(nb_ctx *c)
 {
-    int blocks = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_walk, WALK_T, 0);
+    int blocks = 0, bp = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_walk<false>, WALK_T, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, k_walk<true>, WALK_T, 0);
+    if (bp < blocks) blocks = bp;
     if (blocks < 1) blocks = 1;
     return c->num_sms * blocks * WALK_WARPS;
 }
@@ -181,9 +233,22 @@ void nb_launch_walk(nb_ctx *c)
     static_assert(CNT_LIST_TOT + 4 == CNT_WALK_Q, "counter layout");
     cudaMemsetAsync(&c->cnt[CNT_QMAX], 0, sizeof(long long), c->stream);
     const int blocks = c->walk_warps / WALK_WARPS;
-    k_walk<<<blocks, WALK_T, 0, c->stream>>>(
+    k_walk<false><<<blocks, WALK_T, 0, c->stream>>>(
         c->w_a, c->w_d, c->w_b, c->w_c, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
         c->glen, c->gcells, c->list_id, c->list_xm, c->list_cap, c->list_alloc, c->wq,
-        c->wq_cap, c->err);
+        c->wq_cap, c->err, nullptr, c->root, c->n_depth);
+    c->launches++;
+}
+
+// the probe walk: features of every group (the groups must be formed with
+// the probe's opening angle)
+void nb_launch_probe(nb_ctx *c, float *feat)
+{
+    cudaMemsetAsync(&c->cnt[CNT_WALK_Q], 0, sizeof(long long), c->stream);
+    const int blocks = c->walk_warps / WALK_WARPS;
+    k_walk<true><<<blocks, WALK_T, 0, c->stream>>>(
+        c->w_a, c->w_d, c->w_b, c->w_c, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
+        c->glen, c->gcells, nullptr, nullptr, 0, 0, c->wq, c->wq_cap, c->err, feat, c->root,
+        c->n_depth);
     c->launches++;
 }

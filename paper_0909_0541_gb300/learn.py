@@ -1,0 +1,182 @@
+"""Learned per-group opening angle: training data, training, evaluation.
+
+The paper uses one global theta (Eq. mac, Sec. "Our GPU implementation");
+this module drives the learned form through the C ABI.  Every computation
+runs in libnb's kernels: the probe walk (features), the tree walk and force
+sum at each theta of a grid, the FP64 direct-sum judge, per-group median
+errors, labels, and the tensor-core network's training and inference.  What
+remains here is orchestration: choosing which groups to judge (seeded draws),
+index bookkeeping, and the shuffles handed to the trainer.
+
+Labels: each sampled group is walked and summed at every theta of the grid
+0.30, 0.35, ..., 1.20, giving its median |da|/|a| against the FP64 direct
+sum, e(theta), and its interactions, c(theta).  Its label is the grid theta
+minimising c / n_g + lambda ln e: one exchange rate between interactions and
+error for all groups, so that groups whose error barely grows with theta
+(dense regions, where near neighbours dominate the force) open fewer cells
+and groups whose error grows fast keep a small theta.  lambda is bisected so
+that the n_g-weighted median of the labelled errors meets the budget (1e-3).
+(Requiring every group's own median to meet the budget costs as much as one
+fixed theta at the same global median error.)  The network maps the 12
+probe features to theta in [0.3, 1.2]; the fixed-theta walk is the fallback
+for non-finite output.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import (MLP_NPARAM, NFEAT_STRIDE, NBody, direct_sum, group_errors, mlp_train,
+               theta_labels)
+
+THETA_GRID = np.round(np.arange(0.30, 1.2001, 0.05), 2).astype(np.float32)
+BUDGET = 1e-3
+NIN = 12
+OFF = dict(W1=0, b1=1024, W2=1088, b2=5184, W3=5248, b3=9344, w4=9408, b4=9920, mu=9928,
+           sigma=9944)
+
+
+def pack_params(w: dict, mu, sigma) -> np.ndarray:
+    """Flat FP32 parameters (layout of include/nb.h) from initial weights
+    w (W1 64x12, W2, W3 64x64, w4 64, biases) and feature mean / spread."""
+    p = np.zeros(MLP_NPARAM, np.float64)
+    W1 = np.zeros((64, 16))
+    W1[:, :NIN] = w["W1"]
+    p[OFF["W1"]:OFF["W1"] + 1024] = W1.ravel()
+    p[OFF["b1"]:OFF["b1"] + 64] = w["b1"]
+    p[OFF["W2"]:OFF["W2"] + 4096] = np.ravel(w["W2"])
+    p[OFF["b2"]:OFF["b2"] + 64] = w["b2"]
+    p[OFF["W3"]:OFF["W3"] + 4096] = np.ravel(w["W3"])
+    p[OFF["b3"]:OFF["b3"] + 64] = w["b3"]
+    p[OFF["w4"]:OFF["w4"] + 64] = w["w4"]
+    p[OFF["b4"]] = w["b4"]
+    p[OFF["mu"]:OFF["mu"] + NIN] = mu
+    sg = np.ones(16)
+    sg[:NIN] = np.where(np.asarray(sigma) > 0, sigma, 1.0)
+    p[OFF["sigma"]:OFF["sigma"] + 16] = sg
+    return p.astype(np.float32)
+
+
+def judge_targets(ctx: NBody, groups: np.ndarray):
+    """Caller indices of the members of `groups` (in group order) and the
+    offsets of each group's rows."""
+    gg = ctx.copy_groups()
+    perm = ctx.copy_perm()
+    first, count = gg["gfirst"][groups], gg["gcount"][groups]
+    targets = np.concatenate([perm[f:f + c] for f, c in zip(first, count)]).astype(np.int64)
+    off = np.r_[0, np.cumsum(count)].astype(np.int64)
+    return targets, off
+
+
+def weighted_median(v, w):
+    o = np.argsort(v, kind="stable")
+    cw = np.cumsum(w[o])
+    return float(v[o][np.searchsorted(cw, 0.5 * cw[-1])])
+
+
+def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget=BUDGET,
+                 ctx: NBody | None = None):
+    """(features (S,16), labels (S,), info) for S seeded random groups of the
+    particle set (pos, mass: CUDA tensors); info holds the error and cost
+    curves, the group sizes, the sampled groups and the exchange rate."""
+    import torch
+    n = int(pos.shape[0])
+    own = ctx is None
+    ctx = ctx or NBody(n, eps=eps, n_crit=n_crit)
+    ctx.build_tree(pos, mass)
+    feat = ctx.group_features(n_crit)
+    G = int(feat.shape[0])
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(G, min(n_sample, G), replace=False))
+    targets, off = judge_targets(ctx, sel)
+    size = np.diff(off).astype(np.float32)
+    dev = pos.device
+    t_dev = torch.from_numpy(targets).to(dev)
+    o_dev = torch.from_numpy(off).to(dev)
+    ref, _ = direct_sum(pos, mass, eps, t_dev)
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    errs = torch.empty((len(grid), len(sel)), dtype=torch.float32, device=dev)
+    cost = np.zeros((len(grid), len(sel)), np.float32)
+    for t, th in enumerate(grid):
+        ctx.walk_groups(float(th), n_crit)
+        ctx.forces(eps, acc)
+        errs[t] = group_errors(acc, ref, t_dev, o_dev)
+        cost[t] = size * (ctx.copy_group_lengths()[sel] + size)
+    grid_d = torch.from_numpy(np.asarray(grid, np.float32)).to(dev)
+    cost_d = torch.from_numpy(cost).to(dev)
+    size_d = torch.from_numpy(size).to(dev)
+    E = errs.cpu().numpy()
+    col = np.arange(len(sel))
+
+    def labelled_error(lam):
+        lab = theta_labels(errs, grid_d, budget, cost_d, size_d, lam)
+        ti = np.searchsorted(np.asarray(grid, np.float32), lab.cpu().numpy())
+        return lab, weighted_median(E[np.minimum(ti, len(grid) - 1), col], size)
+
+    lo, hi = 1.0, 1e6          # ln-space bisection on the exchange rate
+    for _ in range(40):
+        mid = float(np.sqrt(lo * hi))
+        if labelled_error(mid)[1] > budget:
+            lo = mid
+        else:
+            hi = mid
+    labels, werr = labelled_error(hi)
+    X = feat[torch.from_numpy(sel).to(dev)].contiguous()
+    if own:
+        ctx.close()
+    info = dict(errors=E, cost=cost, size=size, groups=sel, lam=hi, labelled_error=werr)
+    return X, labels, info
+
+
+def train(X, y, epochs=150, batch=256, lr=2e-3, seed=5):
+    """Fresh network (seeded initial weights) trained on (X, y).  Returns
+    (params CUDA tensor, per-epoch mean loss)."""
+    import torch
+
+    import nbsynth
+    S = int(X.shape[0])
+    Xh = X[:, :NIN].double().cpu().numpy()
+    params = torch.from_numpy(pack_params(nbsynth.mlp_initial_weights(seed), Xh.mean(0),
+                                          Xh.std(0))).to(X.device)
+    rng = np.random.default_rng(seed + 1)
+    order = torch.from_numpy(np.stack([rng.permutation(S) for _ in range(epochs)])
+                             .astype(np.int32)).to(X.device)
+    hist = mlp_train(params, X, y, order, epochs, batch, lr)
+    steps = S // batch
+    return params, (hist / (steps * batch)).cpu().numpy()
+
+
+def median_error(acc, ref, targets):
+    """Median |da|/|a| of acc at targets against the judge ref."""
+    import torch
+    d = (acc[targets].double() - ref).norm(dim=1) / ref.norm(dim=1)
+    return float(torch.median(d).item()) if d.numel() else 0.0
+
+
+def step_cost(ctx: NBody, n_crit, eps, acc, theta=None, params=None, fallback=0.6):
+    """Walk + force once (fixed theta, or the network's per-group theta);
+    returns (interactions, milliseconds of the walk and force phases)."""
+    ctx.set_timing(True)
+    ctx.get_timing()
+    if params is None:
+        ctx.walk_groups(theta, n_crit)
+    else:
+        ctx.walk_groups_learned(n_crit, params, fallback)
+    ctx.forces(eps, acc)
+    tm = ctx.get_timing()
+    ctx.set_timing(False)
+    st = ctx.stats()
+    return st["n_pp"] + st["n_pc"], tm["walk"][0] + tm["force"][0]
+
+
+def matched_fixed_theta(ctx: NBody, n_crit, eps, acc, ref, targets, target_err,
+                        lo=0.3, hi=1.2, iters=12):
+    """Bisection for the fixed theta whose median error equals target_err."""
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        ctx.walk_groups(mid, n_crit)
+        ctx.forces(eps, acc)
+        if median_error(acc, ref, targets) > target_err:
+            hi = mid
+        else:
+            lo = mid
+    return lo

@@ -92,3 +92,29 @@ def test_bf16_forward_close_to_fp64_forward():
     t16, _ = mlp.forward(p, x, bf=True)
     assert np.max(np.abs(t64 - t16)) < 0.02
     assert not np.array_equal(t64, t16)
+
+
+def test_features_closed_form_two_clumps(oracle_lib):
+    # two tight clumps far apart: each is a group whose probe list is the
+    # other clump's cell, so every feature has a closed form
+    from oracle import features
+    rng = np.random.default_rng(0)
+    a = 0.001 * rng.normal(size=(20, 3)) + [-1.0, -1.0, -1.0]   # octant 0
+    b = 0.001 * rng.normal(size=(20, 3)) + [1.0, 1.0, 1.0]      # octant 7
+    pos = np.vstack([a, b])
+    mass = np.full(40, 0.025, np.float32)
+    T = oracle_lib.Tree(pos, mass)
+    f = features.group_features(T, 20)
+    gnode = T.groups(20)
+    assert len(gnode) == 2
+    box = T.group_boxes(gnode)
+    e = T.export()
+    for k, other in ((0, b), (1, a)):
+        lo, hi = box[k, :3].astype(np.float64), box[k, 3:6].astype(np.float64)
+        side = (hi - lo) / T.L
+        assert f[k, 0] == pytest.approx(np.log(20))
+        assert np.allclose(f[k, 1:4], np.log(side + 1e-7))
+        assert f[k, 6] == pytest.approx(np.log(2.0)) and f[k, 7] == 1.0
+        com = other.mean(0)
+        d = np.linalg.norm(com - box[k, 6:9].astype(np.float64)) / T.L
+        assert np.allclose(f[k, 8:11], np.log(d + 1e-7), atol=1e-6)
