@@ -56,6 +56,7 @@ typedef struct nb_config {
     float theta;           /* opening angle, >= 0 (0 = never accept a cell)  */
     int n_crit;            /* maximum group size, >= 1                       */
     int precision;         /* NB_FP32, NB_FP32_COMP or NB_FP64ACC            */
+    int64_t max_systems;   /* systems per batch (nb_build_tree_batched), >= 1 */
 } nb_config;
 
 typedef struct nb_stats {
@@ -106,6 +107,25 @@ int nb_set_sync_checks(nb_ctx *ctx, int on);
 int nb_build_tree(nb_ctx *ctx, const double *pos_dev, const float *mass_dev,
                   int64_t n);
 
+/* A batch of independent systems in one tree build: particles of system s
+ * are rows offsets[s] .. offsets[s+1] of pos_dev / mass_dev (offsets_dev:
+ * n_systems + 1 int64 on the device, offsets[0] = 0, offsets[n_systems] = n,
+ * every system non-empty, owned by the caller and read during the call).
+ * Each system gets its own root cube and Morton keys; particles are sorted by
+ * (system, key), and cells never span two systems, so the result is a
+ * forest whose trees, in system order, are each the tree nb_build_tree
+ * builds for that system alone (node ids offset by the nodes of the systems
+ * before it).  Walks start at the group's own root; walk, forces and the
+ * leapfrog then run once for the whole batch.  n_systems <= cfg.max_systems.
+ * Errors: as nb_build_tree; INVALID_ARG (reported by the device check of the
+ * offsets when sync_checks is on). */
+int nb_build_tree_batched(nb_ctx *ctx, const double *pos_dev, const float *mass_dev,
+                          const int64_t *offsets_dev, int64_t n_systems, int64_t n);
+/* nb_leapfrog_step for a batch (rebuilding with nb_build_tree_batched). */
+int nb_leapfrog_step_batched(nb_ctx *ctx, double *pos_dev, double *vel_dev,
+                             const float *mass_dev, const int64_t *offsets_dev,
+                             int64_t n_systems, int64_t n, double dt);
+
 /* Form groups (each node with count <= n_crit whose parent holds more) and
  * walk the tree once per group (the walk of Fig. "treewalk_iterative" in
  * group form, breadth-first over a level-ordered copy of the tree), writing
@@ -146,6 +166,29 @@ int nb_leapfrog_step(nb_ctx *ctx, double *pos_dev, double *vel_dev,
 int nb_leapfrog_reset(nb_ctx *ctx);
 /* The accelerations (n x 3 FP32, caller order) kept by the last step. */
 int nb_leapfrog_acc(nb_ctx *ctx, float *acc_dev);
+
+/* Capture nsteps leapfrog steps (offsets_dev NULL: one system; else a batch,
+ * see nb_build_tree_batched) into a CUDA graph held by the context, and
+ * replay it with nb_graph_launch on cfg.stream.  Needs a non-NULL cfg.stream
+ * (the legacy stream cannot be captured) and a previous step of the same n
+ * made with sync_checks on, which sizes the list storage; during replay
+ * nothing synchronises or allocates, and a list that outgrows its slot is
+ * latched as NB_ERR_CAPACITY for nb_sync_status.  pos/vel/mass are the
+ * buffers every replay reads and updates. */
+int nb_graph_capture_leapfrog(nb_ctx *ctx, double *pos_dev, double *vel_dev,
+                              const float *mass_dev, const int64_t *offsets_dev,
+                              int64_t n_systems, int64_t n, double dt, int nsteps);
+int nb_graph_launch(nb_ctx *ctx);
+
+/* Autotuner: builds the tree of (pos_dev, mass_dev), then times `reps` walk +
+ * force passes for every n_crit of the list and both force work-item widths
+ * (32 or 64 targets per warp) with CUDA events, keeps the fastest pair in
+ * the context (cfg.n_crit and the item width used from then on) and returns
+ * it; ms_host (nullable, 2 x ncand) receives the mean times (item width 32,
+ * then 64, per candidate). */
+int nb_autotune(nb_ctx *ctx, const double *pos_dev, const float *mass_dev, int64_t n,
+                float eps, float theta, const int *n_crit_host, int ncand, int reps,
+                int *best_n_crit_host, int *best_rows_host, float *ms_host);
 
 /* FP64 direct sum of Eq. (gravity) for the targets listed in targets_dev
  * (nt indices into 0..n-1; NULL = all n), used as the accuracy judge.

@@ -35,7 +35,8 @@ EXPORTED = [
     "nb_error_string", "nb_set_timing", "nb_get_timing", "nb_morton_order_noalloc", "nb_copy_list", "nb_mlp_workspace_size",
     "nb_mlp_forward", "nb_mlp_grad", "nb_mlp_train", "nb_group_features",
     "nb_walk_groups_learned", "nb_group_errors", "nb_theta_labels",
-    "nb_copy_group_lengths",
+    "nb_copy_group_lengths", "nb_build_tree_batched", "nb_leapfrog_step_batched",
+    "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -47,7 +48,7 @@ class nb_config(C.Structure):
     _fields_ = [("max_n", C.c_int64), ("list_capacity", C.c_int64),
                 ("stream", C.c_void_p), ("sync_checks", C.c_int),
                 ("device", C.c_int), ("eps", C.c_float), ("theta", C.c_float),
-                ("n_crit", C.c_int), ("precision", C.c_int)]
+                ("n_crit", C.c_int), ("precision", C.c_int), ("max_systems", C.c_int64)]
 
 
 class nb_stats(C.Structure):
@@ -95,6 +96,11 @@ def _load():
     L.nb_get_timing.argtypes = [vp, vp, vp, vp]
     L.nb_morton_order_noalloc.argtypes = [vp, i64, vp, vp, vp]
     L.nb_group_features.argtypes = [vp, i32, vp, i64, vp]
+    L.nb_build_tree_batched.argtypes = [vp, vp, vp, vp, i64, i64]
+    L.nb_graph_capture_leapfrog.argtypes = [vp, vp, vp, vp, vp, i64, i64, C.c_double, i32]
+    L.nb_graph_launch.argtypes = [vp]
+    L.nb_autotune.argtypes = [vp, vp, vp, i64, C.c_float, C.c_float, vp, i32, i32, vp, vp, vp]
+    L.nb_leapfrog_step_batched.argtypes = [vp, vp, vp, vp, vp, i64, i64, C.c_double]
     L.nb_copy_group_lengths.argtypes = [vp, vp, i64]
     L.nb_walk_groups_learned.argtypes = [vp, i32, vp, C.c_float, vp]
     L.nb_group_errors.argtypes = [vp, vp, vp, vp, i64, vp, vp]
@@ -152,7 +158,7 @@ class NBody:
 
     def __init__(self, max_n, *, eps=0.01, theta=0.6, n_crit=64,
                  precision="fp32", list_capacity=0, sync_checks=True,
-                 stream=None, device=None):
+                 stream=None, device=None, max_systems=1):
         import torch
         dev = torch.cuda.current_device() if device is None else int(device)
         cfg = nb_config()
@@ -165,6 +171,7 @@ class NBody:
         cfg.theta = float(theta)
         cfg.n_crit = int(n_crit)
         cfg.precision = PRECISION.get(precision, precision)
+        cfg.max_systems = int(max_systems)
         self.cfg = cfg
         self.max_n = int(max_n)
         h = C.c_void_p()
@@ -200,6 +207,54 @@ class NBody:
                                   _dptr(mass, torch.float32, None, "mass"), n),
                "nb_build_tree")
         self.n = n
+        self._nsys = 1
+
+    def build_tree_batched(self, pos, mass, offsets):
+        """offsets: (n_systems + 1,) int64 CUDA tensor of row offsets."""
+        import torch
+        n = int(pos.shape[0])
+        _check(_lib.nb_build_tree_batched(self._h, _dptr(pos, torch.float64, 3, "pos"),
+                                          _dptr(mass, torch.float32, None, "mass"),
+                                          _dptr(offsets, torch.int64, None, "offsets"),
+                                          int(offsets.shape[0]) - 1, n), "nb_build_tree_batched")
+        self.n = n
+        self._nsys = int(offsets.shape[0]) - 1
+
+    def leapfrog_step_batched(self, pos, vel, mass, offsets, dt):
+        import torch
+        _check(_lib.nb_leapfrog_step_batched(self._h, _dptr(pos, torch.float64, 3, "pos"),
+                                             _dptr(vel, torch.float64, 3, "vel"),
+                                             _dptr(mass, torch.float32, None, "mass"),
+                                             _dptr(offsets, torch.int64, None, "offsets"),
+                                             int(offsets.shape[0]) - 1, int(pos.shape[0]),
+                                             float(dt)), "nb_leapfrog_step_batched")
+        self.n = int(pos.shape[0])
+
+    def graph_capture_leapfrog(self, pos, vel, mass, dt, nsteps, offsets=None):
+        import torch
+        nsys = 1 if offsets is None else int(offsets.shape[0]) - 1
+        _check(_lib.nb_graph_capture_leapfrog(
+            self._h, _dptr(pos, torch.float64, 3, "pos"), _dptr(vel, torch.float64, 3, "vel"),
+            _dptr(mass, torch.float32, None, "mass"),
+            _dptr(offsets, torch.int64, None, "offsets"), nsys, int(pos.shape[0]), float(dt),
+            int(nsteps)), "nb_graph_capture_leapfrog")
+
+    def graph_launch(self):
+        _check(_lib.nb_graph_launch(self._h), "nb_graph_launch")
+
+    def autotune(self, pos, mass, eps, theta, n_crits=(32, 64, 128, 256, 512), reps=3):
+        """(best n_crit, best item rows, {(n_crit, rows): ms})."""
+        import torch
+        cand = np.asarray(n_crits, np.int32)
+        ms = np.zeros(2 * len(cand), np.float32)
+        bn, br = C.c_int(0), C.c_int(0)
+        _check(_lib.nb_autotune(self._h, _dptr(pos, torch.float64, 3, "pos"),
+                                _dptr(mass, torch.float32, None, "mass"), int(pos.shape[0]),
+                                float(eps), float(theta), _hptr(cand), len(cand), int(reps),
+                                C.byref(bn), C.byref(br), _hptr(ms)), "nb_autotune")
+        table = {(int(c), r + 1): float(ms[2 * k + r]) for k, c in enumerate(cand) for r in range(2)}
+        self.cfg.n_crit = bn.value
+        return bn.value, br.value, table
 
     def walk_groups(self, theta, n_crit, theta_per_group=None):
         import torch
@@ -277,7 +332,7 @@ class NBody:
     def copy_tree(self) -> dict:
         st = self.stats()
         n, nn = st["n"], st["n_nodes"]
-        d = dict(root=np.zeros(7), keys=np.zeros(n, np.uint64), perm=np.zeros(n, np.int32),
+        d = dict(root=np.zeros(max(7, 8 * getattr(self, "_nsys", 1))), keys=np.zeros(n, np.uint64), perm=np.zeros(n, np.int32),
                  level=np.zeros(nn, np.int32), first=np.zeros(nn, np.int32),
                  count=np.zeros(nn, np.int32), next=np.zeros(nn, np.int32),
                  parent=np.zeros(nn, np.int32), nchild=np.zeros(nn, np.int32),

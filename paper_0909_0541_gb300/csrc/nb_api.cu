@@ -27,6 +27,7 @@ void nb_config_default(nb_config *cfg, int64_t max_n)
     cfg->theta = 0.6f;
     cfg->n_crit = 64;
     cfg->precision = NB_FP32;
+    cfg->max_systems = 1;
 }
 
 const char *nb_error_string(int code)
@@ -55,10 +56,13 @@ static void free_all(nb_ctx *c)
                     c->level_start, c->w_a, c->w_d, c->w_b, c->w_c, c->b_mass, c->b_mx,
                     c->b_com, c->gflag, c->gnode, c->gfirst, c->gcount, c->glen, c->gcells,
                     c->gbox, c->items, c->item_cnt, c->list_id, c->list_xm, c->wq, c->gfeat, c->gtheta,
+                    c->sys_of, c->sys_sorted, c->sys_root, c->skey, c->skey_alt, c->sval,
+                    c->sval_alt,
                     c->acc_cache, c->pot_cache, c->err, c->cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cnt_host) cudaFreeHost(c->cnt_host);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->ev) {
         for (int i = 0; i < 2 * NB_EV_POOL; i++) cudaEventDestroy(c->ev[i]);
         free(c->ev);
@@ -75,6 +79,7 @@ static bool dalloc(T **p, int64_t count)
 
 static int err_code(unsigned bits)
 {
+    if (bits & NB_EF_BADARG) return NB_ERR_INVALID_ARG;
     if (bits & NB_EF_NONFINITE) return NB_ERR_NONFINITE;
     if (bits & NB_EF_WALK) return NB_ERR_WALK_LIMIT;
     if (bits & (NB_EF_CAPACITY | NB_EF_QUEUE)) return NB_ERR_CAPACITY;
@@ -161,7 +166,7 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
     *out = nullptr;
     if (cfg->max_n < 1 || cfg->max_n > (int64_t)150000000 || cfg->n_crit < 1 ||
         !(cfg->theta >= 0.f) || !(cfg->eps >= 0.f) || cfg->precision < 0 ||
-        cfg->precision > 2 || cfg->list_capacity < 0)
+        cfg->precision > 2 || cfg->list_capacity < 0 || cfg->max_systems < 0)
         return NB_ERR_INVALID_ARG;
     nb_ctx *c = new (std::nothrow) nb_ctx();
     if (!c) return NB_ERR_NOMEM;
@@ -192,7 +197,7 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
     c->max_items = N + N / 64 + 2;
     bool ok = dalloc(&c->keys, N) && dalloc(&c->keys_alt, N) && dalloc(&c->idx, N) &&
               dalloc(&c->idx_alt, N) && dalloc(&c->sort_hist, c->sort_hist_len) &&
-              dalloc(&c->scan_bsum, c->scan_bsum_len) && dalloc(&c->root, 8) &&
+              dalloc(&c->scan_bsum, c->scan_bsum_len) &&
               dalloc(&c->bbox_part, 6 * (int64_t)c->bbox_blocks) && dalloc(&c->p_hi, N) &&
               dalloc(&c->p_lo, N) && dalloc(&c->p_x64, 3 * N) && dalloc(&c->perm, N) &&
               dalloc(&c->clev, N) && dalloc(&c->ccount, N + 1) && dalloc(&c->cstart, N + 1) &&
@@ -205,6 +210,7 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
               dalloc(&c->b_com, 3 * NN) && dalloc(&c->gflag, NN + 1) && dalloc(&c->gnode, N) &&
               dalloc(&c->gfirst, N) && dalloc(&c->gcount, N) && dalloc(&c->glen, N) &&
               dalloc(&c->gcells, N) && dalloc(&c->gbox, 3 * N) &&
+              dalloc(&c->root, 8 * (cfg->max_systems > 1 ? cfg->max_systems : 1)) &&
               dalloc(&c->gfeat, 16 * N) && dalloc(&c->gtheta, N) &&
               dalloc(&c->items, 2 * c->max_items) && dalloc(&c->item_cnt, N + 1) &&
               dalloc(&c->acc_cache, 3 * N) && dalloc(&c->pot_cache, N) &&
@@ -223,6 +229,18 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
         free_all(c);
         delete c;
         return NB_ERR_CUDA;
+    }
+    c->nsys = 1;
+    c->item_rows = 2;
+    c->max_sys = cfg->max_systems > 1 ? cfg->max_systems : 1;
+    if (c->max_sys > 1 &&
+        !(dalloc(&c->sys_of, N) && dalloc(&c->sys_sorted, N) && dalloc(&c->sys_root, c->max_sys) &&
+          dalloc(&c->skey, N) && dalloc(&c->skey_alt, N) && dalloc(&c->sval, N) &&
+          dalloc(&c->sval_alt, N))) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return NB_ERR_NOMEM;
     }
     c->list_cap = cfg->list_capacity;
     c->walk_warps = nb_walk_warps(c);
@@ -260,6 +278,7 @@ int nb_build_tree(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     c->has_groups = 0;
     c->has_lists = 0;
     c->n = n;
+    c->nsys = 1;
     if (n == 0) {
         CK(cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_PP_CUM, c->stream));
         c->has_tree = 1;
@@ -267,6 +286,26 @@ int nb_build_tree(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     }
     const int tk = phase_begin(c);
     nb_launch_build(c, pos, mass, n);
+    phase_end(c, tk, NB_PHASE_BUILD);
+    c->has_tree = 1;
+    return finish(c);
+}
+
+int nb_build_tree_batched(nb_ctx *c, const double *pos, const float *mass,
+                          const int64_t *offsets, int64_t nsys, int64_t n)
+{
+    if (!c || n < 1 || n > c->max_n || nsys < 1 || nsys > c->max_sys || nsys > n || !pos ||
+        !mass || !offsets)
+        return NB_ERR_INVALID_ARG;
+    c->has_tree = 0;
+    c->has_groups = 0;
+    c->has_lists = 0;
+    c->n = n;
+    c->nsys = nsys;
+    c->sys_off = offsets;
+    const int tk = phase_begin(c);
+    if (nsys == 1) nb_launch_build(c, pos, mass, n);
+    else nb_launch_build_batched(c, pos, mass, n, offsets, nsys);
     phase_end(c, tk, NB_PHASE_BUILD);
     c->has_tree = 1;
     return finish(c);
@@ -438,24 +477,25 @@ int nb_leapfrog_acc(nb_ctx *c, float *acc)
     return finish(c);
 }
 
-static int force_pass(nb_ctx *c, const double *pos, const float *mass, int64_t n)
+static int force_pass(nb_ctx *c, const double *pos, const float *mass, int64_t n,
+                      const int64_t *off = nullptr, int64_t nsys = 1)
 {
-    int rc = nb_build_tree(c, pos, mass, n);
+    int rc = off ? nb_build_tree_batched(c, pos, mass, off, nsys, n) : nb_build_tree(c, pos, mass, n);
     if (rc) return rc;
     rc = nb_walk_groups(c, c->cfg.theta, c->cfg.n_crit, nullptr);
     if (rc) return rc;
     return nb_forces(c, c->cfg.eps, c->acc_cache, c->pot_cache, c->cfg.precision);
 }
 
-int nb_leapfrog_step(nb_ctx *c, double *pos, double *vel, const float *mass, int64_t n,
-                     double dt)
+static int leapfrog(nb_ctx *c, double *pos, double *vel, const float *mass, int64_t n,
+                    double dt, const int64_t *off, int64_t nsys)
 {
     if (!c || n < 0 || n > c->max_n || (n > 0 && (!pos || !vel || !mass)) || !isfinite(dt))
         return NB_ERR_INVALID_ARG;
     if (n == 0) return NB_OK;
     int rc;
     if (!c->acc_valid || c->n != n) {
-        rc = force_pass(c, pos, mass, n);
+        rc = force_pass(c, pos, mass, n, off, nsys);
         if (rc) return rc;
         c->acc_valid = 1;
     }
@@ -464,7 +504,7 @@ int nb_leapfrog_step(nb_ctx *c, double *pos, double *vel, const float *mass, int
     nb_launch_kick(c, vel, c->acc_cache, n, h);
     nb_launch_drift(c, pos, vel, n, dt);
     phase_end(c, tk, NB_PHASE_INTEGRATE);
-    rc = force_pass(c, pos, mass, n);
+    rc = force_pass(c, pos, mass, n, off, nsys);
     if (rc) {
         c->acc_valid = 0;
         return rc;
@@ -473,6 +513,112 @@ int nb_leapfrog_step(nb_ctx *c, double *pos, double *vel, const float *mass, int
     nb_launch_kick(c, vel, c->acc_cache, n, h);
     phase_end(c, tk, NB_PHASE_INTEGRATE);
     return finish(c);
+}
+
+int nb_leapfrog_step(nb_ctx *c, double *pos, double *vel, const float *mass, int64_t n,
+                     double dt)
+{
+    return leapfrog(c, pos, vel, mass, n, dt, nullptr, 1);
+}
+
+int nb_leapfrog_step_batched(nb_ctx *c, double *pos, double *vel, const float *mass,
+                             const int64_t *offsets, int64_t nsys, int64_t n, double dt)
+{
+    if (!offsets || nsys < 1) return NB_ERR_INVALID_ARG;
+    return leapfrog(c, pos, vel, mass, n, dt, offsets, nsys);
+}
+
+int nb_graph_capture_leapfrog(nb_ctx *c, double *pos, double *vel, const float *mass,
+                              const int64_t *offsets, int64_t nsys, int64_t n, double dt,
+                              int nsteps)
+{
+    if (!c || !c->stream || nsteps < 1 || n < 1 || (offsets && nsys < 1)) return NB_ERR_INVALID_ARG;
+    if (!c->acc_valid || c->n != n || c->list_cap < 1 || !c->list_id) return NB_ERR_STATE;
+    CK(cudaStreamSynchronize(c->stream));
+    const int sync = c->sync_checks, timing = c->timing;
+    c->sync_checks = 0;
+    c->timing = 0;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    int rc = NB_OK;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = NB_ERR_CUDA;
+    } else {
+        for (int k = 0; k < nsteps && rc == NB_OK; k++)
+            rc = leapfrog(c, pos, vel, mass, n, dt, offsets, offsets ? nsys : 1);
+        if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess && rc == NB_OK) rc = NB_ERR_CUDA;
+        if (rc == NB_OK && cudaGraphInstantiate(&c->graph_exec, graph, 0) != cudaSuccess)
+            rc = NB_ERR_CUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    c->sync_checks = sync;
+    c->timing = timing;
+    if (rc) {
+        cudaGetLastError();
+        c->graph_exec = nullptr;
+    }
+    return rc;
+}
+
+int nb_graph_launch(nb_ctx *c)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!c->graph_exec) return NB_ERR_STATE;
+    CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    return finish(c);
+}
+
+int nb_autotune(nb_ctx *c, const double *pos, const float *mass, int64_t n, float eps,
+                float theta, const int *n_crit, int ncand, int reps, int *best_n_crit,
+                int *best_rows, float *ms_out)
+{
+    if (!c || !pos || !mass || !n_crit || ncand < 1 || reps < 1 || n < 1) return NB_ERR_INVALID_ARG;
+    int rc = nb_build_tree(c, pos, mass, n);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int sync = c->sync_checks, rows0 = c->item_rows;
+    float best = INFINITY;
+    int bn = n_crit[0], br = rows0;
+    for (int k = 0; k < ncand && rc == NB_OK; k++)
+        for (int rows = 1; rows <= 2 && rc == NB_OK; rows++) {
+            c->item_rows = rows;
+            c->sync_checks = 1;
+            rc = nb_walk_groups(c, theta, n_crit[k], nullptr);   // sizes the lists
+            if (rc) break;
+            rc = nb_forces(c, eps, c->acc_cache, nullptr, NB_FP32);
+            if (rc) break;
+            c->sync_checks = 0;
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < reps && rc == NB_OK; r++) {
+                rc = nb_walk_groups(c, theta, n_crit[k], nullptr);
+                if (!rc) rc = nb_forces(c, eps, c->acc_cache, nullptr, NB_FP32);
+            }
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = NB_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms_out) ms_out[2 * k + rows - 1] = ms;
+            if (ms < best) { best = ms; bn = n_crit[k]; br = rows; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->sync_checks = sync;
+    if (rc) {
+        c->item_rows = rows0;
+        return rc;
+    }
+    c->item_rows = br;
+    c->cfg.n_crit = bn;
+    c->acc_valid = 0;
+    if (best_n_crit) *best_n_crit = bn;
+    if (best_rows) *best_rows = br;
+    return sync_read(c);
 }
 
 int nb_direct_sum(const double *pos, const float *mass, int64_t n, double eps,
@@ -567,7 +713,10 @@ int nb_copy_tree(nb_ctx *c, double *root, uint64_t *keys, int32_t *perm, int32_t
     if (rc) return rc;
     const int64_t nn = c->n > 0 ? c->cnt_host[CNT_NODES] : 0;
     const int64_t n = c->n;
-    if (n > 0) D2H(root, c->root, 7);
+    if (n > 0) {
+        if (c->nsys == 1) D2H(root, c->root, 7);
+        else D2H(root, c->root, 8 * c->nsys);
+    }
     D2H(keys, c->keys, n);
     D2H(perm, c->perm, n);
     D2H(level, c->n_level, nn);

@@ -41,6 +41,7 @@
 #define NB_EF_CAPACITY 2u
 #define NB_EF_WALK 4u
 #define NB_EF_QUEUE 8u
+#define NB_EF_BADARG 16u
 
 // device counters (int64 slots of ctx->cnt)
 enum {
@@ -85,7 +86,17 @@ struct nb_ctx {
     int32_t *scan_bsum;
     int64_t scan_bsum_len;
 
-    // root: centre[3], L, corner[3], 2^21 / L; bbox partials
+    // batches of independent systems: system of each particle (caller and
+    // sorted order), system offsets (caller-owned, device), root node of each
+    // system in level order; nsys = 1 for a single system
+    int64_t nsys, max_sys;
+    int32_t *sys_of, *sys_sorted, *sys_root;
+    const int64_t *sys_off;
+    uint64_t *skey, *skey_alt;
+    uint32_t *sval, *sval_alt;
+
+    // roots: per system centre[3], L, corner[3], 2^21 / L (8 doubles each);
+    // bbox partials
     double *root;
     double *bbox_part;
     int bbox_blocks;
@@ -118,6 +129,7 @@ struct nb_ctx {
     int32_t *gnode, *gfirst, *gcount, *glen, *gcells;
     float4 *gbox;     // 3 per group
     int32_t *items;   // force work items: (group, first member | one-warp-row flag)
+    int item_rows;    // targets per item: 32 x item_rows (1 or 2)
     int32_t *item_cnt;
     int64_t max_items;
 
@@ -137,6 +149,9 @@ struct nb_ctx {
 
     // leapfrog
     float *acc_cache, *pot_cache;
+
+    // captured leapfrog steps
+    cudaGraphExec_t graph_exec;
 
     // timing and launch accounting
     int timing;
@@ -160,11 +175,15 @@ void nb_exclusive_scan_raw(const int32_t *in, int32_t *out, int64_t n_max, int32
                            cudaStream_t s);
 void nb_radix_sort_raw(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uint32_t *idx_alt,
                        uint32_t *hist, int32_t *bsum, int64_t n, cudaStream_t s);
+void nb_radix_sort_passes(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uint32_t *idx_alt,
+                          uint32_t *hist, int32_t *bsum, int64_t n, int passes, cudaStream_t s);
 
 // nb_tree.cu
 void nb_launch_keys_raw(const double *pos, int64_t n, double *part, int nblk, double *root,
                         uint64_t *keys, uint32_t *idx, unsigned *err, cudaStream_t s);
 void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n);
+void nb_launch_build_batched(nb_ctx *c, const double *pos, const float *mass, int64_t n,
+                             const int64_t *offsets, int64_t nsys);
 void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g);
 
 // nb_walk.cu

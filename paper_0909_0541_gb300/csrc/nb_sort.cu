@@ -256,11 +256,19 @@ void nb_exclusive_scan_raw(const int32_t *in, int32_t *out, int64_t n_max, int32
 void nb_radix_sort_raw(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uint32_t *idx_alt,
                        uint32_t *hist, int32_t *bsum, int64_t n, cudaStream_t s)
 {
+    nb_radix_sort_passes(keys, keys_alt, idx, idx_alt, hist, bsum, n, 8, s);
+}
+
+// `passes` (even) 8-bit passes from the lowest digit; the result is back in
+// keys / idx
+void nb_radix_sort_passes(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uint32_t *idx_alt,
+                          uint32_t *hist, int32_t *bsum, int64_t n, int passes, cudaStream_t s)
+{
     if (n <= 1) return;
     const int nb = (int)((n + RS_TILE - 1) / RS_TILE);
     uint64_t *ka = keys, *kb = keys_alt;
     uint32_t *va = idx, *vb = idx_alt;
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = 0; pass < passes; pass++) {
         const int shift = 8 * pass;
         k_rs_hist<<<nb, RS_T, 0, s>>>(ka, n, shift, hist, nb);
         nb_exclusive_scan_raw((const int32_t *)hist, (int32_t *)hist, (int64_t)256 * nb, bsum, s);

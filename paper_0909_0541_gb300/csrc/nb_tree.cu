@@ -130,11 +130,12 @@ __device__ __forceinline__ uint32_t grid_coord(double x, double corner, double s
 }
 
 __global__ void __launch_bounds__(256)
-k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ root,
-       uint64_t *__restrict__ key, uint32_t *__restrict__ idx)
+k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ roots,
+       const int32_t *__restrict__ sys_of, uint64_t *__restrict__ key, uint32_t *__restrict__ idx)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double *root = roots + (sys_of ? 8 * (int64_t)sys_of[i] : 0);
     const double sc = root[7];
     const uint32_t qx = grid_coord(pos[3 * i], root[4], sc);
     const uint32_t qy = grid_coord(pos[3 * i + 1], root[5], sc);
@@ -174,14 +175,15 @@ __device__ __forceinline__ int common_levels(uint64_t a, uint64_t b)
     return (__clzll((long long)x) - 1) / 3;
 }
 
+// (neighbours in different systems share no cell)
 __global__ void __launch_bounds__(256)
-k_levels(const uint64_t *__restrict__ key, int64_t n, int8_t *__restrict__ clev,
-         int32_t *__restrict__ ccount)
+k_levels(const uint64_t *__restrict__ key, int64_t n, const int32_t *__restrict__ sys,
+         int8_t *__restrict__ clev, int32_t *__restrict__ ccount)
 {
     const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a >= n) return;
-    const int ca = a + 1 < n ? common_levels(key[a], key[a + 1]) : -1;
-    const int cp = a > 0 ? common_levels(key[a - 1], key[a]) : -1;
+    const int ca = a + 1 < n && (!sys || sys[a] == sys[a + 1]) ? common_levels(key[a], key[a + 1]) : -1;
+    const int cp = a > 0 && (!sys || sys[a - 1] == sys[a]) ? common_levels(key[a - 1], key[a]) : -1;
     clev[a] = (int8_t)ca;
     ccount[a] = ca > cp ? ca - cp : 0;
 }
@@ -192,10 +194,14 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
         int32_t *__restrict__ n_level, int32_t *__restrict__ n_first,
         int32_t *__restrict__ n_count, int32_t *__restrict__ n_parent,
         int32_t *__restrict__ n_nchild, int8_t *__restrict__ n_depth,
-        long long *__restrict__ cnt)
+        long long *__restrict__ cnt, const int32_t *__restrict__ sys,
+        const int64_t *__restrict__ sys_off)
 {
     const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a >= n) return;
+    // cells never reach past the particle's system (sorted rows of system s
+    // are the caller's rows sys_off[s] .. sys_off[s+1])
+    const int64_t nend = sys ? sys_off[sys[a] + 1] : n;
     const int32_t C = cstart[n];
     const int32_t total = C + (int32_t)n;
     if (a == 0) cnt[CNT_NODES] = total;
@@ -213,7 +219,7 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
     n_nchild[leaf] = 0;
     n_depth[leaf] = (int8_t)((ca > cp ? ca : cp) + 1);
     if (k > 0) n_parent[leaf] = leaf - 1;
-    else if (leaf == 0) n_parent[leaf] = -1;
+    else if (ca < 0 && cp < 0) n_parent[leaf] = -1;   // a one-particle system
 
     // cells starting at a, deepest first; each run contains the deeper one
     const uint64_t ka = key[a];
@@ -224,12 +230,12 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
         const int shift = 63 - 3 * lev;
         const uint64_t P = ka >> shift;
         int64_t lo = b, step = 1, hi = b + 1;
-        while (hi < n && (key[hi] >> shift) == P) {
+        while (hi < nend && (key[hi] >> shift) == P) {
             lo = hi;
             step <<= 1;
             hi = lo + step;
         }
-        if (hi > n) hi = n;
+        if (hi > nend) hi = nend;
         while (hi - lo > 1) {
             const int64_t mid = lo + ((hi - lo) >> 1);
             if ((key[mid] >> shift) == P) lo = mid; else hi = mid;
@@ -241,7 +247,7 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
         n_count[id] = (int32_t)(b - a + 1);
         n_depth[id] = (int8_t)lev;
         if (lev > cp + 1) n_parent[id] = id - 1;
-        else if (id == 0) n_parent[id] = -1;
+        else if (cp < 0) n_parent[id] = -1;   // a system's root
         if (lev > maxlev) maxlev = lev;
     }
     if (maxlev >= 0) atomicMax(&cnt[CNT_MAXLEVEL], (long long)maxlev);
@@ -395,18 +401,19 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
 __global__ void __launch_bounds__(256)
 k_moments_level(int depth, const int32_t *__restrict__ level_start,
                 const uint64_t *__restrict__ key, const int32_t *__restrict__ n_first,
-                const double *__restrict__ root, const int4 *__restrict__ w_b,
+                const double *__restrict__ roots, const int32_t *__restrict__ sys,
+                const int4 *__restrict__ w_b,
                 float4 *__restrict__ w_a, float4 *__restrict__ w_d, float2 *__restrict__ w_c,
                 double *__restrict__ b_mass, double *__restrict__ b_mx,
                 double *__restrict__ b_com)
 {
     const int32_t lo_b = level_start[depth], hi_b = level_start[depth + 1];
-    const double L = root[3];
-    const double lc = ldexp(L, -depth);
     for (int32_t b = lo_b + blockIdx.x * blockDim.x + threadIdx.x; b < hi_b;
          b += gridDim.x * blockDim.x) {
         const int4 wb = w_b[b];
         if (wb.z < 0) continue;
+        const double *root = roots + (sys ? 8 * (int64_t)sys[n_first[wb.x]] : 0);
+        const double lc = ldexp(root[3], -depth);
         double M = 0.0, mx[3] = {0.0, 0.0, 0.0};
         for (int32_t k = 0; k < wb.w; k++) {
             const int64_t ch = wb.z + k;
@@ -438,6 +445,9 @@ k_moments_level(int depth, const int32_t *__restrict__ level_start,
     }
 }
 
+static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t n,
+                       const int32_t *sys_sorted);
+
 void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
 {
     cudaStream_t s = c->stream;
@@ -446,18 +456,164 @@ void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     c->launches++;
     k_root<<<1, 256, 0, s>>>(c->bbox_part, c->bbox_blocks, c->root);
     c->launches++;
-    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, c->keys, c->idx);
+    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, nullptr, c->keys, c->idx);
     c->launches++;
     nb_radix_sort(c, n);
+    build_tail(c, pos, mass, n, nullptr);
+}
+
+// ------------------------------------------------------------ batches
+// system of every particle from the (caller-owned) offsets; checks them
+__global__ void __launch_bounds__(256)
+k_sys_of(const int64_t *__restrict__ off, int64_t nsys, int64_t n, int32_t *__restrict__ sys_of,
+         unsigned *__restrict__ err)
+{
+    for (int64_t sy = blockIdx.x; sy < nsys; sy += gridDim.x) {
+        const int64_t a = off[sy], b = off[sy + 1];
+        if (threadIdx.x == 0 && (!(b > a) || a < 0 || b > n || (sy == 0 && a != 0) ||
+                                 (sy == nsys - 1 && b != n)))
+            atomicOr(err, NB_EF_BADARG);
+        const int64_t lo = a < 0 ? 0 : a, hi = b > n ? n : b;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) sys_of[i] = (int32_t)sy;
+    }
+}
+
+// bounding box and root cube of each system (one block per system), the
+// same arithmetic as k_bbox + k_root
+__global__ void __launch_bounds__(256)
+k_roots_sys(const double *__restrict__ pos, const int64_t *__restrict__ off, int64_t nsys,
+            int64_t n, double *__restrict__ roots, unsigned *__restrict__ err)
+{
+    __shared__ double s[8][6];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t sy = blockIdx.x; sy < nsys; sy += gridDim.x) {
+        int64_t a = off[sy], b = off[sy + 1];
+        a = a < 0 ? 0 : (a > n ? n : a);
+        b = b < a ? a : (b > n ? n : b);
+        double lo[3], hi[3];
+        for (int k = 0; k < 3; k++) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+        bool bad = false;
+        for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x)
+            for (int k = 0; k < 3; k++) {
+                const double x = pos[3 * i + k];
+                bad |= !isfinite(x);
+                lo[k] = fmin(lo[k], x);
+                hi[k] = fmax(hi[k], x);
+            }
+        if (bad) atomicOr(err, NB_EF_NONFINITE);
+        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < 3; k++) {
+                lo[k] = fmin(lo[k], __shfl_down_sync(0xffffffffu, lo[k], o));
+                hi[k] = fmax(hi[k], __shfl_down_sync(0xffffffffu, hi[k], o));
+            }
+        if (lane == 0)
+            for (int k = 0; k < 3; k++) { s[w][k] = lo[k]; s[w][3 + k] = hi[k]; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int ww = 1; ww < (int)(blockDim.x >> 5); ww++)
+                for (int k = 0; k < 3; k++) {
+                    s[0][k] = fmin(s[0][k], s[ww][k]);
+                    s[0][3 + k] = fmax(s[0][3 + k], s[ww][3 + k]);
+                }
+            double *root = roots + 8 * sy;
+            double ext = 0.0;
+            for (int k = 0; k < 3; k++) {
+                root[k] = __dmul_rn(0.5, __dadd_rn(s[0][k], s[0][3 + k]));
+                const double e = __dsub_rn(s[0][3 + k], s[0][k]);
+                if (e > ext) ext = e;
+            }
+            double L = __dmul_rn(ext, 1.0 + 0x1p-20);
+            if (!(L > 0.0)) L = 1.0;
+            root[3] = L;
+            for (int k = 0; k < 3; k++) root[4 + k] = __dsub_rn(root[k], __dmul_rn(0.5, L));
+            root[7] = __ddiv_rn(2097152.0, L);
+        }
+        __syncthreads();
+    }
+}
+
+// second sort key: the system of each Morton-sorted particle
+__global__ void __launch_bounds__(256)
+k_sys_key(const uint32_t *__restrict__ idx, const int32_t *__restrict__ sys_of, int64_t n,
+          uint64_t *__restrict__ skey, uint32_t *__restrict__ sval)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    skey[i] = (uint64_t)sys_of[idx[i]];
+    sval[i] = (uint32_t)i;
+}
+
+// apply the (system)-stable order to the Morton-sorted keys
+__global__ void __launch_bounds__(256)
+k_sys_apply(const uint64_t *__restrict__ key, const uint32_t *__restrict__ idx,
+            const uint64_t *__restrict__ skey, const uint32_t *__restrict__ sval, int64_t n,
+            uint64_t *__restrict__ key_out, uint32_t *__restrict__ idx_out,
+            int32_t *__restrict__ sys_sorted)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = sval[i];
+    key_out[i] = key[j];
+    idx_out[i] = idx[j];
+    sys_sorted[i] = (int32_t)skey[i];
+}
+
+// level-order index of every system's root (depth-0 nodes)
+__global__ void __launch_bounds__(256)
+k_sys_roots(const int32_t *__restrict__ level_start, const int32_t *__restrict__ bfs2pid,
+            const int32_t *__restrict__ n_first, const int32_t *__restrict__ sys_sorted,
+            int32_t *__restrict__ sys_root)
+{
+    const int32_t nr = level_start[1];
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nr; b += gridDim.x * blockDim.x)
+        sys_root[sys_sorted[n_first[bfs2pid[b]]]] = b;
+}
+
+void nb_launch_build_batched(nb_ctx *c, const double *pos, const float *mass, int64_t n,
+                             const int64_t *off, int64_t nsys)
+{
+    cudaStream_t s = c->stream;
+    cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_PP_CUM, s);
+    const int gs = (int)(nsys < 65535 ? nsys : 65535);
+    k_sys_of<<<gs, 256, 0, s>>>(off, nsys, n, c->sys_of, c->err);
+    c->launches++;
+    k_roots_sys<<<gs, 256, 0, s>>>(pos, off, nsys, n, c->root, c->err);
+    c->launches++;
+    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, c->sys_of, c->keys, c->idx);
+    c->launches++;
+    nb_radix_sort(c, n);
+    // stable by system on top of the Morton order: (system, key) order
+    k_sys_key<<<nb_grid(n, 256), 256, 0, s>>>(c->idx, c->sys_of, n, c->skey, c->sval);
+    c->launches++;
+    nb_radix_sort_passes(c->skey, c->skey_alt, c->sval, c->sval_alt, c->sort_hist, c->scan_bsum,
+                         n, 2, s);
+    c->launches += 2 * 5;
+    k_sys_apply<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, c->idx, c->skey, c->sval, n,
+                                                c->keys_alt, c->idx_alt, c->sys_sorted);
+    c->launches++;
+    uint64_t *tk = c->keys; c->keys = c->keys_alt; c->keys_alt = tk;
+    uint32_t *ti = c->idx; c->idx = c->idx_alt; c->idx_alt = ti;
+    build_tail(c, pos, mass, n, c->sys_sorted);
+    k_sys_roots<<<nb_grid(nsys, 256, c->num_sms * 4), 256, 0, s>>>(c->level_start, c->bfs2pid,
+                                                                    c->n_first, c->sys_sorted,
+                                                                    c->sys_root);
+    c->launches++;
+}
+
+static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t n,
+                       const int32_t *sys_sorted)
+{
+    cudaStream_t s = c->stream;
     k_gather<<<nb_grid(n, 256), 256, 0, s>>>(pos, mass, n, c->idx, c->perm, c->p_x64,
                                              c->p_hi, c->p_lo);
     c->launches++;
-    k_levels<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, n, c->clev, c->ccount);
+    k_levels<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, n, sys_sorted, c->clev, c->ccount);
     c->launches++;
     nb_exclusive_scan(c, c->ccount, c->cstart, n, nullptr, &c->cnt[CNT_CELLS]);
     k_cells<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, n, c->clev, c->cstart, c->node_c,
                                             c->n_level, c->n_first, c->n_count, c->n_parent,
-                                            c->n_nchild, c->n_depth, c->cnt);
+                                            c->n_nchild, c->n_depth, c->cnt, sys_sorted,
+                                            c->sys_off);
     c->launches++;
     const int gcap = c->num_sms * 16;
     k_parents<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(c->node_c, c->cnt, c->n_parent,
@@ -480,7 +636,7 @@ void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     const int gl = c->num_sms * 8;
     for (int d = NB_LEVELS; d >= 0; d--) {
         k_moments_level<<<gl, 256, 0, s>>>(d, c->level_start, c->keys, c->n_first, c->root,
-                                           c->w_b, c->w_a, c->w_d, c->w_c, c->b_mass, c->b_mx,
+                                           sys_sorted, c->w_b, c->w_a, c->w_d, c->w_c, c->b_mass, c->b_mx,
                                            c->b_com);
         c->launches++;
     }
@@ -523,7 +679,7 @@ __global__ void __launch_bounds__(256)
 k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gcount,
               const float4 *__restrict__ p_hi, const long long *__restrict__ cnt,
               float theta, const float *__restrict__ theta_g, float4 *__restrict__ gbox,
-              int32_t *__restrict__ item_cnt)
+              int32_t *__restrict__ item_cnt, int iblock)
 {
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G;
@@ -544,19 +700,19 @@ k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gc
         gbox[3 * (int64_t)g] = make_float4(lx, ly, lz, 0.0f);
         gbox[3 * (int64_t)g + 1] = make_float4(hx, hy, hz, 0.0f);
         gbox[3 * (int64_t)g + 2] = make_float4(cx, cy, cz, invth);
-        item_cnt[g] = (m + NB_IBLOCK - 1) / NB_IBLOCK;
+        item_cnt[g] = (m + iblock - 1) / iblock;
     }
 }
 
 __global__ void __launch_bounds__(256)
 k_items(const int32_t *__restrict__ item_off, const int32_t *__restrict__ gcount,
-        const long long *__restrict__ cnt, int32_t *__restrict__ items)
+        const long long *__restrict__ cnt, int32_t *__restrict__ items, int iblock)
 {
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G;
          g += gridDim.x * blockDim.x) {
         const int32_t o = item_off[g], m = gcount[g];
-        for (int32_t i0 = 0, k = 0; i0 < m; i0 += NB_IBLOCK, k++) {
+        for (int32_t i0 = 0, k = 0; i0 < m; i0 += iblock, k++) {
             items[2 * (int64_t)(o + k)] = g;
             // bit 30: the item's targets fit one 32-wide row
             items[2 * (int64_t)(o + k) + 1] = i0 | (m - i0 <= NB_WARP ? (1 << 30) : 0);
@@ -577,12 +733,13 @@ void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
         c->gflag, c->n_first, c->n_count, c->cnt, c->gnode, c->gfirst, c->gcount);
     c->launches++;
     k_group_boxes<<<nb_grid(c->max_n, 256, gcap), 256, 0, s>>>(
-        c->gfirst, c->gcount, c->p_hi, c->cnt, theta, theta_g, c->gbox, c->item_cnt);
+        c->gfirst, c->gcount, c->p_hi, c->cnt, theta, theta_g, c->gbox, c->item_cnt,
+        c->item_rows * NB_WARP);
     c->launches++;
     nb_exclusive_scan(c, c->item_cnt, c->item_cnt, c->max_n, &c->cnt[CNT_GROUPS],
                       &c->cnt[CNT_ITEMS]);
     k_items<<<nb_grid(c->max_n, 256, gcap), 256, 0, s>>>(c->item_cnt, c->gcount, c->cnt,
-                                                          c->items);
+                                                          c->items, c->item_rows * NB_WARP);
     c->launches++;
 }
 
@@ -593,5 +750,5 @@ void nb_launch_keys_raw(const double *pos, int64_t n, double *part, int nblk, do
 {
     k_bbox<<<nblk, 256, 0, s>>>(pos, n, part, err);
     k_root<<<1, 256, 0, s>>>(part, nblk, root);
-    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, root, keys, idx);
+    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, root, nullptr, keys, idx);
 }

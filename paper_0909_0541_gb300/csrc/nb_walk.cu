@@ -59,7 +59,9 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
        long long *__restrict__ cnt, int32_t *__restrict__ glen, int32_t *__restrict__ gcells,
        int32_t *__restrict__ list_id, float4 *__restrict__ list_xm, int64_t cap, int64_t alloc,
        int32_t *__restrict__ wq, int64_t wq_cap, unsigned *__restrict__ err,
-       float *__restrict__ feat, const double *__restrict__ root, const int8_t *__restrict__ n_depth)
+       float *__restrict__ feat, const double *__restrict__ roots, const int8_t *__restrict__ n_depth,
+       const int32_t *__restrict__ gfirst, const int32_t *__restrict__ sys_sorted,
+       const int32_t *__restrict__ sys_root)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -87,7 +89,9 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
         int32_t len = 0, ncell = 0;
         float dmin = INFINITY, dmax = 0.0f, dsum = 0.0f;
         int32_t *qin = qa, *qout = qb;
-        if (lane == 0) qin[0] = 0;   // the root
+        // the root of the group's system (node 0 for a single system)
+        const int32_t gsys = sys_sorted ? sys_sorted[gfirst[g]] : 0;
+        if (lane == 0) qin[0] = sys_root ? sys_root[gsys] : 0;
         __syncwarp();
         int32_t na = 1;
         int depth_guard = 0;
@@ -167,6 +171,7 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
                 dsum += __shfl_xor_sync(FULL, dsum, o);
             }
             if (lane < 16) {
+                const double *root = roots + 8 * (int64_t)gsys;
                 const float L = (float)root[3];
                 const float ng = (float)gcount[g];
                 const float sx = (bhi.x - blo.x) / L, sy = (bhi.y - blo.y) / L,
@@ -236,7 +241,8 @@ void nb_launch_walk(nb_ctx *c)
     k_walk<false><<<blocks, WALK_T, 0, c->stream>>>(
         c->w_a, c->w_d, c->w_b, c->w_c, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
         c->glen, c->gcells, c->list_id, c->list_xm, c->list_cap, c->list_alloc, c->wq,
-        c->wq_cap, c->err, nullptr, c->root, c->n_depth);
+        c->wq_cap, c->err, nullptr, c->root, c->n_depth, c->gfirst,
+        c->nsys > 1 ? c->sys_sorted : nullptr, c->nsys > 1 ? c->sys_root : nullptr);
     c->launches++;
 }
 
@@ -249,6 +255,7 @@ void nb_launch_probe(nb_ctx *c, float *feat)
     k_walk<true><<<blocks, WALK_T, 0, c->stream>>>(
         c->w_a, c->w_d, c->w_b, c->w_c, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
         c->glen, c->gcells, nullptr, nullptr, 0, 0, c->wq, c->wq_cap, c->err, feat, c->root,
-        c->n_depth);
+        c->n_depth, c->gfirst, c->nsys > 1 ? c->sys_sorted : nullptr,
+        c->nsys > 1 ? c->sys_root : nullptr);
     c->launches++;
 }
