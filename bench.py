@@ -291,6 +291,9 @@ def run_ours(args, ws, rank, local):
     vel0 = torch.from_numpy(ps.vel).to(dev)
     mass = torch.from_numpy(ps.mass).to(dev)
     pos, vel = pos0.clone(), vel0.clone()
+    # the copies above ran on torch's current stream; the context's stream
+    # must not read pos / vel before they land
+    stream.wait_stream(torch.cuda.current_stream(dev))
     dt = w["dt"]
     with torch.cuda.stream(stream):
         # first step synchronises: sizes the interaction-list storage

@@ -37,6 +37,10 @@ extern "C" {
 #define NB_ERR_NONFINITE (-5)   /* a position is NaN or infinite           */
 #define NB_ERR_STATE (-6)       /* call order: build, then walk, then force */
 #define NB_ERR_NOMEM (-7)       /* device allocation failed                */
+#define NB_ERR_INTERNAL (-8)    /* a kernel's own bounds check fired: the
+                                   access was skipped, results are invalid
+                                   (a library defect; NB_DEBUG_SYNC=1 in the
+                                   environment names the kernel and site)   */
 
 /* accumulation modes of nb_forces */
 #define NB_FP32 0      /* plain FP32 sums                                   */

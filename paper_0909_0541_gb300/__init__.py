@@ -18,7 +18,7 @@ from . import build as _build
 NB_OK = 0
 NB_ERR = {
     -1: "INVALID_ARG", -2: "CUDA", -3: "CAPACITY", -4: "WALK_LIMIT",
-    -5: "NONFINITE", -6: "STATE", -7: "NOMEM",
+    -5: "NONFINITE", -6: "STATE", -7: "NOMEM", -8: "INTERNAL",
 }
 NB_FP32, NB_FP32_COMP, NB_FP64ACC = 0, 1, 2
 PRECISION = {"fp32": NB_FP32, "fp32_comp": NB_FP32_COMP, "fp64acc": NB_FP64ACC}

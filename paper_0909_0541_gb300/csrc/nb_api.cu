@@ -1,6 +1,7 @@
 // nb_api.cu -- the C ABI declared in include/nb.h: context and storage,
 // argument checks, the order of kernel launches, status and debug export.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -41,6 +42,7 @@ const char *nb_error_string(int code)
     case NB_ERR_NONFINITE: return "non-finite position";
     case NB_ERR_STATE: return "call order: build the tree, then walk, then force";
     case NB_ERR_NOMEM: return "device allocation failed";
+    case NB_ERR_INTERNAL: return "a kernel's bounds self-check fired";
     default: return "unknown error";
     }
 }
@@ -49,18 +51,13 @@ const char *nb_error_string(int code)
 
 static void free_all(nb_ctx *c)
 {
-    void *ptrs[] = {c->keys, c->keys_alt, c->idx, c->idx_alt, c->sort_hist, c->scan_bsum,
-                    c->root, c->bbox_part, c->p_hi, c->p_lo, c->p_x64, c->perm, c->clev,
-                    c->ccount, c->cstart, c->node_c, c->n_level, c->n_first, c->n_count,
-                    c->n_parent, c->n_nchild, c->n_depth, c->bfs2pid, c->pid2bfs, c->dhist,
-                    c->level_start, c->w_a, c->w_d, c->w_b, c->w_c, c->b_mass, c->b_mx,
-                    c->b_com, c->gflag, c->gnode, c->gfirst, c->gcount, c->glen, c->gcells,
-                    c->gbox, c->items, c->item_cnt, c->list_id, c->list_xm, c->wq, c->gfeat, c->gtheta,
-                    c->sys_of, c->sys_sorted, c->sys_root, c->skey, c->skey_alt, c->sval,
-                    c->sval_alt,
-                    c->acc_cache, c->pot_cache, c->err, c->cnt};
+    // three device allocations: the context arena, the list storage, the
+    // walk queues
+    void *ptrs[] = {c->arena, c->list_mem, c->wq};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    c->arena = c->list_mem = nullptr;
+    c->wq = nullptr;
     if (c->cnt_host) cudaFreeHost(c->cnt_host);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->ev) {
@@ -70,15 +67,125 @@ static void free_all(nb_ctx *c)
     }
 }
 
-template <typename T>
-static bool dalloc(T **p, int64_t count)
+// Device memory comes in whole 2 MiB units, each allocation made once and
+// carved into 256-byte aligned arrays.
+#define NB_ALLOC_UNIT ((size_t)2 << 20)
+
+static size_t round_unit(size_t bytes)
 {
-    if (count < 1) count = 1;
-    return cudaMalloc((void **)p, sizeof(T) * (size_t)count) == cudaSuccess;
+    return (bytes + NB_ALLOC_UNIT - 1) / NB_ALLOC_UNIT * NB_ALLOC_UNIT;
 }
+
+static bool dmalloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (cudaMalloc(p, round_unit(bytes ? bytes : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
+
+// two passes over the same list of arrays: sizing (base == nullptr), then
+// placing
+struct Arena {
+    char *base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    void carve(T **p, int64_t count)
+    {
+        if (count < 1) count = 1;
+        off = (off + 255) & ~(size_t)255;
+        *p = base ? (T *)(base + off) : nullptr;
+        off += sizeof(T) * (size_t)count;
+    }
+};
+
+static void carve_context(nb_ctx *c, Arena &a)
+{
+    const int64_t N = c->max_n, NN = c->max_nodes;
+    a.carve(&c->keys, N);
+    a.carve(&c->keys_alt, N);
+    a.carve(&c->idx, N);
+    a.carve(&c->idx_alt, N);
+    a.carve(&c->sort_hist, c->sort_hist_len);
+    a.carve(&c->scan_bsum, c->scan_bsum_len);
+    a.carve(&c->bbox_part, 6 * (int64_t)c->bbox_blocks);
+    a.carve(&c->root, 8 * c->max_sys);
+    a.carve(&c->p_hi, N);
+    a.carve(&c->p_lo, N);
+    a.carve(&c->p_x64, 3 * N);
+    a.carve(&c->perm, N);
+    a.carve(&c->clev, N);
+    a.carve(&c->ccount, N + 1);
+    a.carve(&c->cstart, N + 1);
+    a.carve(&c->node_c, NN);
+    a.carve(&c->n_level, NN);
+    a.carve(&c->n_first, NN);
+    a.carve(&c->n_count, NN);
+    a.carve(&c->n_parent, NN);
+    a.carve(&c->n_nchild, NN);
+    a.carve(&c->n_depth, NN);
+    a.carve(&c->bfs2pid, NN);
+    a.carve(&c->pid2bfs, NN);
+    a.carve(&c->dhist, NB_DEPTHS * c->dtiles + 1);
+    a.carve(&c->level_start, NB_DEPTHS + 1);
+    a.carve(&c->w_a, NN);
+    a.carve(&c->w_d, NN);
+    a.carve(&c->w_b, NN);
+    a.carve(&c->w_c, NN);
+    a.carve(&c->b_mass, NN);
+    a.carve(&c->b_mx, 3 * NN);
+    a.carve(&c->b_com, 3 * NN);
+    a.carve(&c->gflag, NN + 1);
+    a.carve(&c->gnode, N);
+    a.carve(&c->gfirst, N);
+    a.carve(&c->gcount, N);
+    a.carve(&c->glen, N);
+    a.carve(&c->gcells, N);
+    a.carve(&c->gbox, 3 * N);
+    a.carve(&c->gfeat, 16 * N);
+    a.carve(&c->gtheta, N);
+    a.carve(&c->items, 2 * c->max_items);
+    a.carve(&c->item_cnt, N + 1);
+    a.carve(&c->acc_cache, 3 * N);
+    a.carve(&c->pot_cache, N);
+    a.carve(&c->err, 1);
+    a.carve(&c->cnt, CNT_N_);
+    if (c->max_sys > 1) {
+        a.carve(&c->sys_of, N);
+        a.carve(&c->sys_sorted, N);
+        a.carve(&c->sys_root, c->max_sys);
+        a.carve(&c->skey, N);
+        a.carve(&c->skey_alt, N);
+        a.carve(&c->sval, N);
+        a.carve(&c->sval_alt, N);
+    }
+}
+
+// walk queues: two frontier queues of wq_cap entries per warp
+static bool alloc_queues(nb_ctx *c, int64_t wq_cap)
+{
+    if (c->wq) cudaFree(c->wq);
+    c->wq = nullptr;
+    c->wq_cap = 0;
+    if (!dmalloc((void **)&c->wq, sizeof(int32_t) * 2 * (size_t)wq_cap * c->walk_warps))
+        return false;
+    c->wq_cap = wq_cap;
+    return true;
+}
+
+static const char *const SITE_NAME[SITE_N_] = {
+    "none", "k_gather: caller index", "k_cells: node id", "k_parents: child id",
+    "k_depth_scatter: level-order position", "k_bfs_records: node or particle",
+    "k_moments_level: child run", "groups: group or member range", "k_items: item index",
+    "k_walk: queued node", "k_walk: child run", "k_force: item",
+    "k_rs_scatter: destination"};
 
 static int err_code(unsigned bits)
 {
+    if (bits & NB_EF_BOUNDS) return NB_ERR_INTERNAL;
     if (bits & NB_EF_BADARG) return NB_ERR_INVALID_ARG;
     if (bits & NB_EF_NONFINITE) return NB_ERR_NONFINITE;
     if (bits & NB_EF_WALK) return NB_ERR_WALK_LIMIT;
@@ -86,14 +193,56 @@ static int err_code(unsigned bits)
     return NB_OK;
 }
 
-// synchronise, read and clear the device error word
+static void report_bounds(nb_ctx *c)
+{
+    long long v[2] = {0, 0};
+    if (cudaMemcpy(&c->cnt_host[CNT_BAD_SITE], &c->cnt[CNT_BAD_SITE], sizeof(v),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return;
+    v[0] = c->cnt_host[CNT_BAD_SITE];
+    v[1] = c->cnt_host[CNT_BAD_INDEX];
+    const int site = (v[0] > 0 && v[0] < SITE_N_) ? (int)v[0] : 0;
+    fprintf(stderr, "libnb: bounds self-check fired at %s (index %lld)\n", SITE_NAME[site], v[1]);
+}
+
+// synchronise, read and clear the device error word (through the pinned
+// slot after the counters: no device-to-host copy into pageable memory)
 static int sync_read_bits(nb_ctx *c, unsigned *bits)
 {
     *bits = 0;
-    CK(cudaMemcpyAsync(bits, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    unsigned *pinned = (unsigned *)&c->cnt_host[CNT_N_];
+    CK(cudaMemcpyAsync(pinned, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    *bits = *pinned;
+    if (*bits & NB_EF_BOUNDS) report_bounds(c);
     if (*bits) CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
     return NB_OK;
+}
+
+void nb_launched(nb_ctx *c, const char *name)
+{
+    c->launches++;
+    if (!c->debug_sync) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    unsigned bits = 0;
+    if (e == cudaSuccess) {
+        unsigned *pinned = (unsigned *)&c->cnt_host[CNT_N_];
+        e = cudaMemcpy(pinned, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        bits = *pinned;
+    }
+    if (c->fail_site) return;
+    if (e != cudaSuccess) {
+        c->fail_site = name;
+        fprintf(stderr, "libnb: %s failed: %s\n", name, cudaGetErrorString(e));
+    } else if (bits & NB_EF_BOUNDS) {
+        c->fail_site = name;
+        fprintf(stderr, "libnb: after %s:\n", name);
+        report_bounds(c);
+    }
 }
 
 static int sync_read(nb_ctx *c)
@@ -134,24 +283,25 @@ static void phase_end(nb_ctx *c, int k, int phase)
     c->ev_phase[k] = phase;
 }
 
+// List storage: list_xm (16 B) and list_id (4 B) per entry in one
+// allocation with 1/8 headroom, replaced only when a walk needs more.
 static int ensure_lists(nb_ctx *c, int64_t groups, int64_t cap)
 {
     const int64_t need = groups * cap;
     if (need <= c->list_alloc && cap == c->list_cap) return NB_OK;
     if (need > c->list_alloc) {
         CK(cudaStreamSynchronize(c->stream));
-        if (c->list_id) cudaFree(c->list_id);
-        if (c->list_xm) cudaFree(c->list_xm);
+        if (c->list_mem) cudaFree(c->list_mem);
+        c->list_mem = nullptr;
         c->list_id = nullptr;
         c->list_xm = nullptr;
         c->list_alloc = 0;
         const int64_t want = need + need / 8;
-        if (!dalloc(&c->list_id, want) || !dalloc(&c->list_xm, want)) {
-            cudaGetLastError();
-            if (c->list_id) cudaFree(c->list_id);
-            c->list_id = nullptr;
+        const size_t xm_bytes = (sizeof(float4) * (size_t)want + 255) & ~(size_t)255;
+        if (!dmalloc(&c->list_mem, xm_bytes + sizeof(int32_t) * (size_t)want))
             return NB_ERR_NOMEM;
-        }
+        c->list_xm = (float4 *)c->list_mem;
+        c->list_id = (int32_t *)((char *)c->list_mem + xm_bytes);
         c->list_alloc = want;
     }
     c->list_cap = cap;
@@ -195,27 +345,17 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
     c->scan_bsum_len = (scan_n + 2047) / 2048 + 2;
     c->bbox_blocks = c->num_sms * 4;
     c->max_items = N + N / 64 + 2;
-    bool ok = dalloc(&c->keys, N) && dalloc(&c->keys_alt, N) && dalloc(&c->idx, N) &&
-              dalloc(&c->idx_alt, N) && dalloc(&c->sort_hist, c->sort_hist_len) &&
-              dalloc(&c->scan_bsum, c->scan_bsum_len) &&
-              dalloc(&c->bbox_part, 6 * (int64_t)c->bbox_blocks) && dalloc(&c->p_hi, N) &&
-              dalloc(&c->p_lo, N) && dalloc(&c->p_x64, 3 * N) && dalloc(&c->perm, N) &&
-              dalloc(&c->clev, N) && dalloc(&c->ccount, N + 1) && dalloc(&c->cstart, N + 1) &&
-              dalloc(&c->node_c, NN) && dalloc(&c->n_level, NN) && dalloc(&c->n_first, NN) &&
-              dalloc(&c->n_count, NN) && dalloc(&c->n_parent, NN) && dalloc(&c->n_nchild, NN) &&
-              dalloc(&c->n_depth, NN) && dalloc(&c->bfs2pid, NN) && dalloc(&c->pid2bfs, NN) &&
-              dalloc(&c->dhist, dhist_len) && dalloc(&c->level_start, NB_DEPTHS + 1) &&
-              dalloc(&c->w_a, NN) && dalloc(&c->w_d, NN) && dalloc(&c->w_b, NN) &&
-              dalloc(&c->w_c, NN) && dalloc(&c->b_mass, NN) && dalloc(&c->b_mx, 3 * NN) &&
-              dalloc(&c->b_com, 3 * NN) && dalloc(&c->gflag, NN + 1) && dalloc(&c->gnode, N) &&
-              dalloc(&c->gfirst, N) && dalloc(&c->gcount, N) && dalloc(&c->glen, N) &&
-              dalloc(&c->gcells, N) && dalloc(&c->gbox, 3 * N) &&
-              dalloc(&c->root, 8 * (cfg->max_systems > 1 ? cfg->max_systems : 1)) &&
-              dalloc(&c->gfeat, 16 * N) && dalloc(&c->gtheta, N) &&
-              dalloc(&c->items, 2 * c->max_items) && dalloc(&c->item_cnt, N + 1) &&
-              dalloc(&c->acc_cache, 3 * N) && dalloc(&c->pot_cache, N) &&
-              dalloc(&c->err, 1) && dalloc(&c->cnt, CNT_N_) &&
-              cudaMallocHost((void **)&c->cnt_host, sizeof(long long) * CNT_N_) == cudaSuccess;
+    c->max_sys = cfg->max_systems > 1 ? cfg->max_systems : 1;
+    Arena sizing;
+    carve_context(c, sizing);
+    bool ok = dmalloc(&c->arena, sizing.off);
+    if (ok) {
+        Arena place;
+        place.base = (char *)c->arena;
+        carve_context(c, place);
+        c->arena_bytes = round_unit(sizing.off);
+    }
+    ok = ok && cudaMallocHost((void **)&c->cnt_host, sizeof(long long) * (CNT_N_ + 1)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -232,21 +372,15 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
     }
     c->nsys = 1;
     c->item_rows = 2;
-    c->max_sys = cfg->max_systems > 1 ? cfg->max_systems : 1;
-    if (c->max_sys > 1 &&
-        !(dalloc(&c->sys_of, N) && dalloc(&c->sys_sorted, N) && dalloc(&c->sys_root, c->max_sys) &&
-          dalloc(&c->skey, N) && dalloc(&c->skey_alt, N) && dalloc(&c->sval, N) &&
-          dalloc(&c->sval_alt, N))) {
-        cudaGetLastError();
-        free_all(c);
-        delete c;
-        return NB_ERR_NOMEM;
+    {
+        const char *dbg = getenv("NB_DEBUG_SYNC");
+        c->debug_sync = dbg && dbg[0] && dbg[0] != '0';
+        c->fail_site = nullptr;
     }
+
     c->list_cap = cfg->list_capacity;
     c->walk_warps = nb_walk_warps(c);
-    c->wq_cap = 4096;
-    if (!dalloc(&c->wq, 2 * c->wq_cap * c->walk_warps)) {
-        cudaGetLastError();
+    if (!alloc_queues(c, N >= (1 << 20) ? 8192 : 4096)) {
         free_all(c);
         delete c;
         return NB_ERR_NOMEM;
@@ -331,36 +465,38 @@ int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
         if (rc) return rc;
         const int64_t G = c->cnt_host[CNT_GROUPS];
         c->groups_host = G;
-        int64_t cap = c->list_cap > 0 ? c->list_cap : 4096;
-        for (int attempt = 0; attempt < 4; attempt++) {
-            rc = ensure_lists(c, G, cap);
-            if (rc) return rc;
+        // With no list storage yet, the first pass only counts (nothing is
+        // written), so the storage is allocated once at its measured size.
+        int64_t cap = c->list_cap > 0 ? c->list_cap : 0;
+        if (c->list_alloc == 0 && c->cfg.list_capacity <= 0) cap = 0;
+        for (int attempt = 0; attempt < 6; attempt++) {
+            const bool counting = cap == 0;
+            if (counting) {
+                c->list_cap = 0;
+            } else {
+                rc = ensure_lists(c, G, cap);
+                if (rc) return rc;
+            }
             nb_launch_walk(c);
             if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
             unsigned bits = 0;
             rc = sync_read_bits(c, &bits);
             if (rc) return rc;
             rc = err_code(bits);
-            if (rc != NB_ERR_CAPACITY) break;
+            if (rc != NB_OK && rc != NB_ERR_CAPACITY) break;
+            if (rc == NB_OK && !counting) break;
             rc = read_counters(c);
             if (rc) return rc;
             if (bits & NB_EF_QUEUE) {   // a frontier outgrew the walk queues
                 const int64_t want = 2 * (c->cnt_host[CNT_QMAX] > c->wq_cap ? c->cnt_host[CNT_QMAX]
                                                                             : c->wq_cap);
                 CK(cudaStreamSynchronize(c->stream));
-                cudaFree(c->wq);
-                c->wq = nullptr;
-                if (!dalloc(&c->wq, 2 * want * c->walk_warps)) {
-                    cudaGetLastError();
-                    c->wq_cap = 0;
-                    return NB_ERR_NOMEM;
-                }
-                c->wq_cap = want;
-            }
-            if (bits & NB_EF_CAPACITY) {
-                if (c->cfg.list_capacity > 0) return NB_ERR_CAPACITY;
+                if (!alloc_queues(c, want)) return NB_ERR_NOMEM;
+            } else if (counting || (bits & NB_EF_CAPACITY)) {
+                if (!counting && c->cfg.list_capacity > 0) return NB_ERR_CAPACITY;
                 const int64_t need = c->cnt_host[CNT_LIST_MAX];
                 cap = ((need + need / 4 + 255) / 256) * 256;
+                if (cap < 256) cap = 256;
             }
             rc = NB_ERR_CAPACITY;
         }
@@ -394,14 +530,7 @@ static int probe(nb_ctx *c, int n_crit)
         if (rc) return rc;
         const int64_t want = 2 * (c->cnt_host[CNT_QMAX] > c->wq_cap ? c->cnt_host[CNT_QMAX] : c->wq_cap);
         CK(cudaStreamSynchronize(c->stream));
-        cudaFree(c->wq);
-        c->wq = nullptr;
-        if (!dalloc(&c->wq, 2 * want * c->walk_warps)) {
-            cudaGetLastError();
-            c->wq_cap = 0;
-            return NB_ERR_NOMEM;
-        }
-        c->wq_cap = want;
+        if (!alloc_queues(c, want)) return NB_ERR_NOMEM;
     }
     return NB_ERR_CAPACITY;
 }

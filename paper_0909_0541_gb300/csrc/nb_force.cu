@@ -120,13 +120,22 @@ __device__ __forceinline__ void force_item(
     const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
     const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
     const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
-    const float4 *__restrict__ list_xm, int64_t cap, float eps2, float *__restrict__ acc,
-    float *__restrict__ pot)
+    const float4 *__restrict__ list_xm, int64_t cap, int64_t alloc, int64_t n, float eps2,
+    float *__restrict__ acc, float *__restrict__ pot, long long *__restrict__ cnt,
+    unsigned *__restrict__ err)
 {
     const int lane = threadIdx.x & 31;
     const int32_t f = gfirst[g], ng = gcount[g];
-    // a list that outgrew its slot was reported by the walk; never read past the slot
-    const int32_t len = glen[g] < cap ? glen[g] : (int32_t)cap;
+    if (!(f >= 0 && ng >= 1 && (int64_t)f + ng <= n && i0 >= 0 && i0 < ng)) {
+        if (lane == 0) nb_bad(cnt, err, SITE_FORCE, g);
+        return;
+    }
+    // a list that outgrew its slot (or the storage) was reported by the walk;
+    // never read past either
+    const int64_t room = alloc - (int64_t)g * cap;
+    int64_t lim = cap < room ? cap : room;
+    if (lim < 0) lim = 0;
+    const int32_t len = glen[g] < lim ? glen[g] : (int32_t)lim;
     const float4 bc = gbox[3 * (int64_t)g + 2];
     const float4 pad = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
     float xi[R], yi[R], zi[R];
@@ -190,18 +199,24 @@ __device__ __forceinline__ void force_item(
 }
 
 template <int MODE, bool GUARD>
-__global__ void __launch_bounds__(F_T)
+__global__ void __launch_bounds__(F_T, MODE == MODE_COMP ? 4 : 5)
 k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ gfirst,
         const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
         const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
         const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
-        const float4 *__restrict__ list_xm, int64_t cap, long long *__restrict__ cnt,
-        float eps2, float *__restrict__ acc, float *__restrict__ pot)
+        const float4 *__restrict__ list_xm, int64_t cap, int64_t alloc, int64_t n,
+        long long *__restrict__ cnt, float eps2, float *__restrict__ acc, float *__restrict__ pot,
+        unsigned *__restrict__ err, int64_t max_items)
 {
     __shared__ float4 tiles[F_WARPS][NB_WARP];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int32_t nitems = (int32_t)cnt[CNT_ITEMS];
+    int32_t nitems = (int32_t)cnt[CNT_ITEMS];
+    const int32_t ngroups = (int32_t)cnt[CNT_GROUPS];
+    if (nitems > max_items) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) nb_bad(cnt, err, SITE_FORCE, nitems);
+        nitems = (int32_t)max_items;
+    }
     for (;;) {
         int it = 0;
         if (lane == 0) it = (int)nb_atomic_add(&cnt[CNT_FORCE_Q], 1LL);
@@ -209,12 +224,16 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ gfirst,
         if (it >= nitems) break;
         const int32_t g = items[2 * (int64_t)it], word = items[2 * (int64_t)it + 1];
         const int32_t i0 = word & ~ITEM_ONE_ROW;
+        if (g < 0 || g >= ngroups) {
+            if (lane == 0) nb_bad(cnt, err, SITE_FORCE, g);
+            continue;
+        }
         if (word & ITEM_ONE_ROW)
             force_item<MODE, GUARD, 1>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo,
-                                       perm, list_xm, cap, eps2, acc, pot);
+                                       perm, list_xm, cap, alloc, n, eps2, acc, pot, cnt, err);
         else
             force_item<MODE, GUARD, 2>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo,
-                                       perm, list_xm, cap, eps2, acc, pot);
+                                       perm, list_xm, cap, alloc, n, eps2, acc, pot, cnt, err);
     }
 }
 
@@ -228,8 +247,9 @@ static void launch_force(nb_ctx *c, float eps2, float *acc, float *pot)
     }
     k_force<MODE, GUARD><<<c->num_sms * blocks, F_T, 0, c->stream>>>(
         c->items, c->gfirst, c->gcount, c->glen, c->gbox, c->p_hi, c->p_lo, c->perm,
-        c->list_xm, c->list_cap, c->cnt, eps2, acc, pot);
-    c->launches++;
+        c->list_xm, c->list_cap, c->list_alloc, c->n, c->cnt, eps2, acc, pot, c->err,
+        c->max_items);
+    nb_launched(c, "k_force");
 }
 
 void nb_launch_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision)

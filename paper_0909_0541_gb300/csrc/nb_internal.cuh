@@ -42,6 +42,7 @@
 #define NB_EF_WALK 4u
 #define NB_EF_QUEUE 8u
 #define NB_EF_BADARG 16u
+#define NB_EF_BOUNDS 32u   // an index failed a kernel's own bounds check (access skipped)
 
 // device counters (int64 slots of ctx->cnt)
 enum {
@@ -59,7 +60,27 @@ enum {
     CNT_QMAX,        // widest walk frontier
     CNT_PP_CUM,      // n_pp over every walk (never reset)
     CNT_PC_CUM,
+    CNT_BAD_SITE,    // first failed self-check: site code (never reset)
+    CNT_BAD_INDEX,   // ... and the offending index
     CNT_N_
+};
+
+// self-check sites (a kernel's own bounds checks; a hit is a library defect)
+enum {
+    SITE_NONE = 0,
+    SITE_GATHER,      // sorted slot -> caller index out of range
+    SITE_CELLS,       // node id outside the node count
+    SITE_PARENTS,     // child id outside the node count
+    SITE_DEPTH,       // level-order position outside the node count
+    SITE_RECORDS,     // preorder id or particle slot out of range
+    SITE_MOMENTS,     // child run outside the node count
+    SITE_GROUPS,      // group id or member range out of range
+    SITE_ITEMS,       // work item index out of range
+    SITE_WALK_NODE,   // queued node outside the node count
+    SITE_WALK_CHILD,  // child run outside the node count
+    SITE_FORCE,       // force item out of range
+    SITE_SORT,        // radix-sort destination out of range
+    SITE_N_
 };
 
 struct nb_ctx {
@@ -136,6 +157,12 @@ struct nb_ctx {
     // learned opening angle: group features (16 floats) and theta per group
     float *gfeat, *gtheta;
 
+    // device memory: one arena for every fixed-size array, one allocation
+    // for the list storage (list_xm then list_id), one for the walk queues
+    void *arena;
+    size_t arena_bytes;
+    void *list_mem;
+
     // lists
     int64_t list_cap;     // entries per group slot
     int64_t list_alloc;   // entries allocated
@@ -159,6 +186,11 @@ struct nb_ctx {
     cudaEvent_t *ev;         // NB_EV_POOL pairs
     int *ev_phase;
     long long launches;
+
+    // NB_DEBUG_SYNC=1: synchronise after every launch, report the first
+    // kernel that failed (and the first self-check that fired)
+    int debug_sync;
+    const char *fail_site;
 
     // status
     unsigned int *err;
@@ -209,6 +241,25 @@ __device__ __forceinline__ long long nb_atomic_add(long long *p, long long v)
 {
     return (long long)atomicAdd((unsigned long long *)p, (unsigned long long)v);
 }
+
+// A failed self-check: latch NB_EF_BOUNDS and the first site / index.  The
+// caller skips the access.
+static __device__ __forceinline__ void nb_bad(long long *cnt, unsigned *err, int site, long long idx)
+{
+    atomicOr(err, NB_EF_BOUNDS);
+    if (atomicCAS((unsigned long long *)&cnt[CNT_BAD_SITE], 0ull, (unsigned long long)site) == 0ull)
+        cnt[CNT_BAD_INDEX] = idx;
+}
+__device__ __forceinline__ bool nb_in(bool ok, long long *cnt, unsigned *err, int site,
+                                      long long idx)
+{
+    if (!ok) nb_bad(cnt, err, site, idx);
+    return ok;
+}
+
+// after every kernel launch: count it; under NB_DEBUG_SYNC synchronise and
+// report a failure by kernel name
+void nb_launched(nb_ctx *c, const char *name);
 
 // group-relative FP32 coordinate of a value carried as two floats (hi, lo):
 // fl32(fl32(hi - c) + lo)

@@ -325,7 +325,7 @@ void nb_launch_mlp_infer(nb_ctx *c, const float *params, const float *feat, floa
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_mlp_infer, MLP_T, 0);
     if (blocks < 1) blocks = 1;
     k_mlp_infer<<<c->num_sms * blocks, MLP_T, 0, c->stream>>>(params, feat, c->cnt, theta, fallback);
-    c->launches++;
+    nb_launched(c, "k_mlp_infer");
 }
 
 // ------------------------------------------------------------ training data

@@ -135,12 +135,12 @@ void nb_exclusive_scan(nb_ctx *c, const int32_t *in, int32_t *out, int64_t n_max
     const int nb = (int)((n_max + SCAN_TILE - 1) / SCAN_TILE);
     const int g = nb > 0 ? nb : 1;
     k_scan_reduce<<<g, SCAN_T, 0, c->stream>>>(in, n_max, n_dev, c->scan_bsum);
-    c->launches++;
+    nb_launched(c, "k_scan_reduce");
     k_scan_bsum<<<1, 1024, 0, c->stream>>>(c->scan_bsum, g, out, n_max, n_dev,
                                            total_dev);
-    c->launches++;
+    nb_launched(c, "k_scan_bsum");
     k_scan_apply<<<g, SCAN_T, 0, c->stream>>>(in, out, n_max, n_dev, c->scan_bsum);
-    c->launches++;
+    nb_launched(c, "k_scan_apply");
 }
 
 // ------------------------------------------------------------ radix sort
@@ -169,7 +169,8 @@ k_rs_hist(const uint64_t *__restrict__ key, int64_t n, int shift,
 __global__ void __launch_bounds__(RS_T)
 k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-             const uint32_t *__restrict__ offs, int64_t n, int shift, int nb)
+             const uint32_t *__restrict__ offs, int64_t n, int shift, int nb,
+             long long *__restrict__ cnt, unsigned *__restrict__ err)
 {
     __shared__ uint32_t whist[RS_WARPS][256];
     __shared__ uint32_t boff[256];
@@ -211,6 +212,10 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
         if (i < n) {
             const int d = (int)((key[r] >> shift) & 255u);
             const uint32_t pos = boff[d] + whist[w][d] + rnk[r];
+            if (pos >= n) {   // a self-check (recorded when a context is given)
+                if (cnt) nb_bad(cnt, err, SITE_SORT, pos);
+                continue;
+            }
             kout[pos] = key[r];
             vout[pos] = val[r];
         }
@@ -227,12 +232,12 @@ void nb_radix_sort(nb_ctx *c, int64_t n)
     for (int pass = 0; pass < 8; pass++) {
         const int shift = 8 * pass;
         k_rs_hist<<<nb, RS_T, 0, c->stream>>>(ka, n, shift, c->sort_hist, nb);
-        c->launches++;
+        nb_launched(c, "k_rs_hist");
         nb_exclusive_scan(c, (const int32_t *)c->sort_hist, (int32_t *)c->sort_hist,
                           (int64_t)256 * nb, nullptr, nullptr);
         k_rs_scatter<<<nb, RS_T, 0, c->stream>>>(ka, va, kb, vb, c->sort_hist, n,
-                                                 shift, nb);
-        c->launches++;
+                                                 shift, nb, c->cnt, c->err);
+        nb_launched(c, "k_rs_scatter");
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
@@ -272,7 +277,7 @@ void nb_radix_sort_passes(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uin
         const int shift = 8 * pass;
         k_rs_hist<<<nb, RS_T, 0, s>>>(ka, n, shift, hist, nb);
         nb_exclusive_scan_raw((const int32_t *)hist, (int32_t *)hist, (int64_t)256 * nb, bsum, s);
-        k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, hist, n, shift, nb);
+        k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, hist, n, shift, nb, nullptr, nullptr);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }

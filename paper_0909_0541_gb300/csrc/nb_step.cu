@@ -22,11 +22,11 @@ k_drift(double *__restrict__ pos, const double *__restrict__ vel, int64_t m, dou
 void nb_launch_kick(nb_ctx *c, double *vel, const float *acc, int64_t n, double h)
 {
     k_kick<<<nb_grid(3 * n, 256, c->num_sms * 8), 256, 0, c->stream>>>(vel, acc, 3 * n, h);
-    c->launches++;
+    nb_launched(c, "k_kick");
 }
 
 void nb_launch_drift(nb_ctx *c, double *pos, const double *vel, int64_t n, double dt)
 {
     k_drift<<<nb_grid(3 * n, 256, c->num_sms * 8), 256, 0, c->stream>>>(pos, vel, 3 * n, dt);
-    c->launches++;
+    nb_launched(c, "k_drift");
 }

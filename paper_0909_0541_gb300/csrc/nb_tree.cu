@@ -149,11 +149,13 @@ k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ roo
 __global__ void __launch_bounds__(256)
 k_gather(const double *__restrict__ pos, const float *__restrict__ mass, int64_t n,
          const uint32_t *__restrict__ idx, int32_t *__restrict__ perm,
-         double *__restrict__ x64, float4 *__restrict__ p_hi, float4 *__restrict__ p_lo)
+         double *__restrict__ x64, float4 *__restrict__ p_hi, float4 *__restrict__ p_lo,
+         long long *__restrict__ cnt, unsigned *__restrict__ err)
 {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t i = idx[s];
+    if (!nb_in(i < n, cnt, err, SITE_GATHER, i)) return;
     perm[s] = (int32_t)i;
     float h[3], l[3];
 #pragma unroll
@@ -195,7 +197,7 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
         int32_t *__restrict__ n_count, int32_t *__restrict__ n_parent,
         int32_t *__restrict__ n_nchild, int8_t *__restrict__ n_depth,
         long long *__restrict__ cnt, const int32_t *__restrict__ sys,
-        const int64_t *__restrict__ sys_off)
+        const int64_t *__restrict__ sys_off, unsigned *__restrict__ err)
 {
     const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a >= n) return;
@@ -210,6 +212,7 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
     const int k = ca > cp ? ca - cp : 0;
     const int32_t base = cstart[a] + (int32_t)a;
     const int32_t leaf = base + k;
+    if (!nb_in(base >= 0 && leaf < total, cnt, err, SITE_CELLS, leaf)) return;
 
     // particle leaf: one below the deepest cell that holds it
     node_c[leaf] = make_int4(leaf + 1, 0, 0, 1);
@@ -256,8 +259,9 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
 // every cell writes itself as parent of its children (child = id + 1, then
 // next of each child until the cell's own next)
 __global__ void __launch_bounds__(256)
-k_parents(const int4 *__restrict__ node_c, const long long *__restrict__ cnt,
-          int32_t *__restrict__ n_parent, int32_t *__restrict__ n_nchild)
+k_parents(const int4 *__restrict__ node_c, long long *__restrict__ cnt,
+          int32_t *__restrict__ n_parent, int32_t *__restrict__ n_nchild,
+          unsigned *__restrict__ err)
 {
     const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total;
@@ -265,6 +269,7 @@ k_parents(const int4 *__restrict__ node_c, const long long *__restrict__ cnt,
         const int4 cu = node_c[u];
         if (cu.w) continue;
         int32_t ch = u + 1, nch = 0;
+        if (!nb_in(cu.x <= total, cnt, err, SITE_PARENTS, cu.x)) continue;
         while (ch < cu.x) {
             n_parent[ch] = u;
             nch++;
@@ -301,9 +306,9 @@ k_depth_hist(const int8_t *__restrict__ depth, const long long *__restrict__ cnt
 }
 
 __global__ void __launch_bounds__(DS_T)
-k_depth_scatter(const int8_t *__restrict__ depth, const long long *__restrict__ cnt,
+k_depth_scatter(const int8_t *__restrict__ depth, long long *__restrict__ cnt,
                 const uint32_t *__restrict__ offs, int ntiles, int32_t *__restrict__ bfs2pid,
-                int32_t *__restrict__ pid2bfs)
+                int32_t *__restrict__ pid2bfs, unsigned *__restrict__ err)
 {
     __shared__ uint32_t whist[DS_T / NB_WARP][32];
     __shared__ uint32_t boff[32];
@@ -344,6 +349,7 @@ k_depth_scatter(const int8_t *__restrict__ depth, const long long *__restrict__ 
         if (i < total) {
             const int d = depth[i];
             const uint32_t pos = boff[d] + whist[w][d] + rnk[r];
+            if (!nb_in(pos < total, cnt, err, SITE_DEPTH, pos)) continue;
             bfs2pid[pos] = (int32_t)i;
             pid2bfs[i] = (int32_t)pos;
         }
@@ -365,17 +371,21 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
               const int4 *__restrict__ node_c, const int32_t *__restrict__ n_first,
               const int32_t *__restrict__ n_nchild, const float4 *__restrict__ p_hi,
               const float4 *__restrict__ p_lo, const double *__restrict__ x64,
-              const long long *__restrict__ cnt, float4 *__restrict__ w_a,
+              long long *__restrict__ cnt, float4 *__restrict__ w_a,
               float4 *__restrict__ w_d, int4 *__restrict__ w_b, float2 *__restrict__ w_c,
-              double *__restrict__ b_mass, double *__restrict__ b_mx, double *__restrict__ b_com)
+              double *__restrict__ b_mass, double *__restrict__ b_mx, double *__restrict__ b_com,
+              int64_t n, unsigned *__restrict__ err)
 {
     const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < total;
          b += gridDim.x * blockDim.x) {
         const int32_t u = bfs2pid[b];
+        if (!nb_in(u >= 0 && u < total, cnt, err, SITE_RECORDS, u)) continue;
         const int4 c = node_c[u];
+        if (!nb_in(c.w || u + 1 < total, cnt, err, SITE_RECORDS, u)) continue;
         if (c.w) {
             const int32_t slot = n_first[u];
+            if (!nb_in(slot >= 0 && slot < n, cnt, err, SITE_RECORDS, slot)) continue;
             const float4 h = p_hi[slot];
             w_a[b] = h;
             w_d[b] = p_lo[slot];
@@ -405,13 +415,19 @@ k_moments_level(int depth, const int32_t *__restrict__ level_start,
                 const int4 *__restrict__ w_b,
                 float4 *__restrict__ w_a, float4 *__restrict__ w_d, float2 *__restrict__ w_c,
                 double *__restrict__ b_mass, double *__restrict__ b_mx,
-                double *__restrict__ b_com)
+                double *__restrict__ b_com, long long *__restrict__ cnt, int64_t n,
+                unsigned *__restrict__ err)
 {
     const int32_t lo_b = level_start[depth], hi_b = level_start[depth + 1];
+    const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t b = lo_b + blockIdx.x * blockDim.x + threadIdx.x; b < hi_b;
          b += gridDim.x * blockDim.x) {
         const int4 wb = w_b[b];
         if (wb.z < 0) continue;
+        if (!nb_in(wb.z > b && (int64_t)wb.z + wb.w <= total && wb.x >= 0 && wb.x < total &&
+                       n_first[wb.x] >= 0 && n_first[wb.x] < n,
+                   cnt, err, SITE_MOMENTS, b))
+            continue;
         const double *root = roots + (sys ? 8 * (int64_t)sys[n_first[wb.x]] : 0);
         const double lc = ldexp(root[3], -depth);
         double M = 0.0, mx[3] = {0.0, 0.0, 0.0};
@@ -453,11 +469,11 @@ void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     cudaStream_t s = c->stream;
     cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_PP_CUM, s);
     k_bbox<<<c->bbox_blocks, 256, 0, s>>>(pos, n, c->bbox_part, c->err);
-    c->launches++;
+    nb_launched(c, "k_bbox");
     k_root<<<1, 256, 0, s>>>(c->bbox_part, c->bbox_blocks, c->root);
-    c->launches++;
+    nb_launched(c, "k_root");
     k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, nullptr, c->keys, c->idx);
-    c->launches++;
+    nb_launched(c, "k_keys");
     nb_radix_sort(c, n);
     build_tail(c, pos, mass, n, nullptr);
 }
@@ -576,28 +592,28 @@ void nb_launch_build_batched(nb_ctx *c, const double *pos, const float *mass, in
     cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_PP_CUM, s);
     const int gs = (int)(nsys < 65535 ? nsys : 65535);
     k_sys_of<<<gs, 256, 0, s>>>(off, nsys, n, c->sys_of, c->err);
-    c->launches++;
+    nb_launched(c, "k_sys_of");
     k_roots_sys<<<gs, 256, 0, s>>>(pos, off, nsys, n, c->root, c->err);
-    c->launches++;
+    nb_launched(c, "k_roots_sys");
     k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, c->sys_of, c->keys, c->idx);
-    c->launches++;
+    nb_launched(c, "k_keys");
     nb_radix_sort(c, n);
     // stable by system on top of the Morton order: (system, key) order
     k_sys_key<<<nb_grid(n, 256), 256, 0, s>>>(c->idx, c->sys_of, n, c->skey, c->sval);
-    c->launches++;
+    nb_launched(c, "k_sys_key");
     nb_radix_sort_passes(c->skey, c->skey_alt, c->sval, c->sval_alt, c->sort_hist, c->scan_bsum,
                          n, 2, s);
     c->launches += 2 * 5;
     k_sys_apply<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, c->idx, c->skey, c->sval, n,
                                                 c->keys_alt, c->idx_alt, c->sys_sorted);
-    c->launches++;
+    nb_launched(c, "k_sys_apply");
     uint64_t *tk = c->keys; c->keys = c->keys_alt; c->keys_alt = tk;
     uint32_t *ti = c->idx; c->idx = c->idx_alt; c->idx_alt = ti;
     build_tail(c, pos, mass, n, c->sys_sorted);
     k_sys_roots<<<nb_grid(nsys, 256, c->num_sms * 4), 256, 0, s>>>(c->level_start, c->bfs2pid,
                                                                     c->n_first, c->sys_sorted,
                                                                     c->sys_root);
-    c->launches++;
+    nb_launched(c, "k_sys_roots");
 }
 
 static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t n,
@@ -605,67 +621,71 @@ static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t 
 {
     cudaStream_t s = c->stream;
     k_gather<<<nb_grid(n, 256), 256, 0, s>>>(pos, mass, n, c->idx, c->perm, c->p_x64,
-                                             c->p_hi, c->p_lo);
-    c->launches++;
+                                             c->p_hi, c->p_lo, c->cnt, c->err);
+    nb_launched(c, "k_gather");
     k_levels<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, n, sys_sorted, c->clev, c->ccount);
-    c->launches++;
+    nb_launched(c, "k_levels");
     nb_exclusive_scan(c, c->ccount, c->cstart, n, nullptr, &c->cnt[CNT_CELLS]);
     k_cells<<<nb_grid(n, 256), 256, 0, s>>>(c->keys, n, c->clev, c->cstart, c->node_c,
                                             c->n_level, c->n_first, c->n_count, c->n_parent,
                                             c->n_nchild, c->n_depth, c->cnt, sys_sorted,
-                                            c->sys_off);
-    c->launches++;
+                                            c->sys_off, c->err);
+    nb_launched(c, "k_cells");
     const int gcap = c->num_sms * 16;
     k_parents<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(c->node_c, c->cnt, c->n_parent,
-                                                               c->n_nchild);
-    c->launches++;
+                                                               c->n_nchild, c->err);
+    nb_launched(c, "k_parents");
     // level order
     const int nt = (int)c->dtiles;
     k_depth_hist<<<nt, DS_T, 0, s>>>(c->n_depth, c->cnt, c->dhist, nt);
-    c->launches++;
+    nb_launched(c, "k_depth_hist");
     nb_exclusive_scan(c, (const int32_t *)c->dhist, (int32_t *)c->dhist,
                       (int64_t)NB_DEPTHS * nt, nullptr, nullptr);
-    k_depth_scatter<<<nt, DS_T, 0, s>>>(c->n_depth, c->cnt, c->dhist, nt, c->bfs2pid, c->pid2bfs);
-    c->launches++;
+    k_depth_scatter<<<nt, DS_T, 0, s>>>(c->n_depth, c->cnt, c->dhist, nt, c->bfs2pid, c->pid2bfs,
+                                        c->err);
+    nb_launched(c, "k_depth_scatter");
     k_level_start<<<1, 32, 0, s>>>(c->dhist, nt, c->level_start);
-    c->launches++;
+    nb_launched(c, "k_level_start");
     k_bfs_records<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
         c->bfs2pid, c->pid2bfs, c->node_c, c->n_first, c->n_nchild, c->p_hi, c->p_lo, c->p_x64,
-        c->cnt, c->w_a, c->w_d, c->w_b, c->w_c, c->b_mass, c->b_mx, c->b_com);
-    c->launches++;
+        c->cnt, c->w_a, c->w_d, c->w_b, c->w_c, c->b_mass, c->b_mx, c->b_com, n, c->err);
+    nb_launched(c, "k_bfs_records");
     const int gl = c->num_sms * 8;
     for (int d = NB_LEVELS; d >= 0; d--) {
         k_moments_level<<<gl, 256, 0, s>>>(d, c->level_start, c->keys, c->n_first, c->root,
                                            sys_sorted, c->w_b, c->w_a, c->w_d, c->w_c, c->b_mass, c->b_mx,
-                                           c->b_com);
-        c->launches++;
+                                           c->b_com, c->cnt, n, c->err);
+        nb_launched(c, "k_moments_level");
     }
 }
 
 // ------------------------------------------------------------ groups
 __global__ void __launch_bounds__(256)
 k_group_flags(const int32_t *__restrict__ n_count, const int32_t *__restrict__ n_parent,
-              const long long *__restrict__ cnt, int n_crit, int32_t *__restrict__ flag)
+              long long *__restrict__ cnt, int n_crit, int32_t *__restrict__ flag,
+              unsigned *__restrict__ err)
 {
     const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total;
          u += gridDim.x * blockDim.x) {
-        const int32_t p = n_parent[u];
+        int32_t p = n_parent[u];
+        if (!nb_in(p < total, cnt, err, SITE_GROUPS, u)) p = -1;
         flag[u] = (n_count[u] <= n_crit) && (p < 0 || n_count[p] > n_crit);
     }
 }
 
 __global__ void __launch_bounds__(256)
 k_group_scatter(const int32_t *__restrict__ gid, const int32_t *__restrict__ n_first,
-                const int32_t *__restrict__ n_count, const long long *__restrict__ cnt,
+                const int32_t *__restrict__ n_count, long long *__restrict__ cnt,
                 int32_t *__restrict__ gnode, int32_t *__restrict__ gfirst,
-                int32_t *__restrict__ gcount)
+                int32_t *__restrict__ gcount, int64_t n, unsigned *__restrict__ err)
 {
     const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total;
          u += gridDim.x * blockDim.x) {
         const int32_t g = gid[u];
         if (gid[u + 1] != g) {
+            if (!nb_in(g >= 0 && g < n, cnt, err, SITE_GROUPS, g)) continue;
             gnode[g] = u;
             gfirst[g] = n_first[u];
             gcount[g] = n_count[u];
@@ -677,14 +697,18 @@ k_group_scatter(const int32_t *__restrict__ gid, const int32_t *__restrict__ n_f
 // 1/theta, and the number of force work items of the group
 __global__ void __launch_bounds__(256)
 k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gcount,
-              const float4 *__restrict__ p_hi, const long long *__restrict__ cnt,
+              const float4 *__restrict__ p_hi, long long *__restrict__ cnt,
               float theta, const float *__restrict__ theta_g, float4 *__restrict__ gbox,
-              int32_t *__restrict__ item_cnt, int iblock)
+              int32_t *__restrict__ item_cnt, int iblock, int64_t n, unsigned *__restrict__ err)
 {
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G;
          g += gridDim.x * blockDim.x) {
         const int32_t f = gfirst[g], m = gcount[g];
+        if (!nb_in(f >= 0 && m >= 1 && (int64_t)f + m <= n, cnt, err, SITE_GROUPS, g)) {
+            item_cnt[g] = 0;
+            continue;
+        }
         float4 p = p_hi[f];
         float lx = p.x, ly = p.y, lz = p.z, hx = p.x, hy = p.y, hz = p.z;
         for (int32_t k = 1; k < m; k++) {
@@ -706,12 +730,16 @@ k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gc
 
 __global__ void __launch_bounds__(256)
 k_items(const int32_t *__restrict__ item_off, const int32_t *__restrict__ gcount,
-        const long long *__restrict__ cnt, int32_t *__restrict__ items, int iblock)
+        long long *__restrict__ cnt, int32_t *__restrict__ items, int iblock, int64_t max_items,
+        unsigned *__restrict__ err)
 {
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G;
          g += gridDim.x * blockDim.x) {
         const int32_t o = item_off[g], m = gcount[g];
+        if (!nb_in(o >= 0 && (int64_t)o + (m + iblock - 1) / iblock <= max_items, cnt, err,
+                   SITE_ITEMS, g))
+            continue;
         for (int32_t i0 = 0, k = 0; i0 < m; i0 += iblock, k++) {
             items[2 * (int64_t)(o + k)] = g;
             // bit 30: the item's targets fit one 32-wide row
@@ -725,26 +753,27 @@ void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
     cudaStream_t s = c->stream;
     const int gcap = c->num_sms * 16;
     k_group_flags<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
-        c->n_count, c->n_parent, c->cnt, n_crit, c->gflag);
-    c->launches++;
+        c->n_count, c->n_parent, c->cnt, n_crit, c->gflag, c->err);
+    nb_launched(c, "k_group_flags");
     nb_exclusive_scan(c, c->gflag, c->gflag, c->max_nodes, &c->cnt[CNT_NODES],
                       &c->cnt[CNT_GROUPS]);
     k_group_scatter<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
-        c->gflag, c->n_first, c->n_count, c->cnt, c->gnode, c->gfirst, c->gcount);
-    c->launches++;
+        c->gflag, c->n_first, c->n_count, c->cnt, c->gnode, c->gfirst, c->gcount, c->n, c->err);
+    nb_launched(c, "k_group_scatter");
     k_group_boxes<<<nb_grid(c->max_n, 256, gcap), 256, 0, s>>>(
         c->gfirst, c->gcount, c->p_hi, c->cnt, theta, theta_g, c->gbox, c->item_cnt,
-        c->item_rows * NB_WARP);
-    c->launches++;
+        c->item_rows * NB_WARP, c->n, c->err);
+    nb_launched(c, "k_group_boxes");
     nb_exclusive_scan(c, c->item_cnt, c->item_cnt, c->max_n, &c->cnt[CNT_GROUPS],
                       &c->cnt[CNT_ITEMS]);
     k_items<<<nb_grid(c->max_n, 256, gcap), 256, 0, s>>>(c->item_cnt, c->gcount, c->cnt,
-                                                          c->items, c->item_rows * NB_WARP);
-    c->launches++;
+                                                          c->items, c->item_rows * NB_WARP,
+                                                          c->max_items, c->err);
+    nb_launched(c, "k_items");
 }
 
 // Root cube and Morton keys on buffers the caller supplies (no context):
-// part holds 6 * nblk doubles, root 7; idx receives 0..n-1.
+// part holds 6 * nblk doubles, root 8; idx receives 0..n-1.
 void nb_launch_keys_raw(const double *pos, int64_t n, double *part, int nblk, double *root,
                         uint64_t *keys, uint32_t *idx, unsigned *err, cudaStream_t s)
 {

@@ -70,6 +70,7 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
     int32_t *const qa = wq + gw * 2 * wq_cap;
     int32_t *const qb = qa + wq_cap;
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
+    const int32_t total = (int32_t)cnt[CNT_NODES];
     long long pp = 0, pc = 0, tot = 0;
     int32_t mx = 0, qmax = 0;
     unsigned bad = 0;
@@ -83,7 +84,8 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
         const float4 bc = gbox[3 * (int64_t)g + 2];
         const float invth = bc.w;
         const int32_t gpid = gnode[g];
-        const int32_t gb = pid2bfs[gpid];
+        const int32_t gb = nb_in(gpid >= 0 && gpid < total, cnt, err, SITE_WALK_NODE, gpid)
+                               ? pid2bfs[gpid] : -1;
         const int64_t base = (int64_t)g * cap;
         const int64_t room = alloc - base < cap ? (alloc - base > 0 ? alloc - base : 0) : cap;
         int32_t len = 0, ncell = 0;
@@ -102,8 +104,9 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
                 bool emit = false, cell_emit = false, open = false;
                 int32_t b = 0, pid = 0, fc = 0, nch = 0;
                 float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < na) {
-                    b = qin[i];
+                if (i < na) b = qin[i];
+                const bool inb = i < na && nb_in(b >= 0 && b < total, cnt, err, SITE_WALK_NODE, b);
+                if (inb) {
                     const int4 wb = w_b[b];
                     a = w_a[b];
                     pid = wb.x;
@@ -117,7 +120,8 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
                             if (!holds && far_enough(a, wc.x, wc.y, blo, bhi, invth)) {
                                 emit = true;
                                 cell_emit = true;
-                            } else {
+                            } else if (nb_in(fc > b && (int64_t)fc + wb.w <= total, cnt, err,
+                                             SITE_WALK_CHILD, b)) {
                                 open = true;
                                 nch = wb.w;
                             }
@@ -243,7 +247,7 @@ void nb_launch_walk(nb_ctx *c)
         c->glen, c->gcells, c->list_id, c->list_xm, c->list_cap, c->list_alloc, c->wq,
         c->wq_cap, c->err, nullptr, c->root, c->n_depth, c->gfirst,
         c->nsys > 1 ? c->sys_sorted : nullptr, c->nsys > 1 ? c->sys_root : nullptr);
-    c->launches++;
+    nb_launched(c, "k_walk");
 }
 
 // the probe walk: features of every group (the groups must be formed with
@@ -257,5 +261,5 @@ void nb_launch_probe(nb_ctx *c, float *feat)
         c->glen, c->gcells, nullptr, nullptr, 0, 0, c->wq, c->wq_cap, c->err, feat, c->root,
         c->n_depth, c->gfirst, c->nsys > 1 ? c->sys_sorted : nullptr,
         c->nsys > 1 ? c->sys_root : nullptr);
-    c->launches++;
+    nb_launched(c, "k_walk");
 }

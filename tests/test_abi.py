@@ -30,5 +30,6 @@ def test_library_exports_every_declared_symbol():
 
 def test_error_strings():
     import paper_0909_0541_gb300 as nb
-    for code in range(-7, 1):
-        assert nb._lib.nb_error_string(code)
+    for code in range(-8, 1):
+        assert nb._lib.nb_error_string(code) != b"unknown error"
+        assert code == 0 or code in nb.NB_ERR

@@ -63,7 +63,7 @@ def assert_tree_equal(g, T):
     assert np.array_equal(t["l"][cell], o["l"][cell])
     assert np.array_equal(t["s"][cell], o["s"][cell])
     assert np.array_equal(t["root"][:3], T.centre) and t["root"][3] == T.L
-    assert np.array_equal(t["root"][4:], T.corner)
+    assert np.array_equal(t["root"][4:7], T.corner)
 
 
 def assert_lists_equal(g, T, theta, n_crit):
@@ -233,3 +233,23 @@ def test_call_order_and_arguments():
     with pytest.raises(nb.NBError) as ei:
         ctx.build_tree(pos, torch.ones(11, dtype=torch.float32, device=dev))
     assert ei.value.code == -1
+
+
+def test_list_storage_sized_by_counting_walk():
+    """The first synchronising walk of a context only counts, so the list
+    storage is allocated once: capacity = longest list + 1/4, in 256s."""
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(16384, 5)
+    dev = torch.device("cuda")
+    P = torch.from_numpy(ps.pos).to(dev)
+    M = torch.from_numpy(ps.mass).to(dev)
+    ctx = nb.NBody(ps.n, eps=1 / 64, theta=0.75, n_crit=64)
+    ctx.build_tree(P, M)
+    ctx.walk_groups(0.75, 64)
+    st = ctx.stats()
+    need = st["max_list"]
+    assert st["list_capacity"] == max(256, (need + need // 4 + 255) // 256 * 256)
+    acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
+    ctx.forces(1 / 64, acc)
+    ctx.sync_status()
+    assert bool(torch.isfinite(acc).all())
