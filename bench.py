@@ -188,11 +188,12 @@ def allreduce_sum(x, ws):
 
 
 # ----------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(ps, w, seconds, seed=7):
+def cpu_oracle_rate(ps, w, seconds, seed=7, name=WORKLOAD):
     """Force evaluations/s of the CPU oracle (tree build + group walk + FP64
-    force sum) on a bounded sample: the full tree is built and timed, then a
-    random sample of groups is walked and summed for about `seconds`; the
-    build time is charged in proportion to the sampled particles."""
+    force sum) on a bounded sample: the full tree is built and timed, then
+    random groups are walked and summed in growing batches until about
+    `seconds` of CPU time are spent (or every group is done); the build time
+    is charged in proportion to the sampled particles."""
     import oracle
     t0 = time.perf_counter()
     T = oracle.Tree(ps.pos, ps.mass)
@@ -201,25 +202,25 @@ def cpu_oracle_rate(ps, w, seconds, seed=7):
     cnt = T.export()["count"][G]
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(G))
-    # calibrate on a small batch, then size the sample to the time budget
-    k0 = min(len(G), 64)
-    t0 = time.perf_counter()
-    _, _, pp, pc = T.forces(w["n_crit"], w["theta"], w["eps"], gsel=order[:k0])
-    t_cal = time.perf_counter() - t0
-    per_group = t_cal / k0
-    k1 = int(min(len(G) - k0, max(64, (seconds - t_build - t_cal) / max(per_group, 1e-9))))
-    sel = order[k0:k0 + k1]
-    t0 = time.perf_counter()
-    _, _, pp1, pc1 = T.forces(w["n_crit"], w["theta"], w["eps"], gsel=sel)
-    t_force = time.perf_counter() - t0
-    inter = pp + pc + pp1 + pc1
-    parts = int(cnt[order[:k0 + k1]].sum())
-    t_total = t_cal + t_force + t_build * parts / ps.n
+    budget = max(seconds - t_build, 1.0)
+    done, batch, inter, t_force = 0, 256, 0, 0.0
+    while done < len(G) and t_force < budget:
+        sel = order[done:done + batch]
+        t0 = time.perf_counter()
+        _, _, pp, pc = T.forces(w["n_crit"], w["theta"], w["eps"], gsel=sel)
+        t_force += time.perf_counter() - t0
+        inter += pp + pc
+        done += len(sel)
+        # aim the next batch at the remaining budget
+        rate = done / max(t_force, 1e-9)
+        batch = int(max(256, min(4 * batch, (budget - t_force) * rate)))
+    parts = int(cnt[order[:done]].sum())
+    t_total = t_force + t_build * parts / ps.n
     return dict(value=inter / t_total, unit=UNIT, cores=oracle.num_threads(),
                 kind="oracle",
-                sample=(f"{WORKLOAD}: full tree build ({t_build:.2f} s, charged pro rata) + "
-                        f"walk and FP64 force sum of {k0 + k1} random groups "
-                        f"({parts} particles, {inter} interactions) in {t_cal + t_force:.1f} s"),
+                sample=(f"{name}: full tree build ({t_build:.2f} s, charged pro rata) + "
+                        f"walk and FP64 force sum of {done} random groups "
+                        f"({parts} particles, {inter} interactions) in {t_force:.1f} s"),
                 interactions=int(inter), seconds=t_total)
 
 
@@ -408,7 +409,7 @@ def run_ours(args, ws, rank, local):
               for k, v in timing.items() if k != "launches"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(ps, w, args.cpu_seconds)
+        cpu = cpu_oracle_rate(ps, w, args.cpu_seconds, name=args.workload)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:

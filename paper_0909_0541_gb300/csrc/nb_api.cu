@@ -138,6 +138,9 @@ static void carve_context(nb_ctx *c, Arena &a)
     a.carve(&c->b_mass, NN);
     a.carve(&c->b_mx, 3 * NN);
     a.carve(&c->b_com, 3 * NN);
+    a.carve(&c->arrive, NN);
+    a.carve(&c->b_up, NN);
+    a.carve(&c->lcount, NN);
     a.carve(&c->gflag, NN + 1);
     a.carve(&c->gnode, N);
     a.carve(&c->gfirst, N);
@@ -179,7 +182,7 @@ static bool alloc_queues(nb_ctx *c, int64_t wq_cap)
 static const char *const SITE_NAME[SITE_N_] = {
     "none", "k_gather: caller index", "k_cells: node id", "k_parents: child id",
     "k_depth_scatter: level-order position", "k_bfs_records: node or particle",
-    "k_moments_level: child run", "groups: group or member range", "k_items: item index",
+    "k_moments_up: parent or child run", "groups: group or member range", "k_items: item index",
     "k_walk: queued node", "k_walk: child run", "k_force: item",
     "k_rs_scatter: destination"};
 

@@ -73,7 +73,7 @@ enum {
     SITE_PARENTS,     // child id outside the node count
     SITE_DEPTH,       // level-order position outside the node count
     SITE_RECORDS,     // preorder id or particle slot out of range
-    SITE_MOMENTS,     // child run outside the node count
+    SITE_MOMENTS,     // parent, child run or level out of range (bottom-up moments)
     SITE_GROUPS,      // group id or member range out of range
     SITE_ITEMS,       // work item index out of range
     SITE_WALK_NODE,   // queued node outside the node count
@@ -144,6 +144,9 @@ struct nb_ctx {
     int4 *w_b;
     float2 *w_c;
     double *b_mass, *b_mx, *b_com;  // FP64 moments in level order (mx, com: 3 per node)
+    int32_t *arrive;                 // finished children per cell (bottom-up moments)
+    int32_t *b_up;                   // parent's level-order index (-1 at a root)
+    int32_t *lcount;                 // particle-leaf children per cell
 
     // groups
     int32_t *gflag;   // per node flag, scanned in place to group ids (NN + 1)

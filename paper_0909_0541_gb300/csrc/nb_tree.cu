@@ -190,20 +190,14 @@ k_levels(const uint64_t *__restrict__ key, int64_t n, const int32_t *__restrict_
     ccount[a] = ca > cp ? ca - cp : 0;
 }
 
-__global__ void __launch_bounds__(256)
-k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ clev,
-        const int32_t *__restrict__ cstart, int4 *__restrict__ node_c,
-        int32_t *__restrict__ n_level, int32_t *__restrict__ n_first,
-        int32_t *__restrict__ n_count, int32_t *__restrict__ n_parent,
-        int32_t *__restrict__ n_nchild, int8_t *__restrict__ n_depth,
-        long long *__restrict__ cnt, const int32_t *__restrict__ sys,
-        const int64_t *__restrict__ sys_off, unsigned *__restrict__ err)
+// records of particle a's leaf and of the cells whose first particle is a;
+// returns the deepest such cell's level (-1 if none)
+__device__ __forceinline__ int cell_records(
+    int64_t a, int64_t n, const int8_t *__restrict__ clev, const int32_t *__restrict__ cstart,
+    int4 *__restrict__ node_c, int32_t *__restrict__ n_level, int32_t *__restrict__ n_first,
+    int32_t *__restrict__ n_count, int32_t *__restrict__ n_parent, int32_t *__restrict__ n_nchild,
+    int8_t *__restrict__ n_depth, long long *__restrict__ cnt, unsigned *__restrict__ err)
 {
-    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    // cells never reach past the particle's system (sorted rows of system s
-    // are the caller's rows sys_off[s] .. sys_off[s+1])
-    const int64_t nend = sys ? sys_off[sys[a] + 1] : n;
     const int32_t C = cstart[n];
     const int32_t total = C + (int32_t)n;
     if (a == 0) cnt[CNT_NODES] = total;
@@ -212,7 +206,7 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
     const int k = ca > cp ? ca - cp : 0;
     const int32_t base = cstart[a] + (int32_t)a;
     const int32_t leaf = base + k;
-    if (!nb_in(base >= 0 && leaf < total, cnt, err, SITE_CELLS, leaf)) return;
+    if (!nb_in(base >= 0 && leaf < total, cnt, err, SITE_CELLS, leaf)) return -1;
 
     // particle leaf: one below the deepest cell that holds it
     node_c[leaf] = make_int4(leaf + 1, 0, 0, 1);
@@ -224,15 +218,60 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
     if (k > 0) n_parent[leaf] = leaf - 1;
     else if (ca < 0 && cp < 0) n_parent[leaf] = -1;   // a one-particle system
 
-    // cells starting at a, deepest first; each run contains the deeper one
-    const uint64_t ka = key[a];
-    int64_t b = a;
-    int maxlev = -1;
+    // cells starting at a (their ends: k_cell_ends)
     for (int lev = ca; lev > cp; lev--) {
         const int32_t id = base + (lev - cp - 1);
+        n_level[id] = lev;
+        n_first[id] = (int32_t)a;
+        n_depth[id] = (int8_t)lev;
+        if (lev > cp + 1) n_parent[id] = id - 1;
+        else if (cp < 0) n_parent[id] = -1;   // a system's root
+    }
+    return k > 0 ? ca : -1;
+}
+
+__global__ void __launch_bounds__(256)
+k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ clev,
+        const int32_t *__restrict__ cstart, int4 *__restrict__ node_c,
+        int32_t *__restrict__ n_level, int32_t *__restrict__ n_first,
+        int32_t *__restrict__ n_count, int32_t *__restrict__ n_parent,
+        int32_t *__restrict__ n_nchild, int8_t *__restrict__ n_depth,
+        long long *__restrict__ cnt, const int32_t *__restrict__ sys,
+        const int64_t *__restrict__ sys_off, unsigned *__restrict__ err)
+{
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int deepest = -1;
+    if (a < n) deepest = cell_records(a, n, clev, cstart, node_c, n_level, n_first, n_count,
+                                      n_parent, n_nchild, n_depth, cnt, err);
+    // one atomic per warp for the deepest level (a single counter)
+    deepest = __reduce_max_sync(0xffffffffu, deepest);
+    if ((threadIdx.x & 31) == 0 && deepest >= 0) atomicMax(&cnt[CNT_MAXLEVEL], (long long)deepest);
+}
+
+
+// One thread per cell: the last particle b of the run of keys sharing the
+// cell's prefix (gallop from the first particle, then bisection, never past
+// the particle's system), its particle count and its preorder next,
+// S[b+1] + b + 1.  Cells are independent, so long runs near the root are
+// searched side by side instead of one after another.
+__global__ void __launch_bounds__(256)
+k_cell_ends(const uint64_t *__restrict__ key, int64_t n, const int32_t *__restrict__ cstart,
+            const int32_t *__restrict__ n_level, const int32_t *__restrict__ n_first,
+            int4 *__restrict__ node_c, int32_t *__restrict__ n_count,
+            long long *__restrict__ cnt, const int32_t *__restrict__ sys,
+            const int64_t *__restrict__ sys_off, unsigned *__restrict__ err)
+{
+    const int32_t total = (int32_t)cnt[CNT_NODES];
+    for (int32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < total;
+         id += gridDim.x * blockDim.x) {
+        const int lev = n_level[id];
+        if (lev < 0) continue;                     // a particle leaf
+        const int64_t a = n_first[id];
+        if (!nb_in(a >= 0 && a < n && lev <= NB_LEVELS, cnt, err, SITE_CELLS, id)) continue;
+        const int64_t nend = sys ? sys_off[sys[a] + 1] : n;
         const int shift = 63 - 3 * lev;
-        const uint64_t P = ka >> shift;
-        int64_t lo = b, step = 1, hi = b + 1;
+        const uint64_t P = key[a] >> shift;
+        int64_t lo = a, step = 1, hi = a + 1;
         while (hi < nend && (key[hi] >> shift) == P) {
             lo = hi;
             step <<= 1;
@@ -243,17 +282,9 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
             const int64_t mid = lo + ((hi - lo) >> 1);
             if ((key[mid] >> shift) == P) lo = mid; else hi = mid;
         }
-        b = lo;
-        node_c[id] = make_int4(cstart[b + 1] + (int32_t)b + 1, 0, 0, 0);
-        n_level[id] = lev;
-        n_first[id] = (int32_t)a;
-        n_count[id] = (int32_t)(b - a + 1);
-        n_depth[id] = (int8_t)lev;
-        if (lev > cp + 1) n_parent[id] = id - 1;
-        else if (cp < 0) n_parent[id] = -1;   // a system's root
-        if (lev > maxlev) maxlev = lev;
+        node_c[id] = make_int4(cstart[lo + 1] + (int32_t)lo + 1, 0, 0, 0);
+        n_count[id] = (int32_t)(lo - a + 1);
     }
-    if (maxlev >= 0) atomicMax(&cnt[CNT_MAXLEVEL], (long long)maxlev);
 }
 
 // every cell writes itself as parent of its children (child = id + 1, then
@@ -261,11 +292,13 @@ k_cells(const uint64_t *__restrict__ key, int64_t n, const int8_t *__restrict__ 
 __global__ void __launch_bounds__(256)
 k_parents(const int4 *__restrict__ node_c, long long *__restrict__ cnt,
           int32_t *__restrict__ n_parent, int32_t *__restrict__ n_nchild,
-          unsigned *__restrict__ err)
+          int32_t *__restrict__ arrive, int32_t *__restrict__ lcount, unsigned *__restrict__ err)
 {
     const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total;
          u += gridDim.x * blockDim.x) {
+        arrive[u] = 0;     // counters of the bottom-up moments (any index < total)
+        lcount[u] = 0;
         const int4 cu = node_c[u];
         if (cu.w) continue;
         int32_t ch = u + 1, nch = 0;
@@ -365,32 +398,52 @@ __global__ void k_level_start(const uint32_t *__restrict__ hist, int ntiles,
 }
 
 // level-order records: particle leaves get their position and FP64 moments,
-// cells their topology (moments follow level by level)
+// cells their topology and geometry -- side l = L / 2^level (w_c.x) and
+// geometric centre (held in b_com until the moments replace it); every node
+// gets its parent's level-order index and a zero arrival count
+__device__ __forceinline__ double pow2_neg(int k)   // 2^-k, 0 <= k <= 1022
+{
+    return __longlong_as_double((long long)(1023 - k) << 52);
+}
+
 __global__ void __launch_bounds__(256)
 k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ pid2bfs,
               const int4 *__restrict__ node_c, const int32_t *__restrict__ n_first,
-              const int32_t *__restrict__ n_nchild, const float4 *__restrict__ p_hi,
-              const float4 *__restrict__ p_lo, const double *__restrict__ x64,
-              long long *__restrict__ cnt, float4 *__restrict__ w_a,
-              float4 *__restrict__ w_d, int4 *__restrict__ w_b, float2 *__restrict__ w_c,
-              double *__restrict__ b_mass, double *__restrict__ b_mx, double *__restrict__ b_com,
-              int64_t n, unsigned *__restrict__ err)
+              const int32_t *__restrict__ n_nchild, const int32_t *__restrict__ n_parent,
+              const int8_t *__restrict__ n_depth, const uint64_t *__restrict__ key,
+              const double *__restrict__ roots, const int32_t *__restrict__ sys,
+              const float4 *__restrict__ p_hi, const float4 *__restrict__ p_lo,
+              const double *__restrict__ x64, long long *__restrict__ cnt,
+              float4 *__restrict__ w_a, float4 *__restrict__ w_d, int4 *__restrict__ w_b,
+              float2 *__restrict__ w_c, double *__restrict__ b_mass, double *__restrict__ b_mx,
+              double *__restrict__ b_com, int32_t *__restrict__ b_up,
+              int32_t *__restrict__ lcount, int64_t n, unsigned *__restrict__ err)
 {
     const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < total;
          b += gridDim.x * blockDim.x) {
+        b_up[b] = -1;
         const int32_t u = bfs2pid[b];
         if (!nb_in(u >= 0 && u < total, cnt, err, SITE_RECORDS, u)) continue;
         const int4 c = node_c[u];
         if (!nb_in(c.w || u + 1 < total, cnt, err, SITE_RECORDS, u)) continue;
+        const int32_t up = n_parent[u];
+        int32_t pb = -1;
+        if (up >= 0) {
+            if (!nb_in(up < total, cnt, err, SITE_RECORDS, u)) continue;
+            pb = pid2bfs[up];
+            if (!nb_in(pb >= 0 && pb < b, cnt, err, SITE_RECORDS, up)) continue;
+            b_up[b] = pb;
+        }
+        const int32_t slot = n_first[u];
+        if (!nb_in(slot >= 0 && slot < n, cnt, err, SITE_RECORDS, slot)) continue;
         if (c.w) {
-            const int32_t slot = n_first[u];
-            if (!nb_in(slot >= 0 && slot < n, cnt, err, SITE_RECORDS, slot)) continue;
             const float4 h = p_hi[slot];
             w_a[b] = h;
             w_d[b] = p_lo[slot];
             w_b[b] = make_int4(u, c.x, -1, 0);
             w_c[b] = make_float2(0.0f, 0.0f);
+            if (pb >= 0) atomicAdd(&lcount[pb], 1);   // a leaf child of pb (result unused)
             const double m = (double)h.w;
             b_mass[b] = m;
 #pragma unroll
@@ -401,63 +454,132 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
             }
         } else {
             w_b[b] = make_int4(u, c.x, pid2bfs[u + 1], n_nchild[u]);
+            const int depth = n_depth[u];
+            if (!nb_in(depth >= 0 && depth <= NB_LEVELS, cnt, err, SITE_RECORDS, u)) continue;
+            const double *root = roots + (sys ? 8 * (int64_t)sys[slot] : 0);
+            const double lc = __dmul_rn(root[3], pow2_neg(depth));
+            const uint64_t kf = key[slot];
+            const uint32_t cq[3] = {compact3(kf >> 2) >> (NB_LEVELS - depth),
+                                    compact3(kf >> 1) >> (NB_LEVELS - depth),
+                                    compact3(kf) >> (NB_LEVELS - depth)};
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+                b_com[3 * (int64_t)b + d] =
+                    __dadd_rn(root[4 + d], __dmul_rn(__dadd_rn((double)cq[d], 0.5), lc));
+            w_c[b] = make_float2(__double2float_rn(lc), 0.0f);
         }
     }
 }
 
-// FP64 moments of the cells at one depth (= level): fold the children, which
-// are contiguous one level down and in octant order, then COM = sum(m x) / M,
-// l = L / 2^level, s = |COM - geometric centre|.
-__global__ void __launch_bounds__(256)
-k_moments_level(int depth, const int32_t *__restrict__ level_start,
-                const uint64_t *__restrict__ key, const int32_t *__restrict__ n_first,
-                const double *__restrict__ roots, const int32_t *__restrict__ sys,
-                const int4 *__restrict__ w_b,
-                float4 *__restrict__ w_a, float4 *__restrict__ w_d, float2 *__restrict__ w_c,
-                double *__restrict__ b_mass, double *__restrict__ b_mx,
-                double *__restrict__ b_com, long long *__restrict__ cnt, int64_t n,
-                unsigned *__restrict__ err)
+// FP64 moments in two passes.
+//
+// (A) k_moments_up, bottom-up in one launch: M and sum(m x) of every cell,
+// folded over its children -- contiguous one level down, in octant order.
+// k_bfs_records counted each cell's particle-leaf children (lcount); a cell
+// whose children are all leaves is ready at once and is taken by the lane
+// that meets it.  A finished cell counts itself in at its parent (arrive);
+// the arrival that completes the parent's count (arrive + lcount = children)
+// folds the parent in turn.  A warp takes 32 consecutive nodes; after its
+// lanes' folds it fences once (their sums before their arrivals) and, if an
+// arrival completed a parent, once more (the children's sums before the
+// fold); children are read through L2.  No thread waits on another: an
+// arrival that does not complete its parent simply stops.
+//
+// (B) k_moments_fin, one thread per node: COM = sum(m x) / M, l and
+// s = |COM - geometric centre|, and the FP32 hi/lo split -- the FP64
+// divisions and square roots, with every lane of the warp busy.
+__device__ __forceinline__ void fold_sums(int32_t p, const int4 wp, double *b_mass,
+                                          double *b_mx)
 {
-    const int32_t lo_b = level_start[depth], hi_b = level_start[depth + 1];
-    const int32_t total = (int32_t)cnt[CNT_NODES];
-    for (int32_t b = lo_b + blockIdx.x * blockDim.x + threadIdx.x; b < hi_b;
-         b += gridDim.x * blockDim.x) {
-        const int4 wb = w_b[b];
-        if (wb.z < 0) continue;
-        if (!nb_in(wb.z > b && (int64_t)wb.z + wb.w <= total && wb.x >= 0 && wb.x < total &&
-                       n_first[wb.x] >= 0 && n_first[wb.x] < n,
-                   cnt, err, SITE_MOMENTS, b))
-            continue;
-        const double *root = roots + (sys ? 8 * (int64_t)sys[n_first[wb.x]] : 0);
-        const double lc = ldexp(root[3], -depth);
-        double M = 0.0, mx[3] = {0.0, 0.0, 0.0};
-        for (int32_t k = 0; k < wb.w; k++) {
-            const int64_t ch = wb.z + k;
-            M = __dadd_rn(M, b_mass[ch]);
+    double M = 0.0, mx[3] = {0.0, 0.0, 0.0};
+    for (int32_t k0 = 0; k0 < wp.w; k0 += 4) {
+        double cm[4], cx[4][3];
 #pragma unroll
-            for (int d = 0; d < 3; d++) mx[d] = __dadd_rn(mx[d], b_mx[3 * ch + d]);
+        for (int k = 0; k < 4; k++) {
+            const int64_t ch = (int64_t)wp.z + k0 + k;
+            const bool ok = k0 + k < wp.w;
+            cm[k] = ok ? __ldcg(&b_mass[ch]) : 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) cx[k][d] = ok ? __ldcg(&b_mx[3 * ch + d]) : 0.0;
         }
-        const uint64_t kf = key[n_first[wb.x]];
-        const uint32_t cq[3] = {compact3(kf >> 2) >> (NB_LEVELS - depth),
-                                compact3(kf >> 1) >> (NB_LEVELS - depth),
-                                compact3(kf) >> (NB_LEVELS - depth)};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (k0 + k >= wp.w) break;
+            M = __dadd_rn(M, cm[k]);
+#pragma unroll
+            for (int d = 0; d < 3; d++) mx[d] = __dadd_rn(mx[d], cx[k][d]);
+        }
+    }
+    b_mass[p] = M;
+#pragma unroll
+    for (int d = 0; d < 3; d++) b_mx[3 * (int64_t)p + d] = mx[d];
+}
+
+__global__ void __launch_bounds__(256)
+k_moments_up(const int4 *__restrict__ w_b, const int32_t *__restrict__ b_up,
+             const int32_t *__restrict__ lcount, double *b_mass, double *b_mx, int32_t *arrive,
+             long long *__restrict__ cnt, unsigned *__restrict__ err)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int32_t total = (int32_t)cnt[CNT_NODES];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * NB_WARP; base < total; base += nwarps * NB_WARP) {
+        const int32_t b0 = (int32_t)(base + lane);
+        int32_t p = -1;
+        int4 wp = make_int4(0, 0, -1, 0);
+        if (b0 < total) {
+            wp = w_b[b0];
+            if (wp.z >= 0 && lcount[b0] == wp.w) p = b0;   // a cell whose children are all leaves
+        }
+        for (int guard = 0; guard <= NB_DEPTHS && __any_sync(FULL, p >= 0); guard++) {
+            if (p >= 0 && !nb_in(wp.z > p && wp.w >= 1 && (int64_t)wp.z + wp.w <= total, cnt,
+                                 err, SITE_MOMENTS, p))
+                p = -1;
+            if (p >= 0) fold_sums(p, wp, b_mass, b_mx);
+            __threadfence();                       // the warp's sums before its arrivals
+            int32_t q = -1;
+            if (p >= 0) {
+                q = b_up[p];
+                if (q >= 0 && !nb_in(q < p, cnt, err, SITE_MOMENTS, p)) q = -1;
+                if (q >= 0) {
+                    wp = w_b[q];
+                    if (atomicAdd(&arrive[q], 1) + 1 + lcount[q] != wp.w) q = -1;
+                }
+            }
+            p = q;
+            if (__any_sync(FULL, p >= 0)) __threadfence();   // children's sums before folds
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_moments_fin(const int4 *__restrict__ w_b, const double *__restrict__ b_mass,
+              const double *__restrict__ b_mx, double *__restrict__ b_com,
+              float4 *__restrict__ w_a, float4 *__restrict__ w_d, float2 *__restrict__ w_c,
+              const long long *__restrict__ cnt)
+{
+    const int32_t total = (int32_t)cnt[CNT_NODES];
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < total;
+         b += gridDim.x * blockDim.x) {
+        if (w_b[b].z < 0) continue;               // particle leaves are final already
+        const double M = b_mass[b];
         double d2 = 0.0;
         float hi[3], lo[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double g = __dadd_rn(root[4 + d], __dmul_rn(__dadd_rn((double)cq[d], 0.5), lc));
-            const double com = M > 0.0 ? __ddiv_rn(mx[d], M) : g;
+            const double g = b_com[3 * (int64_t)b + d];   // geometric centre
+            const double com = M > 0.0 ? __ddiv_rn(b_mx[3 * (int64_t)b + d], M) : g;
             const double dd = __dsub_rn(com, g);
             d2 = __dadd_rn(d2, __dmul_rn(dd, dd));
             hi[d] = __double2float_rn(com);
             lo[d] = __double2float_rn(__dsub_rn(com, (double)hi[d]));
-            b_mx[3 * (int64_t)b + d] = mx[d];
             b_com[3 * (int64_t)b + d] = com;
         }
-        b_mass[b] = M;
         w_a[b] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(M));
         w_d[b] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-        w_c[b] = make_float2(__double2float_rn(lc), __double2float_rn(__dsqrt_rn(d2)));
+        w_c[b] = make_float2(w_c[b].x, __double2float_rn(__dsqrt_rn(d2)));
     }
 }
 
@@ -632,8 +754,13 @@ static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t 
                                             c->sys_off, c->err);
     nb_launched(c, "k_cells");
     const int gcap = c->num_sms * 16;
+    k_cell_ends<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
+        c->keys, n, c->cstart, c->n_level, c->n_first, c->node_c, c->n_count, c->cnt, sys_sorted,
+        c->sys_off, c->err);
+    nb_launched(c, "k_cell_ends");
     k_parents<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(c->node_c, c->cnt, c->n_parent,
-                                                               c->n_nchild, c->err);
+                                                               c->n_nchild, c->arrive, c->lcount,
+                                                               c->err);
     nb_launched(c, "k_parents");
     // level order
     const int nt = (int)c->dtiles;
@@ -647,16 +774,16 @@ static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t 
     k_level_start<<<1, 32, 0, s>>>(c->dhist, nt, c->level_start);
     nb_launched(c, "k_level_start");
     k_bfs_records<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
-        c->bfs2pid, c->pid2bfs, c->node_c, c->n_first, c->n_nchild, c->p_hi, c->p_lo, c->p_x64,
-        c->cnt, c->w_a, c->w_d, c->w_b, c->w_c, c->b_mass, c->b_mx, c->b_com, n, c->err);
+        c->bfs2pid, c->pid2bfs, c->node_c, c->n_first, c->n_nchild, c->n_parent, c->n_depth,
+        c->keys, c->root, sys_sorted, c->p_hi, c->p_lo, c->p_x64, c->cnt, c->w_a, c->w_d, c->w_b,
+        c->w_c, c->b_mass, c->b_mx, c->b_com, c->b_up, c->lcount, n, c->err);
     nb_launched(c, "k_bfs_records");
-    const int gl = c->num_sms * 8;
-    for (int d = NB_LEVELS; d >= 0; d--) {
-        k_moments_level<<<gl, 256, 0, s>>>(d, c->level_start, c->keys, c->n_first, c->root,
-                                           sys_sorted, c->w_b, c->w_a, c->w_d, c->w_c, c->b_mass, c->b_mx,
-                                           c->b_com, c->cnt, n, c->err);
-        nb_launched(c, "k_moments_level");
-    }
+    k_moments_up<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
+        c->w_b, c->b_up, c->lcount, c->b_mass, c->b_mx, c->arrive, c->cnt, c->err);
+    nb_launched(c, "k_moments_up");
+    k_moments_fin<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
+        c->w_b, c->b_mass, c->b_mx, c->b_com, c->w_a, c->w_d, c->w_c, c->cnt);
+    nb_launched(c, "k_moments_fin");
 }
 
 // ------------------------------------------------------------ groups
