@@ -1,15 +1,19 @@
 // nb_force.cu -- Eq. (gravity) summed over each group's interaction list.
 //
-// Work item = (group, up to 64 consecutive members).  One warp takes one
-// item from a global queue; each lane owns R target particles (R = 2, or 1
-// when the item's targets fit one 32-wide row) as FP32 coordinates relative
-// to the group centre.  The warp streams sources in tiles of 32 records: one
-// coalesced 16-byte load per lane into a per-warp shared-memory tile, then
-// every lane reads each record by broadcast and applies it to its R targets:
+// Work items cut a group's members into 64-target items (two targets per
+// lane) while 64 or more remain, then one 32-target item if more than 32
+// remain, then a tail of at most 32 targets rounded up to a power of two m'.
+// A tail runs as S = 32 / m' source streams: the warp is S rows of m' lanes,
+// stream s takes entries s*W .. s*W+W-1 (W = 32/S) of every 32-record tile,
+// and the streams' sums are combined with shuffles at the end -- so small
+// groups keep every lane busy.  One warp takes one item from a global queue;
+// targets are FP32 coordinates relative to the group centre.  Sources are
+// staged 32 at a time: one coalesced 16-byte load per lane into a per-warp
+// shared-memory tile, then broadcast reads.  Per interaction:
 //   dx = xj - xi (3 FADD); r2 = eps^2 + dx.dx (3 FFMA); ri = rsqrt(r2) (MUFU);
 //   mr = mj ri; mr3 = mr ri ri (3 FMUL); a += mr3 dx (3 FFMA); phi -= mr (FADD)
-// i.e. 13 FP32-pipe instructions and one MUFU per interaction.  This stays on
-// the CUDA cores: there is no dense contraction to hand to the tensor cores.
+// i.e. 13 FP32-pipe instructions and one MUFU.  This stays on the CUDA
+// cores: there is no dense contraction to hand to the tensor cores.
 //
 // Two phases per item: (1) the group's list (particles and accepted cells
 // outside the group), unmasked; (2) the group's own members, read from the
@@ -22,7 +26,10 @@
 
 #define F_T 256
 #define F_WARPS (F_T / NB_WARP)
-#define ITEM_ONE_ROW (1 << 30)
+// item word: first member | log2(source streams) << 27 | two-targets-per-lane flag
+#define ITEM_R2 (1 << 30)
+#define ITEM_LS_SHIFT 27
+#define ITEM_MEMBER_MASK ((1 << 27) - 1)
 
 enum { MODE_FP32 = 0, MODE_COMP = 1, MODE_F64 = 2 };
 
@@ -84,14 +91,14 @@ __device__ __forceinline__ void interact(const float4 q, float xi, float yi, flo
     }
 }
 
-// one 32-record tile against the lane's R targets
-template <int MODE, bool GUARD, bool MASK, int R>
+// NJ records of a tile against the lane's R targets
+template <int MODE, bool GUARD, bool MASK, int R, int NJ>
 __device__ __forceinline__ void tile_pass(const float4 *tile, int32_t j0, const float *xi,
                                           const float *yi, const float *zi, const int32_t *kk,
                                           float eps2, Acc<MODE> *A, Acc<MODE> *T)
 {
 #pragma unroll 8
-    for (int j = 0; j < NB_WARP; j++) {
+    for (int j = 0; j < NJ; j++) {
         const float4 q = tile[j];
 #pragma unroll
         for (int r = 0; r < R; r++) {
@@ -114,7 +121,32 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int32_t j0, const 
     }
 }
 
-template <int MODE, bool GUARD, int R>
+template <int MODE>
+__device__ __forceinline__ void stream_sum(Acc<MODE> &A, int o)
+{
+    const unsigned FULL = 0xffffffffu;
+    if constexpr (MODE == MODE_F64) {
+        A.dx += __shfl_xor_sync(FULL, A.dx, o);
+        A.dy += __shfl_xor_sync(FULL, A.dy, o);
+        A.dz += __shfl_xor_sync(FULL, A.dz, o);
+        A.dp += __shfl_xor_sync(FULL, A.dp, o);
+    } else {
+        A.x += __shfl_xor_sync(FULL, A.x, o);
+        A.y += __shfl_xor_sync(FULL, A.y, o);
+        A.z += __shfl_xor_sync(FULL, A.z, o);
+        A.p += __shfl_xor_sync(FULL, A.p, o);
+        if constexpr (MODE == MODE_COMP) {
+            A.cx += __shfl_xor_sync(FULL, A.cx, o);
+            A.cy += __shfl_xor_sync(FULL, A.cy, o);
+            A.cz += __shfl_xor_sync(FULL, A.cz, o);
+            A.cp += __shfl_xor_sync(FULL, A.cp, o);
+        }
+    }
+}
+
+// R targets per lane (R = 2 only with S = 1); S source streams: lane l is
+// target row l % W of stream l / W, W = 32 / S
+template <int MODE, bool GUARD, int R, int S>
 __device__ __forceinline__ void force_item(
     int32_t g, int32_t i0, float4 *tile, const int32_t *__restrict__ gfirst,
     const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
@@ -124,7 +156,9 @@ __device__ __forceinline__ void force_item(
     float *__restrict__ acc, float *__restrict__ pot, long long *__restrict__ cnt,
     unsigned *__restrict__ err)
 {
+    constexpr int W = NB_WARP / S;
     const int lane = threadIdx.x & 31;
+    const int row = lane % W, stream = lane / W;
     const int32_t f = gfirst[g], ng = gcount[g];
     if (!(f >= 0 && ng >= 1 && (int64_t)f + ng <= n && i0 >= 0 && i0 < ng)) {
         if (lane == 0) nb_bad(cnt, err, SITE_FORCE, g);
@@ -144,7 +178,7 @@ __device__ __forceinline__ void force_item(
     Acc<MODE> A[R], T[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        const int32_t k = i0 + r * NB_WARP + lane;
+        const int32_t k = i0 + r * W + row;
         ok[r] = k < ng;
         kk[r] = k;
         slot[r] = f + (ok[r] ? k : ng - 1);
@@ -161,7 +195,8 @@ __device__ __forceinline__ void force_item(
         const int32_t jj = j0 + lane;
         tile[lane] = jj < len ? src[jj] : pad;
         __syncwarp();
-        tile_pass<MODE, GUARD, false, R>(tile, j0, xi, yi, zi, kk, eps2, A, T);
+        tile_pass<MODE, GUARD, false, R, W>(tile + stream * W, j0 + stream * W, xi, yi, zi, kk,
+                                            eps2, A, T);
         __syncwarp();
     }
     // (2) the group's own members, j != i
@@ -175,8 +210,14 @@ __device__ __forceinline__ void force_item(
             tile[lane] = pad;
         }
         __syncwarp();
-        tile_pass<MODE, GUARD, true, R>(tile, j0, xi, yi, zi, kk, eps2, A, T);
+        tile_pass<MODE, GUARD, true, R, W>(tile + stream * W, j0 + stream * W, xi, yi, zi, kk,
+                                           eps2, A, T);
         __syncwarp();
+    }
+    if constexpr (S > 1) {
+#pragma unroll
+        for (int o = W; o < NB_WARP; o <<= 1) stream_sum<MODE>(A[0], o);
+        if (stream != 0) return;
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -223,17 +264,27 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ gfirst,
         it = __shfl_sync(FULL, it, 0);
         if (it >= nitems) break;
         const int32_t g = items[2 * (int64_t)it], word = items[2 * (int64_t)it + 1];
-        const int32_t i0 = word & ~ITEM_ONE_ROW;
+        const int32_t i0 = word & ITEM_MEMBER_MASK;
         if (g < 0 || g >= ngroups) {
             if (lane == 0) nb_bad(cnt, err, SITE_FORCE, g);
             continue;
         }
-        if (word & ITEM_ONE_ROW)
-            force_item<MODE, GUARD, 1>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo,
-                                       perm, list_xm, cap, alloc, n, eps2, acc, pot, cnt, err);
-        else
-            force_item<MODE, GUARD, 2>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo,
-                                       perm, list_xm, cap, alloc, n, eps2, acc, pot, cnt, err);
+#define NB_FORCE_ITEM(R, S)                                                                   \
+    force_item<MODE, GUARD, R, S>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo, perm, \
+                                  list_xm, cap, alloc, n, eps2, acc, pot, cnt, err)
+        if (word & ITEM_R2) {
+            NB_FORCE_ITEM(2, 1);
+        } else {
+            switch ((word >> ITEM_LS_SHIFT) & 7) {
+            case 0: NB_FORCE_ITEM(1, 1); break;
+            case 1: NB_FORCE_ITEM(1, 2); break;
+            case 2: NB_FORCE_ITEM(1, 4); break;
+            case 3: NB_FORCE_ITEM(1, 8); break;
+            case 4: NB_FORCE_ITEM(1, 16); break;
+            default: NB_FORCE_ITEM(1, 32); break;
+            }
+        }
+#undef NB_FORCE_ITEM
     }
 }
 

@@ -820,6 +820,18 @@ k_group_scatter(const int32_t *__restrict__ gid, const int32_t *__restrict__ n_f
     }
 }
 
+// Force work items of a group of m members (iblock = 64: two targets per
+// lane, or 32): full items of iblock, then (iblock 64) one 32-target item
+// if more than 32 remain, then a tail of <= 32 targets, run as 32/m' source
+// streams with m' the tail rounded up to a power of two.  Word: first member
+// | log2(streams) << 27 | (1 << 30 for a 64-target item).
+__device__ __forceinline__ int32_t item_count(int32_t m, int iblock)
+{
+    int32_t c = m / iblock, rem = m - c * iblock;
+    if (iblock == 64 && rem > 32) { c++; rem -= 32; }
+    return c + (rem > 0 ? 1 : 0);
+}
+
 // group box over the members' FP32 positions, its FP32 centre, FP32
 // 1/theta, and the number of force work items of the group
 __global__ void __launch_bounds__(256)
@@ -851,7 +863,7 @@ k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gc
         gbox[3 * (int64_t)g] = make_float4(lx, ly, lz, 0.0f);
         gbox[3 * (int64_t)g + 1] = make_float4(hx, hy, hz, 0.0f);
         gbox[3 * (int64_t)g + 2] = make_float4(cx, cy, cz, invth);
-        item_cnt[g] = (m + iblock - 1) / iblock;
+        item_cnt[g] = item_count(m, iblock);
     }
 }
 
@@ -864,13 +876,26 @@ k_items(const int32_t *__restrict__ item_off, const int32_t *__restrict__ gcount
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G;
          g += gridDim.x * blockDim.x) {
         const int32_t o = item_off[g], m = gcount[g];
-        if (!nb_in(o >= 0 && (int64_t)o + (m + iblock - 1) / iblock <= max_items, cnt, err,
+        if (!nb_in(o >= 0 && (int64_t)o + item_count(m, iblock) <= max_items, cnt, err,
                    SITE_ITEMS, g))
             continue;
-        for (int32_t i0 = 0, k = 0; i0 < m; i0 += iblock, k++) {
+        int32_t i0 = 0, k = 0;
+        for (; m - i0 >= iblock; i0 += iblock, k++) {
             items[2 * (int64_t)(o + k)] = g;
-            // bit 30: the item's targets fit one 32-wide row
-            items[2 * (int64_t)(o + k) + 1] = i0 | (m - i0 <= NB_WARP ? (1 << 30) : 0);
+            items[2 * (int64_t)(o + k) + 1] = i0 | (iblock == 64 ? (1 << 30) : 0);
+        }
+        int32_t rem = m - i0;
+        if (iblock == 64 && rem > 32) {
+            items[2 * (int64_t)(o + k)] = g;
+            items[2 * (int64_t)(o + k) + 1] = i0;
+            i0 += 32;
+            rem -= 32;
+            k++;
+        }
+        if (rem > 0) {
+            const int lg = rem > 1 ? 32 - __clz(rem - 1) : 0;   // log2 of rem rounded up
+            items[2 * (int64_t)(o + k)] = g;
+            items[2 * (int64_t)(o + k) + 1] = i0 | ((5 - lg) << 27);
         }
     }
 }
