@@ -50,8 +50,102 @@ __device__ __forceinline__ bool far_enough(const float4 &a, float l, float s,
 //   5 ln(|box centre - root centre| / L + 1e-6);  6 ln(list length + 1)
 //   7 accepted cells / list length;  8-10 ln(min, mean, max distance from the
 //   box centre to accepted cells' centres of mass / L + 1e-7);  11 depth / 22
+// one frontier node's level-order records
+struct NodeRec {
+    int32_t b;
+    bool valid;
+    int4 wb;     // preorder id, preorder next, first child, children
+    float4 a;    // centre of mass (hi), mass
+    float2 wc;   // l, s
+    float4 d;    // centre of mass (lo)
+};
+
 template <bool PROBE>
-__global__ void __launch_bounds__(WALK_T)
+__device__ __forceinline__ NodeRec load_node(int32_t i, int32_t na, const int32_t *qin,
+                                             const float4 *__restrict__ w_a,
+                                             const float4 *__restrict__ w_d,
+                                             const int4 *__restrict__ w_b,
+                                             const float2 *__restrict__ w_c, int32_t total,
+                                             long long *cnt, unsigned *err)
+{
+    NodeRec r;
+    r.b = 0;
+    if (i < na) r.b = qin[i];
+    r.valid = i < na && nb_in(r.b >= 0 && r.b < total, cnt, err, SITE_WALK_NODE, r.b);
+    if (r.valid) {
+        r.wb = w_b[r.b];
+        r.a = w_a[r.b];
+        r.wc = w_c[r.b];
+        if (!PROBE) r.d = w_d[r.b];
+    }
+    return r;
+}
+
+// the opening test of one chunk of 32 frontier nodes (one per lane): emit
+// particles and accepted cells to the list (ballot + popc), queue the
+// children of opened cells (warp prefix sum)
+template <bool PROBE>
+__device__ __forceinline__ void visit_node(
+    const NodeRec r, int32_t gb, int32_t gpid, const float4 &blo, const float4 &bhi,
+    const float4 &bc, float invth, int32_t total, long long *cnt, unsigned *err, int lane,
+    unsigned lt, int64_t room, int64_t base, int32_t *__restrict__ list_id,
+    float4 *__restrict__ list_xm, int32_t *qout, int64_t wq_cap, int32_t &len, int32_t &ncell,
+    int32_t &nb, float &dmin, float &dmax, float &dsum)
+{
+    const unsigned FULL = 0xffffffffu;
+    bool emit = false, cell_emit = false, open = false;
+    int32_t fc = 0, nch = 0;
+    if (r.valid) {
+        fc = r.wb.z;
+        if (r.b != gb) {
+            if (fc < 0) {
+                emit = true;
+            } else {
+                const bool holds = (r.wb.x <= gpid) && (gpid < r.wb.y);
+                if (!holds && far_enough(r.a, r.wc.x, r.wc.y, blo, bhi, invth)) {
+                    emit = true;
+                    cell_emit = true;
+                } else if (nb_in(fc > r.b && (int64_t)fc + r.wb.w <= total, cnt, err,
+                                 SITE_WALK_CHILD, r.b)) {
+                    open = true;
+                    nch = r.wb.w;
+                }
+            }
+        }
+    }
+    const unsigned em = __ballot_sync(FULL, emit);
+    if (PROBE && cell_emit) {
+        const float dx = r.a.x - bc.x, dy = r.a.y - bc.y, dz = r.a.z - bc.z;
+        const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+        dmin = fminf(dmin, d);
+        dmax = fmaxf(dmax, d);
+        dsum += d;
+    }
+    if (!PROBE && emit) {
+        const int32_t pos = len + __popc(em & lt);
+        if (pos < room) {
+            list_id[base + pos] = r.wb.x;
+            list_xm[base + pos] = make_float4(nb_rel(r.a.x, r.d.x, bc.x), nb_rel(r.a.y, r.d.y, bc.y),
+                                              nb_rel(r.a.z, r.d.z, bc.z), r.a.w);
+        }
+    }
+    len += __popc(em);
+    ncell += __popc(__ballot_sync(FULL, cell_emit));
+    int32_t incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int32_t start = nb + incl - nch;
+    if (open)
+        for (int32_t k = 0; k < nch; k++)
+            if (start + k < wq_cap) qout[start + k] = fc + k;
+    nb += __shfl_sync(FULL, incl, 31);
+}
+
+template <bool PROBE>
+__global__ void __launch_bounds__(WALK_T, 4)
 k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
        const int4 *__restrict__ w_b, const float2 *__restrict__ w_c,
        const int32_t *__restrict__ pid2bfs, const int32_t *__restrict__ gnode,
@@ -99,66 +193,14 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
         int depth_guard = 0;
         while (na > 0) {
             int32_t nb = 0;
+            // one chunk of 32 frontier nodes per iteration; each lane fetches all
+            // of its node's records at once (one round trip after the queue)
             for (int32_t i0 = 0; i0 < na; i0 += NB_WARP) {
-                const int32_t i = i0 + lane;
-                bool emit = false, cell_emit = false, open = false;
-                int32_t b = 0, pid = 0, fc = 0, nch = 0;
-                float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < na) b = qin[i];
-                const bool inb = i < na && nb_in(b >= 0 && b < total, cnt, err, SITE_WALK_NODE, b);
-                if (inb) {
-                    const int4 wb = w_b[b];
-                    a = w_a[b];
-                    pid = wb.x;
-                    fc = wb.z;
-                    if (b != gb) {
-                        if (fc < 0) {
-                            emit = true;
-                        } else {
-                            const bool holds = (wb.x <= gpid) && (gpid < wb.y);
-                            const float2 wc = w_c[b];
-                            if (!holds && far_enough(a, wc.x, wc.y, blo, bhi, invth)) {
-                                emit = true;
-                                cell_emit = true;
-                            } else if (nb_in(fc > b && (int64_t)fc + wb.w <= total, cnt, err,
-                                             SITE_WALK_CHILD, b)) {
-                                open = true;
-                                nch = wb.w;
-                            }
-                        }
-                    }
-                }
-                const unsigned em = __ballot_sync(FULL, emit);
-                if (PROBE && cell_emit) {
-                    const float dx = a.x - bc.x, dy = a.y - bc.y, dz = a.z - bc.z;
-                    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
-                    dmin = fminf(dmin, d);
-                    dmax = fmaxf(dmax, d);
-                    dsum += d;
-                }
-                if (!PROBE && emit) {
-                    const int32_t pos = len + __popc(em & lt);
-                    if (pos < room) {
-                        const float4 d = w_d[b];
-                        list_id[base + pos] = pid;
-                        list_xm[base + pos] = make_float4(nb_rel(a.x, d.x, bc.x), nb_rel(a.y, d.y, bc.y),
-                                                          nb_rel(a.z, d.z, bc.z), a.w);
-                    }
-                }
-                len += __popc(em);
-                ncell += __popc(__ballot_sync(FULL, cell_emit));
-                // children of opened cells go to the next level's queue
-                int32_t incl = nch;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int32_t y = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int32_t start = nb + incl - nch;
-                if (open)
-                    for (int32_t k = 0; k < nch; k++)
-                        if (start + k < wq_cap) qout[start + k] = fc + k;
-                nb += __shfl_sync(FULL, incl, 31);
+                const NodeRec r = load_node<PROBE>(i0 + lane, na, qin, w_a, w_d, w_b, w_c, total,
+                                                   cnt, err);
+                visit_node<PROBE>(r, gb, gpid, blo, bhi, bc, invth, total, cnt, err, lane, lt, room,
+                                  base, list_id, list_xm, qout, wq_cap, len, ncell, nb, dmin, dmax,
+                                  dsum);
             }
             if (nb > qmax) qmax = nb;
             if (nb > wq_cap) { bad |= NB_EF_QUEUE; break; }
