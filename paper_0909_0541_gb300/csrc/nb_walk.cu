@@ -26,6 +26,10 @@
 
 #define WALK_T 256
 #define WALK_WARPS (WALK_T / NB_WARP)
+// the first WQ_SMEM positions of each frontier queue live in shared memory
+// (8 warps x 2 queues x 768 x 4 B = 48 KB per block); longer frontiers
+// continue at the same positions in the warp's global queue
+#define WQ_SMEM 768
 
 // Eq. (mac) for a group: squared FP32 distance from the cell's centre of
 // mass to the group box against (l / theta + s)^2, every operation rounded
@@ -61,7 +65,8 @@ struct NodeRec {
 };
 
 template <bool PROBE>
-__device__ __forceinline__ NodeRec load_node(int32_t i, int32_t na, const int32_t *qin,
+__device__ __forceinline__ NodeRec load_node(int32_t i, int32_t na, const int32_t *qin_s,
+                                             const int32_t *qin,
                                              const float4 *__restrict__ w_a,
                                              const float4 *__restrict__ w_d,
                                              const int4 *__restrict__ w_b,
@@ -70,7 +75,7 @@ __device__ __forceinline__ NodeRec load_node(int32_t i, int32_t na, const int32_
 {
     NodeRec r;
     r.b = 0;
-    if (i < na) r.b = qin[i];
+    if (i < na) r.b = i < WQ_SMEM ? qin_s[i] : qin[i];
     r.valid = i < na && nb_in(r.b >= 0 && r.b < total, cnt, err, SITE_WALK_NODE, r.b);
     if (r.valid) {
         r.wb = w_b[r.b];
@@ -89,7 +94,8 @@ __device__ __forceinline__ void visit_node(
     const NodeRec r, int32_t gb, int32_t gpid, const float4 &blo, const float4 &bhi,
     const float4 &bc, float invth, int32_t total, long long *cnt, unsigned *err, int lane,
     unsigned lt, int64_t room, int64_t base, int32_t *__restrict__ list_id,
-    float4 *__restrict__ list_xm, int32_t *qout, int64_t wq_cap, int32_t &len, int32_t &ncell,
+    float4 *__restrict__ list_xm, int32_t *qout_s, int32_t *qout, int64_t wq_cap,
+    int32_t &len, int32_t &ncell,
     int32_t &nb, float &dmin, float &dmax, float &dsum)
 {
     const unsigned FULL = 0xffffffffu;
@@ -139,8 +145,11 @@ __device__ __forceinline__ void visit_node(
     }
     const int32_t start = nb + incl - nch;
     if (open)
-        for (int32_t k = 0; k < nch; k++)
-            if (start + k < wq_cap) qout[start + k] = fc + k;
+        for (int32_t k = 0; k < nch; k++) {
+            const int32_t pos = start + k;
+            if (pos < WQ_SMEM) qout_s[pos] = fc + k;
+            else if (pos < wq_cap) qout[pos] = fc + k;
+        }
     nb += __shfl_sync(FULL, incl, 31);
 }
 
@@ -163,6 +172,9 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
     const int64_t gw = (int64_t)blockIdx.x * WALK_WARPS + (threadIdx.x >> 5);
     int32_t *const qa = wq + gw * 2 * wq_cap;
     int32_t *const qb = qa + wq_cap;
+    __shared__ int32_t sq[WALK_WARPS][2 * WQ_SMEM];
+    int32_t *const qa_s = sq[threadIdx.x >> 5];
+    int32_t *const qb_s = qa_s + WQ_SMEM;
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     const int32_t total = (int32_t)cnt[CNT_NODES];
     long long pp = 0, pc = 0, tot = 0;
@@ -184,10 +196,10 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
         const int64_t room = alloc - base < cap ? (alloc - base > 0 ? alloc - base : 0) : cap;
         int32_t len = 0, ncell = 0;
         float dmin = INFINITY, dmax = 0.0f, dsum = 0.0f;
-        int32_t *qin = qa, *qout = qb;
+        int32_t *qin = qa, *qout = qb, *qin_s = qa_s, *qout_s = qb_s;
         // the root of the group's system (node 0 for a single system)
         const int32_t gsys = sys_sorted ? sys_sorted[gfirst[g]] : 0;
-        if (lane == 0) qin[0] = sys_root ? sys_root[gsys] : 0;
+        if (lane == 0) qin_s[0] = sys_root ? sys_root[gsys] : 0;
         __syncwarp();
         int32_t na = 1;
         int depth_guard = 0;
@@ -196,16 +208,17 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
             // one chunk of 32 frontier nodes per iteration; each lane fetches all
             // of its node's records at once (one round trip after the queue)
             for (int32_t i0 = 0; i0 < na; i0 += NB_WARP) {
-                const NodeRec r = load_node<PROBE>(i0 + lane, na, qin, w_a, w_d, w_b, w_c, total,
-                                                   cnt, err);
+                const NodeRec r = load_node<PROBE>(i0 + lane, na, qin_s, qin, w_a, w_d, w_b, w_c,
+                                                   total, cnt, err);
                 visit_node<PROBE>(r, gb, gpid, blo, bhi, bc, invth, total, cnt, err, lane, lt, room,
-                                  base, list_id, list_xm, qout, wq_cap, len, ncell, nb, dmin, dmax,
-                                  dsum);
+                                  base, list_id, list_xm, qout_s, qout, wq_cap, len, ncell, nb, dmin,
+                                  dmax, dsum);
             }
             if (nb > qmax) qmax = nb;
             if (nb > wq_cap) { bad |= NB_EF_QUEUE; break; }
             __syncwarp();
             int32_t *t = qin; qin = qout; qout = t;
+            t = qin_s; qin_s = qout_s; qout_s = t;
             na = nb;
             if (++depth_guard > NB_DEPTHS + 1) { bad |= NB_EF_WALK; break; }
         }
@@ -271,6 +284,12 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
 int nb_walk_warps(nb_ctx *c)
 {
     int blocks = 0, bp = 0;
+    // the queue heads are 48 KB of shared memory per block: ask for the
+    // largest shared-memory carveout so four blocks fit on an SM
+    cudaFuncSetAttribute(k_walk<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_walk<false>, WALK_T, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, k_walk<true>, WALK_T, 0);
     if (bp < blocks) blocks = bp;
