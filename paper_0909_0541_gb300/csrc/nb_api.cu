@@ -131,10 +131,7 @@ static void carve_context(nb_ctx *c, Arena &a)
     a.carve(&c->pid2bfs, NN);
     a.carve(&c->dhist, NB_DEPTHS * c->dtiles + 1);
     a.carve(&c->level_start, NB_DEPTHS + 1);
-    a.carve(&c->w_a, NN);
-    a.carve(&c->w_d, NN);
-    a.carve(&c->w_b, NN);
-    a.carve(&c->w_c, NN);
+    a.carve(&c->wrec, NN);
     a.carve(&c->b_mass, NN);
     a.carve(&c->b_mx, 3 * NN);
     a.carve(&c->b_com, 3 * NN);
@@ -876,8 +873,9 @@ int nb_copy_tree(nb_ctx *c, double *root, uint64_t *keys, int32_t *perm, int32_t
                                 c->stream) != cudaSuccess ||
                 cudaMemcpyAsync(bc, c->b_com, sizeof(double) * 3 * nn, cudaMemcpyDeviceToHost,
                                 c->stream) != cudaSuccess ||
-                cudaMemcpyAsync(wc, c->w_c, sizeof(float2) * nn, cudaMemcpyDeviceToHost,
-                                c->stream) != cudaSuccess ||
+                cudaMemcpy2DAsync(wc, sizeof(float2), &c->wrec[0].c, sizeof(nb_wrec),
+                                  sizeof(float2), nn, cudaMemcpyDeviceToHost,
+                                  c->stream) != cudaSuccess ||
                 cudaStreamSynchronize(c->stream) != cudaSuccess))
         rc = NB_ERR_CUDA;
     for (int64_t u = 0; !rc && u < nn; u++) {

@@ -10,11 +10,7 @@
 //                     number of children, depth
 //   walk records      level order ("bfs": nodes sorted by depth, preorder
 //                     inside a depth), so the children of a cell are one
-//                     contiguous run:
-//                       w_a float4 (centre of mass hi part, FP32 mass)
-//                       w_b int4   (pid, preorder next, first child, children)
-//                       w_c float2 (l, s)
-//                       w_d float4 (centre of mass lo part, 0)
+//                     contiguous run; one 64-byte nb_wrec per node
 //                     and FP64 mass, first moment and centre of mass
 //   groups            gnode (pid), first slot, size, box 3 x float4 (lo, hi,
 //                     centre + 1/theta), list length, cell entries
@@ -83,6 +79,30 @@ enum {
     SITE_N_
 };
 
+// The walk's view of one node, in level order, as one 64-byte record so a
+// visited node touches one cache line: centre of mass as FP32 hi part and
+// FP32 mass; FP32 lo part; preorder id, preorder next, first child (level
+// order; -1 for a particle leaf), number of children; side l and offset s.
+struct __align__(64) nb_wrec {
+    float4 a;
+    float4 d;
+    int4 b;
+    float2 c;
+    float2 pad;
+};
+
+// writes in whole 32-byte sectors: (a, d) and (b, c + pad)
+__device__ __forceinline__ void nb_wrec_put_lo(nb_wrec *w, float4 a, float4 d)
+{
+    w->a = a;
+    w->d = d;
+}
+__device__ __forceinline__ void nb_wrec_put_hi(nb_wrec *w, int4 b, float l, float s)
+{
+    w->b = b;
+    *reinterpret_cast<float4 *>(&w->c) = make_float4(l, s, 0.0f, 0.0f);
+}
+
 struct nb_ctx {
     int device;
     cudaStream_t stream;
@@ -140,9 +160,7 @@ struct nb_ctx {
     uint32_t *dhist;       // depth histogram per tile, scanned (NB_DEPTHS x tiles + 1)
     int64_t dtiles;
     int32_t *level_start;  // NB_DEPTHS + 1
-    float4 *w_a, *w_d;
-    int4 *w_b;
-    float2 *w_c;
+    struct nb_wrec *wrec;  // one 64-byte record per node (see nb_wrec)
     double *b_mass, *b_mx, *b_com;  // FP64 moments in level order (mx, com: 3 per node)
     int32_t *arrive;                 // finished children per cell (bottom-up moments)
     int32_t *b_up;                   // parent's level-order index (-1 at a root)

@@ -398,7 +398,7 @@ __global__ void k_level_start(const uint32_t *__restrict__ hist, int ntiles,
 }
 
 // level-order records: particle leaves get their position and FP64 moments,
-// cells their topology and geometry -- side l = L / 2^level (w_c.x) and
+// cells their topology and geometry -- side l = L / 2^level (c.x) and
 // geometric centre (held in b_com until the moments replace it); every node
 // gets its parent's level-order index and a zero arrival count
 __device__ __forceinline__ double pow2_neg(int k)   // 2^-k, 0 <= k <= 1022
@@ -414,8 +414,7 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
               const double *__restrict__ roots, const int32_t *__restrict__ sys,
               const float4 *__restrict__ p_hi, const float4 *__restrict__ p_lo,
               const double *__restrict__ x64, long long *__restrict__ cnt,
-              float4 *__restrict__ w_a, float4 *__restrict__ w_d, int4 *__restrict__ w_b,
-              float2 *__restrict__ w_c, double *__restrict__ b_mass, double *__restrict__ b_mx,
+              nb_wrec *__restrict__ wrec, double *__restrict__ b_mass, double *__restrict__ b_mx,
               double *__restrict__ b_com, int32_t *__restrict__ b_up,
               int32_t *__restrict__ lcount, int64_t n, unsigned *__restrict__ err)
 {
@@ -439,10 +438,8 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
         if (!nb_in(slot >= 0 && slot < n, cnt, err, SITE_RECORDS, slot)) continue;
         if (c.w) {
             const float4 h = p_hi[slot];
-            w_a[b] = h;
-            w_d[b] = p_lo[slot];
-            w_b[b] = make_int4(u, c.x, -1, 0);
-            w_c[b] = make_float2(0.0f, 0.0f);
+            nb_wrec_put_lo(&wrec[b], h, p_lo[slot]);
+            nb_wrec_put_hi(&wrec[b], make_int4(u, c.x, -1, 0), 0.0f, 0.0f);
             if (pb >= 0) atomicAdd(&lcount[pb], 1);   // a leaf child of pb (result unused)
             const double m = (double)h.w;
             b_mass[b] = m;
@@ -453,7 +450,7 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
                 b_mx[3 * (int64_t)b + d] = __dmul_rn(m, x);
             }
         } else {
-            w_b[b] = make_int4(u, c.x, pid2bfs[u + 1], n_nchild[u]);
+            const int4 wb = make_int4(u, c.x, pid2bfs[u + 1], n_nchild[u]);
             const int depth = n_depth[u];
             if (!nb_in(depth >= 0 && depth <= NB_LEVELS, cnt, err, SITE_RECORDS, u)) continue;
             const double *root = roots + (sys ? 8 * (int64_t)sys[slot] : 0);
@@ -466,7 +463,7 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
             for (int d = 0; d < 3; d++)
                 b_com[3 * (int64_t)b + d] =
                     __dadd_rn(root[4 + d], __dmul_rn(__dadd_rn((double)cq[d], 0.5), lc));
-            w_c[b] = make_float2(__double2float_rn(lc), 0.0f);
+            nb_wrec_put_hi(&wrec[b], wb, __double2float_rn(lc), 0.0f);
         }
     }
 }
@@ -516,7 +513,7 @@ __device__ __forceinline__ void fold_sums(int32_t p, const int4 wp, double *b_ma
 }
 
 __global__ void __launch_bounds__(256)
-k_moments_up(const int4 *__restrict__ w_b, const int32_t *__restrict__ b_up,
+k_moments_up(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ b_up,
              const int32_t *__restrict__ lcount, double *b_mass, double *b_mx, int32_t *arrive,
              long long *__restrict__ cnt, unsigned *__restrict__ err)
 {
@@ -530,7 +527,7 @@ k_moments_up(const int4 *__restrict__ w_b, const int32_t *__restrict__ b_up,
         int32_t p = -1;
         int4 wp = make_int4(0, 0, -1, 0);
         if (b0 < total) {
-            wp = w_b[b0];
+            wp = wrec[b0].b;
             if (wp.z >= 0 && lcount[b0] == wp.w) p = b0;   // a cell whose children are all leaves
         }
         for (int guard = 0; guard <= NB_DEPTHS && __any_sync(FULL, p >= 0); guard++) {
@@ -544,7 +541,7 @@ k_moments_up(const int4 *__restrict__ w_b, const int32_t *__restrict__ b_up,
                 q = b_up[p];
                 if (q >= 0 && !nb_in(q < p, cnt, err, SITE_MOMENTS, p)) q = -1;
                 if (q >= 0) {
-                    wp = w_b[q];
+                    wp = wrec[q].b;
                     if (atomicAdd(&arrive[q], 1) + 1 + lcount[q] != wp.w) q = -1;
                 }
             }
@@ -555,15 +552,16 @@ k_moments_up(const int4 *__restrict__ w_b, const int32_t *__restrict__ b_up,
 }
 
 __global__ void __launch_bounds__(256)
-k_moments_fin(const int4 *__restrict__ w_b, const double *__restrict__ b_mass,
+k_moments_fin(nb_wrec *__restrict__ wrec, const double *__restrict__ b_mass,
               const double *__restrict__ b_mx, double *__restrict__ b_com,
-              float4 *__restrict__ w_a, float4 *__restrict__ w_d, float2 *__restrict__ w_c,
               const long long *__restrict__ cnt)
 {
     const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < total;
          b += gridDim.x * blockDim.x) {
-        if (w_b[b].z < 0) continue;               // particle leaves are final already
+        const int4 wb = wrec[b].b;
+        if (wb.z < 0) continue;                   // particle leaves are final already
+        const float lcf = wrec[b].c.x;
         const double M = b_mass[b];
         double d2 = 0.0;
         float hi[3], lo[3];
@@ -577,9 +575,9 @@ k_moments_fin(const int4 *__restrict__ w_b, const double *__restrict__ b_mass,
             lo[d] = __double2float_rn(__dsub_rn(com, (double)hi[d]));
             b_com[3 * (int64_t)b + d] = com;
         }
-        w_a[b] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(M));
-        w_d[b] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-        w_c[b] = make_float2(w_c[b].x, __double2float_rn(__dsqrt_rn(d2)));
+        nb_wrec_put_lo(&wrec[b], make_float4(hi[0], hi[1], hi[2], __double2float_rn(M)),
+                       make_float4(lo[0], lo[1], lo[2], 0.0f));
+        nb_wrec_put_hi(&wrec[b], wb, lcf, __double2float_rn(__dsqrt_rn(d2)));
     }
 }
 
@@ -775,14 +773,14 @@ static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t 
     nb_launched(c, "k_level_start");
     k_bfs_records<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
         c->bfs2pid, c->pid2bfs, c->node_c, c->n_first, c->n_nchild, c->n_parent, c->n_depth,
-        c->keys, c->root, sys_sorted, c->p_hi, c->p_lo, c->p_x64, c->cnt, c->w_a, c->w_d, c->w_b,
-        c->w_c, c->b_mass, c->b_mx, c->b_com, c->b_up, c->lcount, n, c->err);
+        c->keys, c->root, sys_sorted, c->p_hi, c->p_lo, c->p_x64, c->cnt, c->wrec, c->b_mass,
+        c->b_mx, c->b_com, c->b_up, c->lcount, n, c->err);
     nb_launched(c, "k_bfs_records");
     k_moments_up<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
-        c->w_b, c->b_up, c->lcount, c->b_mass, c->b_mx, c->arrive, c->cnt, c->err);
+        c->wrec, c->b_up, c->lcount, c->b_mass, c->b_mx, c->arrive, c->cnt, c->err);
     nb_launched(c, "k_moments_up");
     k_moments_fin<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
-        c->w_b, c->b_mass, c->b_mx, c->b_com, c->w_a, c->w_d, c->w_c, c->cnt);
+        c->wrec, c->b_mass, c->b_mx, c->b_com, c->cnt);
     nb_launched(c, "k_moments_fin");
 }
 

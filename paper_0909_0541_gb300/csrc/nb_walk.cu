@@ -67,10 +67,7 @@ struct NodeRec {
 template <bool PROBE>
 __device__ __forceinline__ NodeRec load_node(int32_t i, int32_t na, const int32_t *qin_s,
                                              const int32_t *qin,
-                                             const float4 *__restrict__ w_a,
-                                             const float4 *__restrict__ w_d,
-                                             const int4 *__restrict__ w_b,
-                                             const float2 *__restrict__ w_c, int32_t total,
+                                             const nb_wrec *__restrict__ wrec, int32_t total,
                                              long long *cnt, unsigned *err)
 {
     NodeRec r;
@@ -78,10 +75,11 @@ __device__ __forceinline__ NodeRec load_node(int32_t i, int32_t na, const int32_
     if (i < na) r.b = i < WQ_SMEM ? qin_s[i] : qin[i];
     r.valid = i < na && nb_in(r.b >= 0 && r.b < total, cnt, err, SITE_WALK_NODE, r.b);
     if (r.valid) {
-        r.wb = w_b[r.b];
-        r.a = w_a[r.b];
-        r.wc = w_c[r.b];
-        if (!PROBE) r.d = w_d[r.b];
+        const nb_wrec *w = wrec + r.b;     // one 64-byte line
+        r.wb = w->b;
+        r.a = w->a;
+        r.wc = w->c;
+        if (!PROBE) r.d = w->d;
     }
     return r;
 }
@@ -155,8 +153,7 @@ __device__ __forceinline__ void visit_node(
 
 template <bool PROBE>
 __global__ void __launch_bounds__(WALK_T, 4)
-k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
-       const int4 *__restrict__ w_b, const float2 *__restrict__ w_c,
+k_walk(const nb_wrec *__restrict__ wrec,
        const int32_t *__restrict__ pid2bfs, const int32_t *__restrict__ gnode,
        const int32_t *__restrict__ gcount, const float4 *__restrict__ gbox,
        long long *__restrict__ cnt, int32_t *__restrict__ glen, int32_t *__restrict__ gcells,
@@ -208,7 +205,7 @@ k_walk(const float4 *__restrict__ w_a, const float4 *__restrict__ w_d,
             // one chunk of 32 frontier nodes per iteration; each lane fetches all
             // of its node's records at once (one round trip after the queue)
             for (int32_t i0 = 0; i0 < na; i0 += NB_WARP) {
-                const NodeRec r = load_node<PROBE>(i0 + lane, na, qin_s, qin, w_a, w_d, w_b, w_c,
+                const NodeRec r = load_node<PROBE>(i0 + lane, na, qin_s, qin, wrec,
                                                    total, cnt, err);
                 visit_node<PROBE>(r, gb, gpid, blo, bhi, bc, invth, total, cnt, err, lane, lt, room,
                                   base, list_id, list_xm, qout_s, qout, wq_cap, len, ncell, nb, dmin,
@@ -304,7 +301,7 @@ void nb_launch_walk(nb_ctx *c)
     cudaMemsetAsync(&c->cnt[CNT_QMAX], 0, sizeof(long long), c->stream);
     const int blocks = c->walk_warps / WALK_WARPS;
     k_walk<false><<<blocks, WALK_T, 0, c->stream>>>(
-        c->w_a, c->w_d, c->w_b, c->w_c, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
+        c->wrec, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
         c->glen, c->gcells, c->list_id, c->list_xm, c->list_cap, c->list_alloc, c->wq,
         c->wq_cap, c->err, nullptr, c->root, c->n_depth, c->gfirst,
         c->nsys > 1 ? c->sys_sorted : nullptr, c->nsys > 1 ? c->sys_root : nullptr);
@@ -318,7 +315,7 @@ void nb_launch_probe(nb_ctx *c, float *feat)
     cudaMemsetAsync(&c->cnt[CNT_WALK_Q], 0, sizeof(long long), c->stream);
     const int blocks = c->walk_warps / WALK_WARPS;
     k_walk<true><<<blocks, WALK_T, 0, c->stream>>>(
-        c->w_a, c->w_d, c->w_b, c->w_c, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
+        c->wrec, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
         c->glen, c->gcells, nullptr, nullptr, 0, 0, c->wq, c->wq_cap, c->err, feat, c->root,
         c->n_depth, c->gfirst, c->nsys > 1 ? c->sys_sorted : nullptr,
         c->nsys > 1 ? c->sys_root : nullptr);
