@@ -563,12 +563,23 @@ k_moments_fin(nb_wrec *__restrict__ wrec, const double *__restrict__ b_mass,
         if (wb.z < 0) continue;                   // particle leaves are final already
         const float lcf = wrec[b].c.x;
         const double M = b_mass[b];
+        // COM = sum(m x) / M, correctly rounded: one correctly rounded
+        // reciprocal y = RN(1/M) shared by the three quotients, then
+        // Markstein's correction q = RN(q0 + RN(a - M q0) y), q0 = RN(a y),
+        // which gives RN(a / M) (Markstein 1990, IBM J. Res. Dev. 34(1))
+        const double y = M > 0.0 ? __drcp_rn(M) : 0.0;
         double d2 = 0.0;
         float hi[3], lo[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const double g = b_com[3 * (int64_t)b + d];   // geometric centre
-            const double com = M > 0.0 ? __ddiv_rn(b_mx[3 * (int64_t)b + d], M) : g;
+            const double a = b_mx[3 * (int64_t)b + d];
+            double com = g;
+            if (M > 0.0) {
+                const double q0 = __dmul_rn(a, y);
+                const double r = __fma_rn(-q0, M, a);
+                com = __fma_rn(r, y, q0);
+            }
             const double dd = __dsub_rn(com, g);
             d2 = __dadd_rn(d2, __dmul_rn(dd, dd));
             hi[d] = __double2float_rn(com);
