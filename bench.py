@@ -48,10 +48,12 @@ def parse():
     ap.add_argument("--n-crit", type=int, default=None)
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--precision", default="fp32")
-    ap.add_argument("--judge-targets", type=int, default=2048)
+    ap.add_argument("--judge-targets", type=int, default=8192)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph-steps", type=int, default=100,
+                    help="KDK steps per captured graph (batch512 workload)")
     return ap.parse_args()
 
 
@@ -372,20 +374,30 @@ def run_ours(args, ws, rank, local):
                "d2h_bytes_per_step": int(hpos.numel() * 8 + hvel.numel() * 8),
                "ms_per_step": ms_e2e / args.steps}
 
-    # ---- accuracy against the FP64 direct-sum judge (outside the timed regions)
+    # ---- accuracy against the FP64 direct-sum judge (outside the timed regions):
+    # the same tree and lists summed in each accumulation mode (precision
+    # study), each force pass timed on the library's stream
+    precision = {}
     with torch.cuda.stream(stream):
         ctx.set_sync_checks(True)
         ctx.build_tree(pos0, mass)
         ctx.walk_groups(w["theta"], w["n_crit"])
-        acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
-        ctx.forces(w["eps"], acc, None, args.precision)
         g = torch.Generator().manual_seed(99)
         tg = torch.randperm(n, generator=g)[: args.judge_targets].to(dev)
         aj, _ = nb.direct_sum(pos0, mass, w["eps"], tg, stream=stream)
-        torch.cuda.synchronize()
-    d = (acc[tg].double() - aj).norm(dim=1) / aj.norm(dim=1)
-    d = d.cpu().numpy()
-    accuracy = {"median_rel_err": float(np.median(d)), "p99_rel_err": float(np.percentile(d, 99)),
+        acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        for mode in ("fp32", "fp32_comp", "fp64acc"):
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            ctx.forces(w["eps"], acc, None, mode)
+            p1.record(stream)
+            torch.cuda.synchronize()
+            d = ((acc[tg].double() - aj).norm(dim=1) / aj.norm(dim=1)).cpu().numpy()
+            precision[mode] = {"median_rel_err": float(np.median(d)),
+                               "p99_rel_err": float(np.percentile(d, 99)),
+                               "force_ms": p0.elapsed_time(p1)}
+    accuracy = {"median_rel_err": precision[args.precision]["median_rel_err"],
+                "p99_rel_err": precision[args.precision]["p99_rel_err"],
                 "targets": int(args.judge_targets), "judge": "nb_direct_sum (FP64 GPU direct sum)"}
 
     # ---- roofline of the dominant kernel (force sum)
@@ -427,6 +439,7 @@ def run_ours(args, ws, rank, local):
             "interactions_per_step": inter / args.steps,
             "particle_forces_per_s": ws * n * args.steps / (ms_max / 1e3),
             "accuracy": accuracy,
+            "precision_study": precision,
             "phases_ms": phases,
             "gpu_launches": int(timing["launches"]),
             "roofline": roofline,
@@ -440,11 +453,84 @@ def run_ours(args, ws, rank, local):
     ctx.close()
 
 
+
+# ----------------------------------------------------------------- batched systems
+def run_batch(args, ws, rank, local):
+    """512 independent Plummer / Hernquist systems (N log-uniform in
+    [1024, 65536]) in one forest: the autotuner picks n_crit and the force
+    item width, 100 KDK steps are captured in one CUDA graph, and each of
+    --steps timed replays runs those 100 steps."""
+    import torch
+
+    import nbsynth
+    import paper_0909_0541_gb300 as nb
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    systems = nbsynth.batched_systems(512)
+    off = np.r_[0, np.cumsum([ps.n for ps in systems])].astype(np.int64)
+    n = int(off[-1])
+    eps, theta, dt, nsteps = 1.0 / 64, 0.75, 1.0 / 128, args.graph_steps
+    P = torch.from_numpy(np.concatenate([ps.pos for ps in systems])).to(dev)
+    V = torch.from_numpy(np.concatenate([ps.vel for ps in systems])).to(dev)
+    M = torch.from_numpy(np.concatenate([ps.mass for ps in systems])).to(dev)
+    O = torch.from_numpy(off).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    ctx = nb.NBody(n, eps=eps, theta=theta, n_crit=64, max_systems=len(systems),
+                   sync_checks=True, stream=stream)
+    with torch.cuda.stream(stream):
+        best, rows, table = ctx.autotune(P, M, eps, theta, n_crits=(32, 64, 128, 256, 512),
+                                         reps=2, offsets=O)
+        ctx.leapfrog_step_batched(P, V, M, O, dt)      # sizes the lists, caches a(x)
+        ctx.set_sync_checks(False)
+        ctx.graph_capture_leapfrog(P, V, M, dt, nsteps, offsets=O)
+        for _ in range(args.warmup):
+            ctx.graph_launch()
+        ctx.sync_status()
+        st0 = ctx.stats()
+        sampler = ClockSampler(local)
+        sampler.start()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = sampler.mark()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = sampler.mark()
+        clocks = sampler.stop(t0, t1)
+        ctx.sync_status()
+        st1 = ctx.stats()
+    ms = e0.elapsed_time(e1)
+    inter = (st1["n_pp_total"] - st0["n_pp_total"]) + (st1["n_pc_total"] - st0["n_pc_total"])
+    kdk = args.steps * nsteps
+    line = {
+        "metric": "force evals/s, 512 batched systems, KDK steps in one CUDA graph",
+        "value": inter / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": kdk,
+        "warmup": args.warmup * nsteps, "ms_per_step": ms / kdk, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch512", "n": n, "systems": len(systems), "theta": theta,
+                   "eps": eps, "dt": dt, "graph_steps": nsteps,
+                   "autotuned": {"n_crit": best, "item_targets": 32 * rows},
+                   "l2": "inputs larger than L2"},
+        "autotune_ms": {f"{k[0]}/{32 * k[1]}": v for k, v in table.items()},
+        "interactions_per_step": inter / kdk,
+        "particle_steps_per_s": n * kdk / (ms / 1e3),
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batch512":
+        run_batch(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -99,7 +99,8 @@ def _load():
     L.nb_build_tree_batched.argtypes = [vp, vp, vp, vp, i64, i64]
     L.nb_graph_capture_leapfrog.argtypes = [vp, vp, vp, vp, vp, i64, i64, C.c_double, i32]
     L.nb_graph_launch.argtypes = [vp]
-    L.nb_autotune.argtypes = [vp, vp, vp, i64, C.c_float, C.c_float, vp, i32, i32, vp, vp, vp]
+    L.nb_autotune.argtypes = [vp, vp, vp, vp, i64, i64, C.c_float, C.c_float, vp, i32, i32, vp, vp,
+                              vp]
     L.nb_leapfrog_step_batched.argtypes = [vp, vp, vp, vp, vp, i64, i64, C.c_double]
     L.nb_copy_group_lengths.argtypes = [vp, vp, i64]
     L.nb_walk_groups_learned.argtypes = [vp, i32, vp, C.c_float, vp]
@@ -242,14 +243,19 @@ class NBody:
     def graph_launch(self):
         _check(_lib.nb_graph_launch(self._h), "nb_graph_launch")
 
-    def autotune(self, pos, mass, eps, theta, n_crits=(32, 64, 128, 256, 512), reps=3):
-        """(best n_crit, best item rows, {(n_crit, rows): ms})."""
+    def autotune(self, pos, mass, eps, theta, n_crits=(32, 64, 128, 256, 512), reps=3,
+                 offsets=None):
+        """(best n_crit, best item rows, {(n_crit, rows): ms}); offsets (int64
+        CUDA tensor of n_systems + 1 row offsets) tunes a batch of systems."""
         import torch
         cand = np.asarray(n_crits, np.int32)
         ms = np.zeros(2 * len(cand), np.float32)
         bn, br = C.c_int(0), C.c_int(0)
+        nsys = 1 if offsets is None else int(offsets.shape[0]) - 1
         _check(_lib.nb_autotune(self._h, _dptr(pos, torch.float64, 3, "pos"),
-                                _dptr(mass, torch.float32, None, "mass"), int(pos.shape[0]),
+                                _dptr(mass, torch.float32, None, "mass"),
+                                _dptr(offsets, torch.int64, None, "offsets"), nsys,
+                                int(pos.shape[0]),
                                 float(eps), float(theta), _hptr(cand), len(cand), int(reps),
                                 C.byref(bn), C.byref(br), _hptr(ms)), "nb_autotune")
         table = {(int(c), r + 1): float(ms[2 * k + r]) for k, c in enumerate(cand) for r in range(2)}

@@ -700,12 +700,13 @@ int nb_graph_launch(nb_ctx *c)
     return finish(c);
 }
 
-int nb_autotune(nb_ctx *c, const double *pos, const float *mass, int64_t n, float eps,
-                float theta, const int *n_crit, int ncand, int reps, int *best_n_crit,
-                int *best_rows, float *ms_out)
+int nb_autotune(nb_ctx *c, const double *pos, const float *mass, const int64_t *offsets,
+                int64_t nsys, int64_t n, float eps, float theta, const int *n_crit, int ncand,
+                int reps, int *best_n_crit, int *best_rows, float *ms_out)
 {
     if (!c || !pos || !mass || !n_crit || ncand < 1 || reps < 1 || n < 1) return NB_ERR_INVALID_ARG;
-    int rc = nb_build_tree(c, pos, mass, n);
+    int rc = offsets ? nb_build_tree_batched(c, pos, mass, offsets, nsys, n)
+                     : nb_build_tree(c, pos, mass, n);
     if (rc) return rc;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

@@ -130,3 +130,27 @@ def test_autotune_picks_a_candidate():
     acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
     ctx.forces(1 / 64, acc)
     assert torch.isfinite(acc).all()
+
+
+def test_autotune_a_forest(oracle_lib):
+    """The autotuner on a batch: it builds the forest, keeps the fastest
+    (n_crit, item width), and a batched step with it still matches every
+    system's oracle step."""
+    import paper_0909_0541_gb300 as nb
+    systems, off, pos, vel, mass = batch(10, 9, 300, 4000)
+    dev = torch.device("cuda")
+    eps, theta, dt = 1 / 64, 0.6, 1 / 128
+    P = torch.from_numpy(pos).to(dev)
+    V = torch.from_numpy(vel).to(dev)
+    M = torch.from_numpy(mass).to(dev)
+    O = torch.from_numpy(off).to(dev)
+    ctx = nb.NBody(len(pos), eps=eps, theta=theta, n_crit=64, max_systems=len(systems))
+    best, rows, table = ctx.autotune(P, M, eps, theta, n_crits=(16, 64, 256), reps=2, offsets=O)
+    assert best in (16, 64, 256) and rows in (1, 2)
+    assert table[(best, rows)] == min(table.values())
+    ctx.leapfrog_step_batched(P, V, M, O, dt)
+    for k, ps in enumerate(systems):
+        xo, vo, ao = oracle_lib.leapfrog(ps.pos, ps.vel, ps.mass, eps, dt, 1, use_tree=True,
+                                         theta=theta, n_crit=best)
+        amax = np.abs(ao).max() if len(ao) > 1 else 1.0
+        assert np.max(np.abs(P.cpu().numpy()[off[k]:off[k + 1]] - xo)) <= dt * dt * 1e-4 * amax + 1e-15
