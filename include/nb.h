@@ -216,6 +216,12 @@ int nb_get_timing(nb_ctx *ctx, double *ms_host, int64_t *calls_host,
 
 /* Synchronise the stream and return (and clear) any latched device error. */
 int nb_sync_status(nb_ctx *ctx);
+/* Self-test of the bounded wait used where one warp waits for others (the
+ * bottom-up moments of nb_build_tree): one warp waits, polling at most
+ * spin_limit times, for a count that nothing raises.  Synchronises and
+ * returns the latched status, NB_ERR_INTERNAL when the wait gave up as
+ * designed; the context stays usable.  No tree state is touched. */
+int nb_selftest_wait(nb_ctx *ctx, unsigned spin_limit);
 /* Synchronise and fill *st. */
 int nb_get_stats(nb_ctx *ctx, nb_stats *st);
 

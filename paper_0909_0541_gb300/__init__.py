@@ -36,7 +36,7 @@ EXPORTED = [
     "nb_mlp_forward", "nb_mlp_grad", "nb_mlp_train", "nb_group_features",
     "nb_walk_groups_learned", "nb_group_errors", "nb_theta_labels",
     "nb_copy_group_lengths", "nb_build_tree_batched", "nb_leapfrog_step_batched",
-    "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune",
+    "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune", "nb_selftest_wait",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -87,6 +87,7 @@ def _load():
     L.nb_leapfrog_acc.argtypes = [vp, vp]
     L.nb_direct_sum.argtypes = [vp, vp, i64, C.c_double, vp, i64, vp, vp, vp]
     L.nb_sync_status.argtypes = [vp]
+    L.nb_selftest_wait.argtypes = [vp, C.c_uint]
     L.nb_get_stats.argtypes = [vp, C.POINTER(nb_stats)]
     L.nb_copy_tree.argtypes = [vp] * 14
     L.nb_copy_groups.argtypes = [vp] * 6
@@ -328,6 +329,11 @@ class NBody:
 
     def sync_status(self):
         _check(_lib.nb_sync_status(self._h), "nb_sync_status")
+
+    def selftest_wait(self, spin_limit: int) -> int:
+        """Status of one warp's bounded wait on a count nothing raises
+        (NB_ERR_INTERNAL when the wait gave up as designed)."""
+        return int(_lib.nb_selftest_wait(self._h, int(spin_limit)))
 
     def stats(self) -> dict:
         st = nb_stats()

@@ -138,6 +138,9 @@ static void carve_context(nb_ctx *c, Arena &a)
     a.carve(&c->arrive, NN);
     a.carve(&c->b_up, NN);
     a.carve(&c->lcount, NN);
+    a.carve(&c->cbkt, NN);
+    a.carve(&c->cbkt_cnt, 2 * NB_CBKT);
+    a.carve(&c->clist, c->clist_len);
     a.carve(&c->gflag, NN + 1);
     a.carve(&c->gnode, N);
     a.carve(&c->gfirst, N);
@@ -149,6 +152,8 @@ static void carve_context(nb_ctx *c, Arena &a)
     a.carve(&c->gtheta, N);
     a.carve(&c->items, 2 * c->max_items);
     a.carve(&c->item_cnt, N + 1);
+    a.carve(&c->item_order, c->max_items);
+    a.carve(&c->item_bkt, 2 * NB_IBKT);
     a.carve(&c->acc_cache, 3 * N);
     a.carve(&c->pot_cache, N);
     a.carve(&c->err, 1);
@@ -179,9 +184,9 @@ static bool alloc_queues(nb_ctx *c, int64_t wq_cap)
 static const char *const SITE_NAME[SITE_N_] = {
     "none", "k_gather: caller index", "k_cells: node id", "k_parents: child id",
     "k_depth_scatter: level-order position", "k_bfs_records: node or particle",
-    "k_moments_up: parent or child run", "groups: group or member range", "k_items: item index",
-    "k_walk: queued node", "k_walk: child run", "k_force: item",
-    "k_rs_scatter: destination"};
+    "k_moments: cell, parent or child run", "groups: group or member range",
+    "k_items: item index", "k_walk: queued node", "k_walk: child run", "k_force: item",
+    "k_rs_scatter: destination", "k_moments: wait for children ran out"};
 
 static int err_code(unsigned bits)
 {
@@ -345,6 +350,7 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
     c->scan_bsum_len = (scan_n + 2047) / 2048 + 2;
     c->bbox_blocks = c->num_sms * 4;
     c->max_items = N + N / 64 + 2;
+    c->clist_len = NN + 32 * (int64_t)NB_CBKT;
     c->max_sys = cfg->max_systems > 1 ? cfg->max_systems : 1;
     Arena sizing;
     carve_context(c, sizing);
@@ -566,9 +572,12 @@ int nb_walk_groups_learned(nb_ctx *c, int n_crit, const float *params, float fal
     if (!c || !params || n_crit < 1 || !(fallback >= 0.f)) return NB_ERR_INVALID_ARG;
     if (!c->has_tree) return NB_ERR_STATE;
     if (c->n == 0) return nb_walk_groups(c, fallback, n_crit, nullptr);
+    // the probe walk and the network count as part of the walk phase
+    const int tk = phase_begin(c);
     int rc = probe(c, n_crit);
     if (rc) return rc;
     nb_launch_mlp_infer(c, params, c->gfeat, c->gtheta, fallback);
+    phase_end(c, tk, NB_PHASE_WALK);
     if (theta_out) {
         // group count is known on the device only; copy the whole slot range
         CK(cudaMemcpyAsync(theta_out, c->gtheta, sizeof(float) * c->n, cudaMemcpyDeviceToDevice,
@@ -803,6 +812,20 @@ int nb_sync_status(nb_ctx *c)
     if (!c) return NB_ERR_INVALID_ARG;
     if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
     return sync_read(c);
+}
+
+int nb_selftest_wait(nb_ctx *c, unsigned spin_limit)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    int rc = sync_read(c);   // start from a clear error word
+    if (rc) return rc;
+    nb_launch_wait_probe(c, spin_limit);
+    if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
+    rc = sync_read(c);
+    // the probe's report is not a failure of the tree: clear the latched site
+    CK(cudaMemsetAsync(&c->cnt[CNT_BAD_SITE], 0, 2 * sizeof(long long), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return rc;
 }
 
 int nb_get_stats(nb_ctx *c, nb_stats *st)

@@ -20,6 +20,13 @@
 // sorted particle arrays and converted to the same group-relative FP32
 // coordinates, with the j == i term dropped by index.  Padding records are
 // massless and far away.
+//
+// Queue order: after the walk, when every list length is known, the items
+// are counting-sorted by estimated cost (records x targets per lane, in
+// quarter-octave buckets) so that the queue hands out the costliest items
+// first and the kernel does not end on one warp finishing a long list.  An
+// item's result does not depend on when it runs, so the order changes
+// timing only.
 #include <float.h>
 
 #include "nb_internal.cuh"
@@ -239,9 +246,86 @@ __device__ __forceinline__ void force_item(
     }
 }
 
+// cost bucket of an item, 0 = costliest: 4 x log2 of (list + members) x
+// targets per lane / source streams, in quarter octaves
+__device__ __forceinline__ int item_bucket(const int32_t *__restrict__ items,
+                                           const int32_t *__restrict__ gcount,
+                                           const int32_t *__restrict__ glen, int32_t it,
+                                           int32_t ngroups)
+{
+    const int32_t g = items[2 * (int64_t)it], word = items[2 * (int64_t)it + 1];
+    if (g < 0 || g >= ngroups) return NB_IBKT - 1;   // k_force reports the bad item
+    const uint32_t len = (uint32_t)max(glen[g], 0) + (uint32_t)max(gcount[g], 0);
+    const int ls = (word & ITEM_R2) ? 0 : min((word >> ITEM_LS_SHIFT) & 7, 5);
+    uint32_t w = ((word & ITEM_R2) ? 2u * len : len) >> ls;
+    if (w < 1) w = 1;
+    const int e = 31 - __clz(w);
+    const int q = e >= 2 ? (int)((w >> (e - 2)) & 3u) : (int)((w << (2 - e)) & 3u);
+    const int b = 4 * e + q;
+    return NB_IBKT - 1 - min(b, NB_IBKT - 1);
+}
+
+__device__ __forceinline__ int32_t force_items(const long long *cnt, int64_t max_items)
+{
+    const long long v = cnt[CNT_ITEMS];
+    return (int32_t)(v < max_items ? v : max_items);
+}
+
+__global__ void __launch_bounds__(256)
+k_item_hist(const int32_t *__restrict__ items, const int32_t *__restrict__ gcount,
+            const int32_t *__restrict__ glen, const long long *__restrict__ cnt,
+            int64_t max_items, int32_t *__restrict__ bkt)
+{
+    __shared__ int32_t h[NB_IBKT];
+    if (threadIdx.x < NB_IBKT) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int32_t nitems = force_items(cnt, max_items), ngroups = (int32_t)cnt[CNT_GROUPS];
+    for (int32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+         it += gridDim.x * blockDim.x)
+        atomicAdd(&h[item_bucket(items, gcount, glen, it, ngroups)], 1);
+    __syncthreads();
+    if (threadIdx.x < NB_IBKT && h[threadIdx.x]) atomicAdd(&bkt[threadIdx.x], h[threadIdx.x]);
+}
+
+// bkt[0..NB_IBKT) bucket sizes, bkt[NB_IBKT..2 NB_IBKT) fill cursors (zeroed)
+__global__ void __launch_bounds__(256)
+k_item_order(const int32_t *__restrict__ items, const int32_t *__restrict__ gcount,
+             const int32_t *__restrict__ glen, long long *__restrict__ cnt, int64_t max_items,
+             int32_t *__restrict__ bkt, int32_t *__restrict__ order, unsigned *__restrict__ err)
+{
+    static_assert(NB_IBKT <= 256, "one bucket per thread");
+    __shared__ int32_t start[NB_IBKT];
+    {
+        int32_t all;
+        const int32_t st = nb_block_scan256(threadIdx.x < NB_IBKT ? bkt[threadIdx.x] : 0, &all);
+        if (threadIdx.x < NB_IBKT) start[threadIdx.x] = st;
+        __syncthreads();
+    }
+    const int32_t nitems = force_items(cnt, max_items), ngroups = (int32_t)cnt[CNT_GROUPS];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (int32_t base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * NB_WARP;
+         base < nitems; base += warps * NB_WARP) {
+        const int32_t it = base + lane;
+        const bool ok = it < nitems;
+        const int b = ok ? item_bucket(items, gcount, glen, it, ngroups) : NB_IBKT + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        int32_t got = 0;
+        if (ok && lane == leader) got = atomicAdd(&bkt[NB_IBKT + b], __popc(peers));
+        got = __shfl_sync(0xffffffffu, got, leader);
+        if (!ok) continue;
+        const int32_t pos = start[b] + got + __popc(peers & lt);
+        if (!nb_in(pos >= 0 && pos < nitems, cnt, err, SITE_FORCE, pos)) continue;
+        order[pos] = it;
+    }
+}
+
 template <int MODE, bool GUARD>
 __global__ void __launch_bounds__(F_T, MODE == MODE_COMP ? 4 : 5)
-k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ gfirst,
+k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
+        const int32_t *__restrict__ gfirst,
         const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
         const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
         const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
@@ -263,6 +347,11 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ gfirst,
         if (lane == 0) it = (int)nb_atomic_add(&cnt[CNT_FORCE_Q], 1LL);
         it = __shfl_sync(FULL, it, 0);
         if (it >= nitems) break;
+        it = order[it];
+        if (it < 0 || it >= nitems) {
+            if (lane == 0) nb_bad(cnt, err, SITE_FORCE, it);
+            continue;
+        }
         const int32_t g = items[2 * (int64_t)it], word = items[2 * (int64_t)it + 1];
         const int32_t i0 = word & ITEM_MEMBER_MASK;
         if (g < 0 || g >= ngroups) {
@@ -297,7 +386,7 @@ static void launch_force(nb_ctx *c, float eps2, float *acc, float *pot)
         if (blocks < 1) blocks = 1;
     }
     k_force<MODE, GUARD><<<c->num_sms * blocks, F_T, 0, c->stream>>>(
-        c->items, c->gfirst, c->gcount, c->glen, c->gbox, c->p_hi, c->p_lo, c->perm,
+        c->items, c->item_order, c->gfirst, c->gcount, c->glen, c->gbox, c->p_hi, c->p_lo, c->perm,
         c->list_xm, c->list_cap, c->list_alloc, c->n, c->cnt, eps2, acc, pot, c->err,
         c->max_items);
     nb_launched(c, "k_force");
@@ -306,6 +395,14 @@ static void launch_force(nb_ctx *c, float eps2, float *acc, float *pot)
 void nb_launch_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision)
 {
     cudaMemsetAsync(&c->cnt[CNT_FORCE_Q], 0, sizeof(long long), c->stream);
+    cudaMemsetAsync(c->item_bkt, 0, sizeof(int32_t) * 2 * NB_IBKT, c->stream);
+    const int ig = c->num_sms * 2;
+    k_item_hist<<<ig, 256, 0, c->stream>>>(c->items, c->gcount, c->glen, c->cnt, c->max_items,
+                                           c->item_bkt);
+    nb_launched(c, "k_item_hist");
+    k_item_order<<<ig, 256, 0, c->stream>>>(c->items, c->gcount, c->glen, c->cnt, c->max_items,
+                                            c->item_bkt, c->item_order, c->err);
+    nb_launched(c, "k_item_order");
     const float eps2 = eps * eps;
     const bool guard = !(eps2 >= FLT_MIN);
     switch (precision * 2 + (guard ? 1 : 0)) {

@@ -27,6 +27,9 @@
 
 #define NB_LEVELS 21
 #define NB_DEPTHS 23   // tree depths 0..22 (level-21 buckets hold depth-22 leaves)
+#define NB_IBKT 64     // cost buckets of the force work queue (quarter octaves)
+#define NB_CBKT (NB_DEPTHS * 8)   // cell buckets for the moments: (depth, children)
+#define NB_SPIN_LIMIT (1u << 20)  // polls before a wait for another warp gives up
 #define NB_WARP 32
 #define NB_EV_POOL 2048
 #define NB_IBLOCK 64   // targets per force work item (two per lane)
@@ -54,6 +57,8 @@ enum {
     CNT_ITEMS,       // force work items
     CNT_MAXLEVEL,
     CNT_QMAX,        // widest walk frontier
+    CNT_MOM_Q,       // moments work queue head (32-cell chunks)
+    CNT_MOM_CHUNKS,  // chunks in the moments work list
     CNT_PP_CUM,      // n_pp over every walk (never reset)
     CNT_PC_CUM,
     CNT_BAD_SITE,    // first failed self-check: site code (never reset)
@@ -76,6 +81,7 @@ enum {
     SITE_WALK_CHILD,  // child run outside the node count
     SITE_FORCE,       // force item out of range
     SITE_SORT,        // radix-sort destination out of range
+    SITE_MOMENTS_WAIT,  // a wait for a cell's children ran out (moments)
     SITE_N_
 };
 
@@ -165,6 +171,10 @@ struct nb_ctx {
     int32_t *arrive;                 // finished children per cell (bottom-up moments)
     int32_t *b_up;                   // parent's level-order index (-1 at a root)
     int32_t *lcount;                 // particle-leaf children per cell
+    int16_t *cbkt;                   // moments bucket per node (-1 at a particle leaf)
+    int32_t *cbkt_cnt;               // bucket sizes and fill cursors (2 x NB_CBKT)
+    int32_t *clist;                  // cells by bucket, each bucket padded to 32 (-1)
+    int64_t clist_len;
 
     // groups
     int32_t *gflag;   // per node flag, scanned in place to group ids (NN + 1)
@@ -174,6 +184,8 @@ struct nb_ctx {
     int item_rows;    // targets per item: 32 x item_rows (1 or 2)
     int32_t *item_cnt;
     int64_t max_items;
+    int32_t *item_order;  // queue position -> item, costliest first (max_items)
+    int32_t *item_bkt;    // cost-bucket sizes and fill cursors (2 x NB_IBKT)
 
     // learned opening angle: group features (16 floats) and theta per group
     float *gfeat, *gtheta;
@@ -256,6 +268,7 @@ int nb_launch_direct(const double *pos, const float *mass, int64_t n, double eps
 
 // nb_step.cu
 void nb_launch_kick(nb_ctx *c, double *vel, const float *acc, int64_t n, double h);
+void nb_launch_wait_probe(nb_ctx *c, unsigned limit);
 void nb_launch_drift(nb_ctx *c, double *pos, const double *vel, int64_t n, double dt);
 
 __device__ __forceinline__ long long nb_atomic_add(long long *p, long long v)
@@ -276,6 +289,32 @@ __device__ __forceinline__ bool nb_in(bool ok, long long *cnt, unsigned *err, in
 {
     if (!ok) nb_bad(cnt, err, site, idx);
     return ok;
+}
+
+// Exclusive scan of one value per thread over a block of 256 threads
+// (every thread calls it); *total gets the block's sum.
+static __device__ __forceinline__ int32_t nb_block_scan256(int32_t v, int32_t *total)
+{
+    __shared__ int32_t nb_wsum[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) nb_wsum[w] = x;
+    __syncthreads();
+    int32_t pre = 0, all = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int32_t s = nb_wsum[k];
+        pre += k < w ? s : 0;
+        all += s;
+    }
+    __syncthreads();
+    *total = all;
+    return pre + x - v;
 }
 
 // after every kernel launch: count it; under NB_DEBUG_SYNC synchronise and

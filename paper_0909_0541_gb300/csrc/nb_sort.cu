@@ -166,28 +166,47 @@ k_rs_hist(const uint64_t *__restrict__ key, int64_t n, int shift,
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(RS_T)
+// Stable scatter of one tile.  (1) every key and value is loaded; (2) each
+// warp ranks its 16 rounds of 32 keys by digit with match-any and running
+// per-warp digit counts; (3) the warps' counts are scanned per digit and the
+// tile's digit totals across digits, giving each key its place in the
+// tile's digit order; (4) keys and values are staged there in shared memory
+// and (5) written out by consecutive threads, so that each digit's run goes
+// to global memory as contiguous, coalesced stores.
+#define RS_SMEM (RS_TILE * (int)(sizeof(uint64_t) + sizeof(uint32_t)))
+
+__global__ void __launch_bounds__(RS_T, 2)
 k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
              const uint32_t *__restrict__ offs, int64_t n, int shift, int nb,
              long long *__restrict__ cnt, unsigned *__restrict__ err)
 {
+    extern __shared__ __align__(16) unsigned char rs_stage[];
+    uint64_t *sk = (uint64_t *)rs_stage;
+    uint32_t *sv = (uint32_t *)(rs_stage + RS_TILE * sizeof(uint64_t));
     __shared__ uint32_t whist[RS_WARPS][256];
     __shared__ uint32_t boff[256];
+    __shared__ uint32_t lstart[256];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     for (int i = t; i < RS_WARPS * 256; i += RS_T) (&whist[0][0])[i] = 0u;
     boff[t] = offs[(int64_t)t * nb + blockIdx.x];
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (RS_TILE / RS_WARPS);
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t rem = n - tile0;
+    const int tn = rem < RS_TILE ? (int)rem : RS_TILE;   // keys in this tile
+    const int wbase = w * (RS_TILE / RS_WARPS);
     const unsigned lt = (1u << lane) - 1u;
     uint64_t key[RS_I];
     uint32_t val[RS_I], rnk[RS_I];
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
-        const int64_t i = base + r * NB_WARP + lane;
-        const bool ok = i < n;
-        key[r] = ok ? kin[i] : 0ull;
-        val[r] = ok ? vin[i] : 0u;
+        const int e = wbase + r * NB_WARP + lane;
+        key[r] = e < tn ? kin[tile0 + e] : 0ull;
+        val[r] = e < tn ? vin[tile0 + e] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        const bool ok = wbase + r * NB_WARP + lane < tn;
         const int d = ok ? (int)((key[r] >> shift) & 255u) : 256 + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const unsigned before = __popc(peers & lt);
@@ -205,21 +224,56 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
         whist[ww][t] = run;
         run += v;
     }
+    // run = the tile's count of digit t; lstart = exclusive scan over digits
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __shared__ uint32_t wtot[RS_WARPS];
+    if (lane == 31) wtot[w] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+#pragma unroll
+    for (int ww = 0; ww < RS_WARPS; ww++) wpre += ww < w ? wtot[ww] : 0u;
+    lstart[t] = wpre + x - run;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
-        const int64_t i = base + r * NB_WARP + lane;
-        if (i < n) {
+        if (wbase + r * NB_WARP + lane < tn) {
             const int d = (int)((key[r] >> shift) & 255u);
-            const uint32_t pos = boff[d] + whist[w][d] + rnk[r];
-            if (pos >= n) {   // a self-check (recorded when a context is given)
-                if (cnt) nb_bad(cnt, err, SITE_SORT, pos);
-                continue;
+            const uint32_t lp = lstart[d] + whist[w][d] + rnk[r];
+            if (lp < (uint32_t)tn) {
+                sk[lp] = key[r];
+                sv[lp] = val[r];
+            } else if (cnt) {
+                nb_bad(cnt, err, SITE_SORT, lp);
             }
-            kout[pos] = key[r];
-            vout[pos] = val[r];
         }
     }
+    __syncthreads();
+#pragma unroll 4
+    for (int e = t; e < tn; e += RS_T) {
+        const uint64_t k = sk[e];
+        const int d = (int)((k >> shift) & 255u);
+        const uint32_t pos = boff[d] + (uint32_t)e - lstart[d];
+        if (pos >= n) {   // a self-check (recorded when a context is given)
+            if (cnt) nb_bad(cnt, err, SITE_SORT, pos);
+            continue;
+        }
+        kout[pos] = k;
+        vout[pos] = sv[e];
+    }
+}
+
+// the staging buffer is dynamic shared memory above the 48 KB default
+static void rs_setup()
+{
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    done = true;
 }
 
 // Sort (c->keys, c->idx)[0..n) by key, stably.  Result in c->keys / c->idx.
@@ -227,6 +281,7 @@ void nb_radix_sort(nb_ctx *c, int64_t n)
 {
     if (n <= 1) return;
     const int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    rs_setup();
     uint64_t *ka = c->keys, *kb = c->keys_alt;
     uint32_t *va = c->idx, *vb = c->idx_alt;
     for (int pass = 0; pass < 8; pass++) {
@@ -235,8 +290,8 @@ void nb_radix_sort(nb_ctx *c, int64_t n)
         nb_launched(c, "k_rs_hist");
         nb_exclusive_scan(c, (const int32_t *)c->sort_hist, (int32_t *)c->sort_hist,
                           (int64_t)256 * nb, nullptr, nullptr);
-        k_rs_scatter<<<nb, RS_T, 0, c->stream>>>(ka, va, kb, vb, c->sort_hist, n,
-                                                 shift, nb, c->cnt, c->err);
+        k_rs_scatter<<<nb, RS_T, RS_SMEM, c->stream>>>(ka, va, kb, vb, c->sort_hist, n,
+                                                       shift, nb, c->cnt, c->err);
         nb_launched(c, "k_rs_scatter");
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
@@ -271,13 +326,15 @@ void nb_radix_sort_passes(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uin
 {
     if (n <= 1) return;
     const int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    rs_setup();
     uint64_t *ka = keys, *kb = keys_alt;
     uint32_t *va = idx, *vb = idx_alt;
     for (int pass = 0; pass < passes; pass++) {
         const int shift = 8 * pass;
         k_rs_hist<<<nb, RS_T, 0, s>>>(ka, n, shift, hist, nb);
         nb_exclusive_scan_raw((const int32_t *)hist, (int32_t *)hist, (int64_t)256 * nb, bsum, s);
-        k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, hist, n, shift, nb, nullptr, nullptr);
+        k_rs_scatter<<<nb, RS_T, RS_SMEM, s>>>(ka, va, kb, vb, hist, n, shift, nb, nullptr,
+                                               nullptr);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }

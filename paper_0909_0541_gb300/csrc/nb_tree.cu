@@ -338,6 +338,10 @@ k_depth_hist(const int8_t *__restrict__ depth, const long long *__restrict__ cnt
     if (threadIdx.x < NB_DEPTHS) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter by depth, staged like the radix sort's: nodes are ranked
+// per warp with match-any, placed in the tile's depth order in shared
+// memory, then written out as contiguous runs.  Tiles past the node count
+// return at once (the grid covers the node capacity).
 __global__ void __launch_bounds__(DS_T)
 k_depth_scatter(const int8_t *__restrict__ depth, long long *__restrict__ cnt,
                 const uint32_t *__restrict__ offs, int ntiles, int32_t *__restrict__ bfs2pid,
@@ -345,19 +349,31 @@ k_depth_scatter(const int8_t *__restrict__ depth, long long *__restrict__ cnt,
 {
     __shared__ uint32_t whist[DS_T / NB_WARP][32];
     __shared__ uint32_t boff[32];
+    __shared__ uint32_t lstart[32];
+    __shared__ int32_t sid[DS_TILE];
+    __shared__ int8_t sdep[DS_TILE];
+    const int64_t total = cnt[CNT_NODES];
+    const int64_t tile0 = (int64_t)blockIdx.x * DS_TILE;
+    if (tile0 >= total) return;
+    const int64_t rem = total - tile0;
+    const int tn = rem < DS_TILE ? (int)rem : DS_TILE;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     for (int i = t; i < (DS_T / NB_WARP) * 32; i += DS_T) (&whist[0][0])[i] = 0u;
-    if (t < NB_DEPTHS) boff[t] = offs[(int64_t)t * ntiles + blockIdx.x];
+    if (t < 32) boff[t] = t < NB_DEPTHS ? offs[(int64_t)t * ntiles + blockIdx.x] : 0u;
     __syncthreads();
-    const int64_t total = cnt[CNT_NODES];
-    const int64_t base = (int64_t)blockIdx.x * DS_TILE + (int64_t)w * (DS_TILE / (DS_T / NB_WARP));
+    const int wbase = w * (DS_TILE / (DS_T / NB_WARP));
     const unsigned lt = (1u << lane) - 1u;
     uint32_t rnk[DS_I];
+    int dep[DS_I];
 #pragma unroll
     for (int r = 0; r < DS_I; r++) {
-        const int64_t i = base + r * NB_WARP + lane;
-        const bool ok = i < total;
-        const int d = ok ? (int)depth[i] : 32 + lane;
+        const int e = wbase + r * NB_WARP + lane;
+        dep[r] = e < tn ? (int)depth[tile0 + e] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < DS_I; r++) {
+        const bool ok = wbase + r * NB_WARP + lane < tn && dep[r] >= 0 && dep[r] < NB_DEPTHS;
+        const int d = ok ? dep[r] : 32 + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const unsigned before = __popc(peers & lt);
         const uint32_t pre = ok ? whist[w][d] : 0u;
@@ -374,18 +390,34 @@ k_depth_scatter(const int8_t *__restrict__ depth, long long *__restrict__ cnt,
             whist[ww][t] = run;
             run += v;
         }
+        uint32_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        lstart[t] = x - run;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < DS_I; r++) {
-        const int64_t i = base + r * NB_WARP + lane;
-        if (i < total) {
-            const int d = depth[i];
-            const uint32_t pos = boff[d] + whist[w][d] + rnk[r];
-            if (!nb_in(pos < total, cnt, err, SITE_DEPTH, pos)) continue;
-            bfs2pid[pos] = (int32_t)i;
-            pid2bfs[i] = (int32_t)pos;
-        }
+        const int e = wbase + r * NB_WARP + lane;
+        if (e >= tn) continue;
+        const int d = dep[r];
+        if (!nb_in(d >= 0 && d < NB_DEPTHS, cnt, err, SITE_DEPTH, tile0 + e)) continue;
+        const uint32_t lp = lstart[d] + whist[w][d] + rnk[r];
+        if (!nb_in(lp < (uint32_t)tn, cnt, err, SITE_DEPTH, lp)) continue;
+        sid[lp] = (int32_t)(tile0 + e);
+        sdep[lp] = (int8_t)d;
+        pid2bfs[tile0 + e] = (int32_t)(boff[d] + whist[w][d] + rnk[r]);
+    }
+    __syncthreads();
+    for (int e = t; e < tn; e += DS_T) {
+        const int d = sdep[e];
+        if (d < 0 || d >= NB_DEPTHS) continue;   // a slot left by a reported bad depth
+        const uint32_t pos = boff[d] + (uint32_t)e - lstart[d];
+        if (!nb_in(pos < total, cnt, err, SITE_DEPTH, pos)) continue;
+        bfs2pid[pos] = sid[e];
     }
 }
 
@@ -416,12 +448,17 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
               const double *__restrict__ x64, long long *__restrict__ cnt,
               nb_wrec *__restrict__ wrec, double *__restrict__ b_mass, double *__restrict__ b_mx,
               double *__restrict__ b_com, int32_t *__restrict__ b_up,
-              int32_t *__restrict__ lcount, int64_t n, unsigned *__restrict__ err)
+              int32_t *__restrict__ lcount, int16_t *__restrict__ cbkt,
+              int32_t *__restrict__ cbkt_cnt, int64_t n, unsigned *__restrict__ err)
 {
+    __shared__ int32_t hb[NB_CBKT];   // cells per moments bucket in this block
+    for (int k = threadIdx.x; k < NB_CBKT; k += blockDim.x) hb[k] = 0;
+    __syncthreads();
     const int32_t total = (int32_t)cnt[CNT_NODES];
     for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < total;
          b += gridDim.x * blockDim.x) {
         b_up[b] = -1;
+        cbkt[b] = -1;
         const int32_t u = bfs2pid[b];
         if (!nb_in(u >= 0 && u < total, cnt, err, SITE_RECORDS, u)) continue;
         const int4 c = node_c[u];
@@ -453,6 +490,11 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
             const int4 wb = make_int4(u, c.x, pid2bfs[u + 1], n_nchild[u]);
             const int depth = n_depth[u];
             if (!nb_in(depth >= 0 && depth <= NB_LEVELS, cnt, err, SITE_RECORDS, u)) continue;
+            if (!nb_in(wb.w >= 1 && wb.w <= 8, cnt, err, SITE_RECORDS, u)) continue;
+            // moments bucket: deepest level first, then by number of children
+            const int k = (NB_DEPTHS - 1 - depth) * 8 + wb.w - 1;
+            cbkt[b] = (int16_t)k;
+            atomicAdd(&hb[k], 1);
             const double *root = roots + (sys ? 8 * (int64_t)sys[slot] : 0);
             const double lc = __dmul_rn(root[3], pow2_neg(depth));
             const uint64_t kf = key[slot];
@@ -466,126 +508,211 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
             nb_wrec_put_hi(&wrec[b], wb, __double2float_rn(lc), 0.0f);
         }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NB_CBKT; k += blockDim.x)
+        if (hb[k]) atomicAdd(&cbkt_cnt[k], hb[k]);
 }
 
-// FP64 moments in two passes.
+// FP64 moments, bottom-up in one launch.
 //
-// (A) k_moments_up, bottom-up in one launch: M and sum(m x) of every cell,
-// folded over its children -- contiguous one level down, in octant order.
-// k_bfs_records counted each cell's particle-leaf children (lcount); a cell
-// whose children are all leaves is ready at once and is taken by the lane
-// that meets it.  A finished cell counts itself in at its parent (arrive);
-// the arrival that completes the parent's count (arrive + lcount = children)
-// folds the parent in turn.  A warp takes 32 consecutive nodes; after its
-// lanes' folds it fences once (their sums before their arrivals) and, if an
-// arrival completed a parent, once more (the children's sums before the
-// fold); children are read through L2.  No thread waits on another: an
-// arrival that does not complete its parent simply stops.
+// GB300 runs FP64 at a small fraction of its FP32 rate, and an FP64 warp
+// instruction costs the pipe the same whether 3 or 32 lanes are active, so
+// the work is arranged for full warps of equal work.  k_bfs_records put each
+// cell in a bucket (depth, deepest first; number of children); k_cell_list
+// lists the cells bucket by bucket, every bucket padded to whole warps.  A
+// warp of k_moments takes the next 32 entries from a global queue, so every
+// lane folds the same number of children, and no warp mixes two depths.
 //
-// (B) k_moments_fin, one thread per node: COM = sum(m x) / M, l and
-// s = |COM - geometric centre|, and the FP32 hi/lo split -- the FP64
-// divisions and square roots, with every lane of the warp busy.
-__device__ __forceinline__ void fold_sums(int32_t p, const int4 wp, double *b_mass,
-                                          double *b_mx)
-{
-    double M = 0.0, mx[3] = {0.0, 0.0, 0.0};
-    for (int32_t k0 = 0; k0 < wp.w; k0 += 4) {
-        double cm[4], cx[4][3];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int64_t ch = (int64_t)wp.z + k0 + k;
-            const bool ok = k0 + k < wp.w;
-            cm[k] = ok ? __ldcg(&b_mass[ch]) : 0.0;
-#pragma unroll
-            for (int d = 0; d < 3; d++) cx[k][d] = ok ? __ldcg(&b_mx[3 * ch + d]) : 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (k0 + k >= wp.w) break;
-            M = __dadd_rn(M, cm[k]);
-#pragma unroll
-            for (int d = 0; d < 3; d++) mx[d] = __dadd_rn(mx[d], cx[k][d]);
-        }
-    }
-    b_mass[p] = M;
-#pragma unroll
-    for (int d = 0; d < 3; d++) b_mx[3 * (int64_t)p + d] = mx[d];
-}
-
+// A cell is ready once its cell children have arrived (particle-leaf
+// children, counted by k_bfs_records in lcount, are final from the start).
+// The warp waits for its cells with a bounded poll: the children are
+// deeper, so their chunks came earlier from the queue and are held by warps
+// that are running, and the wait ends; if it does not within the limit, the
+// warp reports SITE_MOMENTS_WAIT and every waiting warp stops.  The fold
+// adds M and sum(m x) over the children in octant order; the sums are made
+// visible (fence) before the arrival at the parent; then COM = sum(m x) / M,
+// s = |COM - geometric centre| and the FP32 hi/lo split of the record.
 __global__ void __launch_bounds__(256)
-k_moments_up(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ b_up,
-             const int32_t *__restrict__ lcount, double *b_mass, double *b_mx, int32_t *arrive,
-             long long *__restrict__ cnt, unsigned *__restrict__ err)
+k_cell_list(const int16_t *__restrict__ cbkt, int32_t *__restrict__ cbkt_cnt,
+            long long *__restrict__ cnt, int32_t *__restrict__ clist, int64_t clist_len,
+            unsigned *__restrict__ err)
 {
-    const unsigned FULL = 0xffffffffu;
+    static_assert(NB_CBKT <= 256, "one bucket per thread");
+    __shared__ int32_t start[NB_CBKT + 1];
+    {
+        const int t = threadIdx.x;
+        const int32_t sz = t < NB_CBKT ? cbkt_cnt[t] : 0;
+        const int32_t padded = (sz + NB_WARP - 1) / NB_WARP * NB_WARP;
+        int32_t all;
+        const int32_t st = nb_block_scan256(padded, &all);
+        if (t < NB_CBKT) start[t] = st;
+        if (t == 0) start[NB_CBKT] = all;
+        if (blockIdx.x == 0 && t == 0) cnt[CNT_MOM_CHUNKS] = all / NB_WARP;
+        // block 0 marks each bucket's padding (at most 31 slots): no cell
+        if (blockIdx.x == 0 && t < NB_CBKT)
+            for (int32_t i = st + sz; i < st + padded; i++)
+                if (i < clist_len) clist[i] = -1;
+        __syncthreads();
+    }
     const int32_t total = (int32_t)cnt[CNT_NODES];
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * NB_WARP; base < total; base += nwarps * NB_WARP) {
-        const int32_t b0 = (int32_t)(base + lane);
-        int32_t p = -1;
-        int4 wp = make_int4(0, 0, -1, 0);
-        if (b0 < total) {
-            wp = wrec[b0].b;
-            if (wp.z >= 0 && lcount[b0] == wp.w) p = b0;   // a cell whose children are all leaves
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t nw = gridDim.x * (blockDim.x >> 5);
+    for (int32_t base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * NB_WARP;
+         base < total; base += nw * NB_WARP) {
+        const int32_t b = base + lane;
+        int k = b < total ? (int)cbkt[b] : -1;
+        if (k >= NB_CBKT) {
+            nb_bad(cnt, err, SITE_MOMENTS, b);
+            k = -1;
         }
-        for (int guard = 0; guard <= NB_DEPTHS && __any_sync(FULL, p >= 0); guard++) {
-            if (p >= 0 && !nb_in(wp.z > p && wp.w >= 1 && (int64_t)wp.z + wp.w <= total, cnt,
-                                 err, SITE_MOMENTS, p))
-                p = -1;
-            if (p >= 0) fold_sums(p, wp, b_mass, b_mx);
-            __threadfence();                       // the warp's sums before its arrivals
-            int32_t q = -1;
-            if (p >= 0) {
-                q = b_up[p];
-                if (q >= 0 && !nb_in(q < p, cnt, err, SITE_MOMENTS, p)) q = -1;
-                if (q >= 0) {
-                    wp = wrec[q].b;
-                    if (atomicAdd(&arrive[q], 1) + 1 + lcount[q] != wp.w) q = -1;
-                }
-            }
-            p = q;
-            if (__any_sync(FULL, p >= 0)) __threadfence();   // children's sums before folds
-        }
+        const int key = k >= 0 ? k : NB_CBKT + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        int32_t got = 0;
+        if (k >= 0 && lane == leader) got = atomicAdd(&cbkt_cnt[NB_CBKT + k], __popc(peers));
+        got = __shfl_sync(0xffffffffu, got, leader);
+        if (k < 0) continue;
+        const int32_t pos = start[k] + got + __popc(peers & lt);
+        if (!nb_in(pos >= 0 && pos < start[k + 1] && pos < clist_len, cnt, err, SITE_MOMENTS,
+                   pos))
+            continue;
+        clist[pos] = b;
     }
 }
 
-__global__ void __launch_bounds__(256)
-k_moments_fin(nb_wrec *__restrict__ wrec, const double *__restrict__ b_mass,
-              const double *__restrict__ b_mx, double *__restrict__ b_com,
-              const long long *__restrict__ cnt)
+__device__ __forceinline__ int32_t ld_acquire(const int32_t *p)
 {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait of a whole warp until each waiting lane sees arrive[b] >=
+// need (lanes with `ready` set do not wait).  A lane's result is false if
+// it gave up: after `limit` polls (reported as SITE_MOMENTS_WAIT), or
+// because another warp had reported a failure.
+__device__ __forceinline__ bool wait_arrivals(const int32_t *arrive, int32_t b, int32_t need,
+                                              bool ready, unsigned limit, long long *cnt,
+                                              unsigned *err)
+{
+    for (unsigned spins = 0;; spins++) {
+        if (!ready) ready = ld_acquire(&arrive[b]) >= need;
+        if (__all_sync(0xffffffffu, ready)) return true;
+        bool stop = spins >= limit;
+        if (!stop && (spins & 63u) == 63u)
+            stop = (*(volatile unsigned *)err & NB_EF_BOUNDS) != 0u;
+        if (__any_sync(0xffffffffu, stop)) {
+            if (!ready && spins >= limit) nb_bad(cnt, err, SITE_MOMENTS_WAIT, b);
+            return ready;
+        }
+        __nanosleep(64);
+    }
+}
+
+// one warp: lane 0 waits for a count that nothing raises (a test of the
+// bounded wait; the status is read by the host)
+__global__ void k_wait_probe(const int32_t *flag, unsigned limit, long long *cnt, unsigned *err)
+{
+    wait_arrivals(flag, 0, 1, threadIdx.x != 0, limit, cnt, err);
+}
+
+void nb_launch_wait_probe(nb_ctx *c, unsigned limit)
+{
+    cudaMemsetAsync(c->cbkt_cnt, 0, sizeof(int32_t), c->stream);
+    k_wait_probe<<<1, NB_WARP, 0, c->stream>>>(c->cbkt_cnt, limit, c->cnt, c->err);
+    nb_launched(c, "k_wait_probe");
+}
+
+__global__ void __launch_bounds__(256)
+k_moments(const int32_t *__restrict__ clist, int64_t clist_len, nb_wrec *__restrict__ wrec,
+          const int32_t *__restrict__ b_up, const int32_t *__restrict__ lcount, double *b_mass,
+          double *b_mx, double *__restrict__ b_com, int32_t *arrive, long long *__restrict__ cnt,
+          unsigned *err)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int32_t total = (int32_t)cnt[CNT_NODES];
-    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < total;
-         b += gridDim.x * blockDim.x) {
-        const int4 wb = wrec[b].b;
-        if (wb.z < 0) continue;                   // particle leaves are final already
-        const float lcf = wrec[b].c.x;
-        const double M = b_mass[b];
+    long long nchunks = cnt[CNT_MOM_CHUNKS];
+    if (nchunks > clist_len / NB_WARP) nchunks = clist_len / NB_WARP;
+    for (;;) {
+        long long ch = 0;
+        if (lane == 0) ch = nb_atomic_add(&cnt[CNT_MOM_Q], 1LL);
+        ch = __shfl_sync(FULL, ch, 0);
+        if (ch >= nchunks) break;
+        int32_t b = clist[ch * NB_WARP + lane];
+        int4 wb = make_int4(0, 0, -1, 0);
+        int32_t need = 0;
+        if (b >= 0) {
+            if (nb_in(b < total, cnt, err, SITE_MOMENTS, b)) {
+                wb = wrec[b].b;
+                if (nb_in(wb.z > b && wb.w >= 1 && wb.w <= 8 && (int64_t)wb.z + wb.w <= total, cnt,
+                          err, SITE_MOMENTS, b))
+                    need = wb.w - lcount[b];   // cell children still to arrive
+                else
+                    b = -1;
+            } else {
+                b = -1;
+            }
+        }
+        // bounded wait for the lanes' cell children
+        if (!wait_arrivals(arrive, b, need, b < 0 || need <= 0, NB_SPIN_LIMIT, cnt, err)) b = -1;
+        // fold the children in octant order
+        const int32_t nch = b >= 0 ? wb.w : 0;
+        double M = 0.0, mx[3] = {0.0, 0.0, 0.0};
+        for (int32_t k0 = 0; k0 < nch; k0 += 4) {
+            double cm[4], cx[4][3];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int64_t c = (int64_t)wb.z + k0 + k;
+                const bool ok = k0 + k < nch;
+                cm[k] = ok ? __ldcg(&b_mass[c]) : 0.0;
+#pragma unroll
+                for (int d = 0; d < 3; d++) cx[k][d] = ok ? __ldcg(&b_mx[3 * c + d]) : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (k0 + k >= nch) break;
+                M = __dadd_rn(M, cm[k]);
+#pragma unroll
+                for (int d = 0; d < 3; d++) mx[d] = __dadd_rn(mx[d], cx[k][d]);
+            }
+        }
+        if (b >= 0) {
+            b_mass[b] = M;
+#pragma unroll
+            for (int d = 0; d < 3; d++) b_mx[3 * (int64_t)b + d] = mx[d];
+        }
+        __threadfence();   // the sums before the arrivals
+        if (b >= 0) {
+            const int32_t q = b_up[b];
+            if (q >= 0 && nb_in(q < b, cnt, err, SITE_MOMENTS, b)) atomicAdd(&arrive[q], 1);
+        }
+        if (b < 0) continue;
         // COM = sum(m x) / M, correctly rounded: one correctly rounded
         // reciprocal y = RN(1/M) shared by the three quotients, then
         // Markstein's correction q = RN(q0 + RN(a - M q0) y), q0 = RN(a y),
-        // which gives RN(a / M) (Markstein 1990, IBM J. Res. Dev. 34(1))
+        // which gives RN(a / M) (Markstein 1990, IBM J. Res. Dev. 34(1)).
+        // d2 starts as the first square: 0 + x = x exactly for x >= 0.
         const double y = M > 0.0 ? __drcp_rn(M) : 0.0;
         double d2 = 0.0;
         float hi[3], lo[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const double g = b_com[3 * (int64_t)b + d];   // geometric centre
-            const double a = b_mx[3 * (int64_t)b + d];
             double com = g;
             if (M > 0.0) {
-                const double q0 = __dmul_rn(a, y);
-                const double r = __fma_rn(-q0, M, a);
+                const double q0 = __dmul_rn(mx[d], y);
+                const double r = __fma_rn(-q0, M, mx[d]);
                 com = __fma_rn(r, y, q0);
             }
             const double dd = __dsub_rn(com, g);
-            d2 = __dadd_rn(d2, __dmul_rn(dd, dd));
+            d2 = d == 0 ? __dmul_rn(dd, dd) : __dadd_rn(d2, __dmul_rn(dd, dd));
             hi[d] = __double2float_rn(com);
             lo[d] = __double2float_rn(__dsub_rn(com, (double)hi[d]));
             b_com[3 * (int64_t)b + d] = com;
         }
+        const float lcf = wrec[b].c.x;
         nb_wrec_put_lo(&wrec[b], make_float4(hi[0], hi[1], hi[2], __double2float_rn(M)),
                        make_float4(lo[0], lo[1], lo[2], 0.0f));
         nb_wrec_put_hi(&wrec[b], wb, lcf, __double2float_rn(__dsqrt_rn(d2)));
@@ -782,17 +909,24 @@ static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t 
     nb_launched(c, "k_depth_scatter");
     k_level_start<<<1, 32, 0, s>>>(c->dhist, nt, c->level_start);
     nb_launched(c, "k_level_start");
+    cudaMemsetAsync(c->cbkt_cnt, 0, sizeof(int32_t) * 2 * NB_CBKT, s);
     k_bfs_records<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
         c->bfs2pid, c->pid2bfs, c->node_c, c->n_first, c->n_nchild, c->n_parent, c->n_depth,
         c->keys, c->root, sys_sorted, c->p_hi, c->p_lo, c->p_x64, c->cnt, c->wrec, c->b_mass,
-        c->b_mx, c->b_com, c->b_up, c->lcount, n, c->err);
+        c->b_mx, c->b_com, c->b_up, c->lcount, c->cbkt, c->cbkt_cnt, n, c->err);
     nb_launched(c, "k_bfs_records");
-    k_moments_up<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
-        c->wrec, c->b_up, c->lcount, c->b_mass, c->b_mx, c->arrive, c->cnt, c->err);
-    nb_launched(c, "k_moments_up");
-    k_moments_fin<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
-        c->wrec, c->b_mass, c->b_mx, c->b_com, c->cnt);
-    nb_launched(c, "k_moments_fin");
+    k_cell_list<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(c->cbkt, c->cbkt_cnt, c->cnt,
+                                                                 c->clist, c->clist_len, c->err);
+    nb_launched(c, "k_cell_list");
+    static int mblocks = 0;
+    if (mblocks == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mblocks, k_moments, 256, 0);
+        if (mblocks < 1) mblocks = 1;
+    }
+    k_moments<<<c->num_sms * mblocks, 256, 0, s>>>(c->clist, c->clist_len, c->wrec, c->b_up,
+                                                   c->lcount, c->b_mass, c->b_mx, c->b_com,
+                                                   c->arrive, c->cnt, c->err);
+    nb_launched(c, "k_moments");
 }
 
 // ------------------------------------------------------------ groups

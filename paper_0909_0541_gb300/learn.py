@@ -168,6 +168,30 @@ def step_cost(ctx: NBody, n_crit, eps, acc, theta=None, params=None, fallback=0.
     return st["n_pp"] + st["n_pc"], tm["walk"][0] + tm["force"][0]
 
 
+def calibrate(ctx: NBody, params, n_crit, eps, acc, ref, targets, target_err,
+              lo=-4.0, hi=4.0, iters=14, fallback=0.6):
+    """Shift of the output bias b4 (a common offset of every group's logit)
+    bisected so that the learned walk's median error over `targets` equals
+    target_err; ctx holds the tree of the calibration set.  The labels bound
+    a weighted median of per-group medians, and this matches the global
+    median instead.  Returns (calibrated parameters, shift)."""
+    base = params.clone()
+    p = params.clone()
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        p.copy_(base)
+        p[OFF["b4"]] += mid
+        ctx.walk_groups_learned(n_crit, p, fallback)
+        ctx.forces(eps, acc)
+        if median_error(acc, ref, targets) > target_err:
+            hi = mid
+        else:
+            lo = mid
+    p.copy_(base)
+    p[OFF["b4"]] += lo
+    return p, lo
+
+
 def matched_fixed_theta(ctx: NBody, n_crit, eps, acc, ref, targets, target_err,
                         lo=0.3, hi=1.2, iters=12):
     """Bisection for the fixed theta whose median error equals target_err."""

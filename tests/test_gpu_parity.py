@@ -253,3 +253,18 @@ def test_list_storage_sized_by_counting_walk():
     ctx.forces(1 / 64, acc)
     ctx.sync_status()
     assert bool(torch.isfinite(acc).all())
+
+
+def test_bounded_wait_gives_up_and_context_survives(oracle_lib):
+    """The bottom-up moments make a warp wait for other warps' cells.  The
+    wait is bounded: a warp waiting on a count that nothing raises gives up
+    after the poll limit and latches NB_ERR_INTERNAL (-8), and the context
+    then builds a tree that still matches the oracle bit for bit."""
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(3000, 21)
+    dev = torch.device("cuda")
+    ctx = nb.NBody(ps.n)
+    assert ctx.selftest_wait(2000) == -8
+    ctx.build_tree(torch.from_numpy(ps.pos).to(dev), torch.from_numpy(ps.mass).to(dev))
+    ctx.sync_status()
+    assert_tree_equal(dict(tree=ctx.copy_tree()), oracle_lib.Tree(ps.pos, ps.mass))
