@@ -33,6 +33,7 @@
 
 #define F_T 256
 #define F_WARPS (F_T / NB_WARP)
+#define F_TILE 32   // list records staged per tile (a multiple of 32)
 // item word: first member | log2(source streams) << 27 | two-targets-per-lane flag
 #define ITEM_R2 (1 << 30)
 #define ITEM_LS_SHIFT 27
@@ -104,7 +105,7 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int32_t j0, const 
                                           const float *yi, const float *zi, const int32_t *kk,
                                           float eps2, Acc<MODE> *A, Acc<MODE> *T)
 {
-#pragma unroll 8
+#pragma unroll
     for (int j = 0; j < NJ; j++) {
         const float4 q = tile[j];
 #pragma unroll
@@ -196,14 +197,18 @@ __device__ __forceinline__ void force_item(
         A[r].init();
         T[r].init();
     }
-    // (1) the list: sources outside the group
+    // (1) the list: sources outside the group, F_TILE records per tile
+    constexpr int TK = F_TILE / NB_WARP;   // records each lane stages per tile
     const float4 *__restrict__ src = list_xm + (int64_t)g * cap;
-    for (int32_t j0 = 0; j0 < len; j0 += NB_WARP) {
-        const int32_t jj = j0 + lane;
-        tile[lane] = jj < len ? src[jj] : pad;
+    for (int32_t j0 = 0; j0 < len; j0 += F_TILE) {
+#pragma unroll
+        for (int k = 0; k < TK; k++) {
+            const int32_t jj = j0 + k * NB_WARP + lane;
+            tile[k * NB_WARP + lane] = jj < len ? src[jj] : pad;
+        }
         __syncwarp();
-        tile_pass<MODE, GUARD, false, R, W>(tile + stream * W, j0 + stream * W, xi, yi, zi, kk,
-                                            eps2, A, T);
+        tile_pass<MODE, GUARD, false, R, W * TK>(tile + stream * W * TK, j0 + stream * W * TK, xi,
+                                                 yi, zi, kk, eps2, A, T);
         __syncwarp();
     }
     // (2) the group's own members, j != i
@@ -333,7 +338,7 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
         long long *__restrict__ cnt, float eps2, float *__restrict__ acc, float *__restrict__ pot,
         unsigned *__restrict__ err, int64_t max_items)
 {
-    __shared__ float4 tiles[F_WARPS][NB_WARP];
+    __shared__ float4 tiles[F_WARPS][F_TILE];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t nitems = (int32_t)cnt[CNT_ITEMS];
