@@ -110,6 +110,7 @@ static void carve_context(nb_ctx *c, Arena &a)
     a.carve(&c->idx, N);
     a.carve(&c->idx_alt, N);
     a.carve(&c->sort_hist, c->sort_hist_len);
+    a.carve(&c->rs_status, c->rs_status_len);
     a.carve(&c->scan_bsum, c->scan_bsum_len);
     a.carve(&c->bbox_part, 6 * (int64_t)c->bbox_blocks);
     a.carve(&c->root, 8 * c->max_sys);
@@ -186,7 +187,8 @@ static const char *const SITE_NAME[SITE_N_] = {
     "k_depth_scatter: level-order position", "k_bfs_records: node or particle",
     "k_moments: cell, parent or child run", "groups: group or member range",
     "k_items: item index", "k_walk: queued node", "k_walk: child run", "k_force: item",
-    "k_rs_scatter: destination", "k_moments: wait for children ran out"};
+    "k_rs_scatter: destination", "k_moments: wait for children ran out",
+    "k_rs_scatter: look-back wait ran out"};
 
 static int err_code(unsigned bits)
 {
@@ -343,6 +345,7 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
     c->max_nodes = NN;
     const int64_t rs_tiles = (N + 4095) / 4096;
     c->sort_hist_len = 256 * rs_tiles + 1;
+    c->rs_status_len = 8 * 256 * rs_tiles + 8 * 256 + 8;
     c->dtiles = (NN + 4095) / 4096;
     const int64_t dhist_len = NB_DEPTHS * c->dtiles + 1;
     int64_t scan_n = NN + 1 > c->sort_hist_len ? NN + 1 : c->sort_hist_len;

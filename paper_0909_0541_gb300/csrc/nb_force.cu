@@ -34,6 +34,7 @@
 #define F_T 256
 #define F_WARPS (F_T / NB_WARP)
 #define F_TILE 32   // list records staged per tile (a multiple of 32)
+static constexpr int F_MASK_UNROLL = 8;   // unroll of the masked phase
 // item word: first member | log2(source streams) << 27 | two-targets-per-lane flag
 #define ITEM_R2 (1 << 30)
 #define ITEM_LS_SHIFT 27
@@ -105,8 +106,9 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int32_t j0, const 
                                           const float *yi, const float *zi, const int32_t *kk,
                                           float eps2, Acc<MODE> *A, Acc<MODE> *T)
 {
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
+    // the list phase is unrolled in full; the masked phase (the group's own
+    // members, a few per cent of the work) is kept short for the I-cache
+    auto rec = [&](int j) {
         const float4 q = tile[j];
 #pragma unroll
         for (int r = 0; r < R; r++) {
@@ -116,6 +118,13 @@ __device__ __forceinline__ void tile_pass(const float4 *tile, int32_t j0, const 
             else
                 interact<MODE, GUARD, MASK>(q, xi[r], yi[r], zi[r], eps2, me, A[r]);
         }
+    };
+    if constexpr (MASK) {
+#pragma unroll F_MASK_UNROLL
+        for (int j = 0; j < NJ; j++) rec(j);
+    } else {
+#pragma unroll
+        for (int j = 0; j < NJ; j++) rec(j);
     }
     if constexpr (MODE == MODE_COMP) {
 #pragma unroll

@@ -82,6 +82,7 @@ enum {
     SITE_FORCE,       // force item out of range
     SITE_SORT,        // radix-sort destination out of range
     SITE_MOMENTS_WAIT,  // a wait for a cell's children ran out (moments)
+    SITE_SORT_WAIT,     // a radix-sort look-back wait ran out
     SITE_N_
 };
 
@@ -128,6 +129,8 @@ struct nb_ctx {
     uint32_t *idx, *idx_alt;
     uint32_t *sort_hist;
     int64_t sort_hist_len;
+    uint32_t *rs_status;     // onesweep: tile status words, digit histograms, tile counters
+    int64_t rs_status_len;
 
     // scan scratch
     int32_t *scan_bsum;
@@ -289,6 +292,22 @@ __device__ __forceinline__ bool nb_in(bool ok, long long *cnt, unsigned *err, in
 {
     if (!ok) nb_bad(cnt, err, site, idx);
     return ok;
+}
+
+// The lanes of the warp whose BITS-bit value v equals this lane's, from one
+// ballot per bit (every lane calls it; a lane with ok false matches only
+// itself and is left out of the others' masks).
+template <int BITS>
+static __device__ __forceinline__ unsigned nb_match_bits(unsigned v, bool ok)
+{
+    unsigned m = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int b = 0; b < BITS; b++) {
+        const bool bit = (v >> b) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bb : ~bb;
+    }
+    return ok ? m : (1u << (threadIdx.x & 31));
 }
 
 // Exclusive scan of one value per thread over a block of 256 threads

@@ -2,12 +2,16 @@
 // (63-bit Morton key, particle index) pairs that puts particles in Morton
 // order (Sec. "Test and Optimization": depth-first leaf order of the tree).
 //
-// Radix sort: 8 passes of 8-bit digits.  Each pass = per-tile digit
-// histograms (tile 4096 keys) -> exclusive scan of the digit-major
-// histogram table -> stable scatter.  Stability inside a tile comes from
-// warp-level match/rank over 32 consecutive keys at a time with per-warp
-// running digit counts, then a scan of those counts across the 8 warps.
-// No step waits on another block, so nothing can spin.
+// Radix sort: 8 passes of 8-bit digits over tiles of 4096 keys.  The
+// context's sort is single-pass per digit (Onesweep, see k_rs_scatter): one
+// histogram of all eight digits, then one scatter launch per pass whose
+// tiles find their offsets by a bounded decoupled look-back.  The sort on
+// caller-supplied buffers (no context) keeps three phases per pass, none
+// of which waits on another block: per-tile digit histograms -> exclusive
+// scan of the digit-major table -> stable scatter.  Stability inside a tile
+// comes from warp-level ranking of 32 consecutive keys at a time with
+// per-warp running digit counts, then a scan of those counts across the 8
+// warps.
 #include "nb_internal.cuh"
 
 #define SCAN_T 256
@@ -167,19 +171,48 @@ k_rs_hist(const uint64_t *__restrict__ key, int64_t n, int shift,
 }
 
 // Stable scatter of one tile.  (1) every key and value is loaded; (2) each
-// warp ranks its 16 rounds of 32 keys by digit with match-any and running
-// per-warp digit counts; (3) the warps' counts are scanned per digit and the
+// warp ranks its 16 rounds of 32 keys by digit (warp match from one ballot
+// per digit bit) and running per-warp digit counts; (3) the warps' counts are scanned per digit and the
 // tile's digit totals across digits, giving each key its place in the
 // tile's digit order; (4) keys and values are staged there in shared memory
 // and (5) written out by consecutive threads, so that each digit's run goes
 // to global memory as contiguous, coalesced stores.
+//
+// ONESWEEP (Adinets and Merrill, "Onesweep: a faster least significant digit
+// radix sort for GPUs", 2022): no histogram or scan launch per pass.  A
+// block claims its tile from a counter, so tiles are claimed in order; the
+// digit bases come from one histogram of all eight digits made before the
+// first pass; each tile publishes its digit counts and finds the counts of
+// the tiles before it by decoupled look-back (Merrill and Garland,
+// "Single-pass parallel prefix scan with decoupled look-back", 2016).  A
+// status word holds a flag (2 bits: not ready, this tile's count, inclusive
+// prefix) and a 30-bit count.  A tile waits only for tiles claimed before it,
+// whose blocks are running; every wait is bounded, and a wait that runs out
+// is reported (SITE_SORT_WAIT) and makes every other waiting block stop.
 #define RS_SMEM (RS_TILE * (int)(sizeof(uint64_t) + sizeof(uint32_t)))
+#define RS_AGG (1u << 30)
+#define RS_INC (2u << 30)
+#define RS_VAL ((1u << 30) - 1u)
 
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <bool ONESWEEP>
 __global__ void __launch_bounds__(RS_T, 2)
 k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
              const uint32_t *__restrict__ offs, int64_t n, int shift, int nb,
-             long long *__restrict__ cnt, unsigned *__restrict__ err)
+             long long *__restrict__ cnt, unsigned *__restrict__ err, uint32_t *status,
+             const uint32_t *__restrict__ ghist, uint32_t *tilectr)
 {
     extern __shared__ __align__(16) unsigned char rs_stage[];
     uint64_t *sk = (uint64_t *)rs_stage;
@@ -187,11 +220,17 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     __shared__ uint32_t whist[RS_WARPS][256];
     __shared__ uint32_t boff[256];
     __shared__ uint32_t lstart[256];
+    __shared__ int blk_s;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     for (int i = t; i < RS_WARPS * 256; i += RS_T) (&whist[0][0])[i] = 0u;
-    boff[t] = offs[(int64_t)t * nb + blockIdx.x];
+    if (ONESWEEP) {
+        if (t == 0) blk_s = (int)atomicAdd(tilectr, 1u);
+    } else {
+        boff[t] = offs[(int64_t)t * nb + blockIdx.x];
+    }
     __syncthreads();
-    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int blk = ONESWEEP ? blk_s : (int)blockIdx.x;
+    const int64_t tile0 = (int64_t)blk * RS_TILE;
     const int64_t rem = n - tile0;
     const int tn = rem < RS_TILE ? (int)rem : RS_TILE;   // keys in this tile
     const int wbase = w * (RS_TILE / RS_WARPS);
@@ -208,7 +247,7 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     for (int r = 0; r < RS_I; r++) {
         const bool ok = wbase + r * NB_WARP + lane < tn;
         const int d = ok ? (int)((key[r] >> shift) & 255u) : 256 + lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned peers = nb_match_bits<8>((unsigned)d, ok);
         const unsigned before = __popc(peers & lt);
         const uint32_t pre = ok ? whist[w][d] : 0u;
         __syncwarp();
@@ -223,6 +262,40 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
         const uint32_t v = whist[ww][t];
         whist[ww][t] = run;
         run += v;
+    }
+    if (ONESWEEP) {
+        // digit base of the pass, then this tile's place among the tiles
+        int32_t all;
+        const uint32_t dbase = (uint32_t)nb_block_scan256((int32_t)ghist[t], &all);
+        uint32_t *my = status + (int64_t)blk * 256 + t;
+        if (blk == 0) {
+            st_relaxed(my, RS_INC | run);
+            boff[t] = dbase;
+        } else {
+            st_relaxed(my, RS_AGG | run);
+            uint32_t excl = 0;
+            int j = blk - 1;
+            unsigned spins = 0;
+            while (j >= 0) {
+                const uint32_t sw = ld_relaxed(status + (int64_t)j * 256 + t);
+                if ((sw & ~RS_VAL) == 0u) {   // not published yet
+                    if (++spins >= NB_SPIN_LIMIT) {
+                        nb_bad(cnt, err, SITE_SORT_WAIT, j);
+                        break;
+                    }
+                    if ((spins & 63u) == 0u &&
+                        (*(volatile unsigned *)err & NB_EF_BOUNDS) != 0u)
+                        break;   // another block gave up
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += sw & RS_VAL;
+                if (sw & RS_INC) break;
+                j--;
+            }
+            st_relaxed(my, RS_INC | ((excl + run) & RS_VAL));
+            boff[t] = dbase + excl;
+        }
     }
     // run = the tile's count of digit t; lstart = exclusive scan over digits
     uint32_t x = run;
@@ -272,8 +345,31 @@ static void rs_setup()
 {
     static bool done = false;
     if (done) return;
-    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    cudaFuncSetAttribute(k_rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         RS_SMEM);
+    cudaFuncSetAttribute(k_rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         RS_SMEM);
     done = true;
+}
+
+// all eight 8-bit digit histograms in one read of the keys: shared-memory
+// counts (the hardware serialises equal digits), then one global add per
+// digit and block
+__global__ void __launch_bounds__(RS_T)
+k_rs_ghist(const uint64_t *__restrict__ key, int64_t n, uint32_t *__restrict__ ghist)
+{
+    __shared__ uint32_t h[8][256];
+    for (int i = threadIdx.x; i < 8 * 256; i += RS_T) (&h[0][0])[i] = 0u;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * RS_T + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * RS_T) {
+        const uint64_t k = key[i];
+#pragma unroll
+        for (int p = 0; p < 8; p++) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 8 * 256; i += RS_T)
+        if ((&h[0][0])[i]) atomicAdd(&ghist[i], (&h[0][0])[i]);
 }
 
 // Sort (c->keys, c->idx)[0..n) by key, stably.  Result in c->keys / c->idx.
@@ -284,14 +380,34 @@ void nb_radix_sort(nb_ctx *c, int64_t n)
     rs_setup();
     uint64_t *ka = c->keys, *kb = c->keys_alt;
     uint32_t *va = c->idx, *vb = c->idx_alt;
+    if (n < (int64_t)RS_VAL && (int64_t)nb * 256 * 8 + 8 * 256 + 8 <= c->rs_status_len) {
+        // onesweep: status words of the 8 passes, the 8 digit histograms and
+        // the 8 tile counters, zeroed together
+        uint32_t *ghist = c->rs_status + (int64_t)nb * 256 * 8;
+        uint32_t *tctr = ghist + 8 * 256;
+        cudaMemsetAsync(c->rs_status, 0, sizeof(uint32_t) * ((int64_t)nb * 256 * 8 + 8 * 256 + 8),
+                        c->stream);
+        k_rs_ghist<<<c->num_sms * 4, RS_T, 0, c->stream>>>(ka, n, ghist);
+        nb_launched(c, "k_rs_ghist");
+        for (int pass = 0; pass < 8; pass++) {
+            k_rs_scatter<true><<<nb, RS_T, RS_SMEM, c->stream>>>(
+                ka, va, kb, vb, nullptr, n, 8 * pass, nb, c->cnt, c->err,
+                c->rs_status + (int64_t)pass * nb * 256, ghist + 256 * pass, tctr + pass);
+            nb_launched(c, "k_rs_scatter");
+            uint64_t *tk = ka; ka = kb; kb = tk;
+            uint32_t *tv = va; va = vb; vb = tv;
+        }
+        return;   // 8 passes: the result is back in c->keys / c->idx
+    }
     for (int pass = 0; pass < 8; pass++) {
         const int shift = 8 * pass;
         k_rs_hist<<<nb, RS_T, 0, c->stream>>>(ka, n, shift, c->sort_hist, nb);
         nb_launched(c, "k_rs_hist");
         nb_exclusive_scan(c, (const int32_t *)c->sort_hist, (int32_t *)c->sort_hist,
                           (int64_t)256 * nb, nullptr, nullptr);
-        k_rs_scatter<<<nb, RS_T, RS_SMEM, c->stream>>>(ka, va, kb, vb, c->sort_hist, n,
-                                                       shift, nb, c->cnt, c->err);
+        k_rs_scatter<false><<<nb, RS_T, RS_SMEM, c->stream>>>(ka, va, kb, vb, c->sort_hist, n,
+                                                              shift, nb, c->cnt, c->err, nullptr,
+                                                              nullptr, nullptr);
         nb_launched(c, "k_rs_scatter");
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
@@ -333,8 +449,8 @@ void nb_radix_sort_passes(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uin
         const int shift = 8 * pass;
         k_rs_hist<<<nb, RS_T, 0, s>>>(ka, n, shift, hist, nb);
         nb_exclusive_scan_raw((const int32_t *)hist, (int32_t *)hist, (int64_t)256 * nb, bsum, s);
-        k_rs_scatter<<<nb, RS_T, RS_SMEM, s>>>(ka, va, kb, vb, hist, n, shift, nb, nullptr,
-                                               nullptr);
+        k_rs_scatter<false><<<nb, RS_T, RS_SMEM, s>>>(ka, va, kb, vb, hist, n, shift, nb, nullptr,
+                                                      nullptr, nullptr, nullptr, nullptr);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }

@@ -13,6 +13,8 @@
 //     next(node)       =  S[b+1] + b + 1, b = last particle of the node
 // Every FP64/FP32 operation that decides a key, a moment or an opening test
 // is written with explicit round-to-nearest intrinsics, never contracted.
+#include <climits>
+
 #include "nb_internal.cuh"
 
 
@@ -21,18 +23,25 @@ __global__ void __launch_bounds__(256)
 k_bbox(const double *__restrict__ pos, int64_t n, double *__restrict__ part,
        unsigned *__restrict__ err)
 {
-    double lo[3], hi[3];
+    // min / max on an order-preserving integer image of the FP64 bits (the
+    // FP64 pipe is slow on this part): k = bits for x >= 0, and the low 63
+    // bits flipped for x < 0, so signed order = numeric order (-0 sorts
+    // below +0, which changes neither the centre nor the extent)
+    const long long FLIP = 0x7fffffffffffffffll;
+    long long lo[3], hi[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+    for (int k = 0; k < 3; k++) { lo[k] = LLONG_MAX; hi[k] = LLONG_MIN; }
     bool bad = false;
+    const long long *__restrict__ pb = reinterpret_cast<const long long *>(pos);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const double x = pos[3 * i + k];
-            bad |= !isfinite(x);
-            lo[k] = fmin(lo[k], x);
-            hi[k] = fmax(hi[k], x);
+            const long long bits = pb[3 * i + k];
+            bad |= (bits & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;   // inf or NaN
+            const long long key = bits ^ ((bits >> 63) & FLIP);
+            lo[k] = min(lo[k], key);
+            hi[k] = max(hi[k], key);
         }
     }
     if (bad) atomicOr(err, NB_EF_NONFINITE);
@@ -40,19 +49,25 @@ k_bbox(const double *__restrict__ pos, int64_t n, double *__restrict__ part,
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            lo[k] = fmin(lo[k], __shfl_down_sync(0xffffffffu, lo[k], o));
-            hi[k] = fmax(hi[k], __shfl_down_sync(0xffffffffu, hi[k], o));
+            lo[k] = min(lo[k], __shfl_down_sync(0xffffffffu, lo[k], o));
+            hi[k] = max(hi[k], __shfl_down_sync(0xffffffffu, hi[k], o));
         }
-    __shared__ double s[8][6];
+    __shared__ long long s[8][6];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0)
         for (int k = 0; k < 3; k++) { s[w][k] = lo[k]; s[w][3 + k] = hi[k]; }
     __syncthreads();
     if (threadIdx.x < 6) {
-        double v = s[0][threadIdx.x];
+        long long v = s[0][threadIdx.x];
         for (int ww = 1; ww < 8; ww++)
-            v = threadIdx.x < 3 ? fmin(v, s[ww][threadIdx.x]) : fmax(v, s[ww][threadIdx.x]);
-        part[blockIdx.x * 6 + threadIdx.x] = v;
+            v = threadIdx.x < 3 ? min(v, s[ww][threadIdx.x]) : max(v, s[ww][threadIdx.x]);
+        // back to FP64 bits (the map is its own inverse); a block that saw
+        // no particle keeps +-inf
+        double x;
+        if (v == LLONG_MAX) x = INFINITY;
+        else if (v == LLONG_MIN) x = -INFINITY;
+        else x = __longlong_as_double(v ^ ((v >> 63) & FLIP));
+        part[blockIdx.x * 6 + threadIdx.x] = x;
     }
 }
 
@@ -123,10 +138,11 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x)
 
 __device__ __forceinline__ uint32_t grid_coord(double x, double corner, double scale)
 {
-    const double f = floor(__dmul_rn(__dsub_rn(x, corner), scale));
-    if (f < 0.0) return 0u;
-    if (f > 2097151.0) return 2097151u;
-    return (uint32_t)f;
+    // floor by a round-down conversion (saturating outside int64), then the
+    // clamp to the grid in integers: fewer FP64-pipe instructions than
+    // floor + compares + conversion, same result
+    const long long f = __double2ll_rd(__dmul_rn(__dsub_rn(x, corner), scale));
+    return f < 0 ? 0u : (f > 2097151 ? 2097151u : (uint32_t)f);
 }
 
 __global__ void __launch_bounds__(256)
@@ -339,7 +355,7 @@ k_depth_hist(const int8_t *__restrict__ depth, const long long *__restrict__ cnt
 }
 
 // Stable scatter by depth, staged like the radix sort's: nodes are ranked
-// per warp with match-any, placed in the tile's depth order in shared
+// per warp with a ballot match, placed in the tile's depth order in shared
 // memory, then written out as contiguous runs.  Tiles past the node count
 // return at once (the grid covers the node capacity).
 __global__ void __launch_bounds__(DS_T)
@@ -374,7 +390,7 @@ k_depth_scatter(const int8_t *__restrict__ depth, long long *__restrict__ cnt,
     for (int r = 0; r < DS_I; r++) {
         const bool ok = wbase + r * NB_WARP + lane < tn && dep[r] >= 0 && dep[r] < NB_DEPTHS;
         const int d = ok ? dep[r] : 32 + lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned peers = nb_match_bits<5>((unsigned)d, ok);
         const unsigned before = __popc(peers & lt);
         const uint32_t pre = ok ? whist[w][d] : 0u;
         __syncwarp();
@@ -532,6 +548,13 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
 // adds M and sum(m x) over the children in octant order; the sums are made
 // visible (fence) before the arrival at the parent; then COM = sum(m x) / M,
 // s = |COM - geometric centre| and the FP32 hi/lo split of the record.
+#define CL_I 16
+#define CL_TILE (256 * CL_I)
+
+// One tile of CL_TILE level-order nodes per block.  Ranks inside a bucket
+// come from shared-memory counters and each block reserves its range of a
+// bucket with one global atomic, so no counter is hit by every warp; the
+// order of cells inside a bucket is free (each cell's moments are its own).
 __global__ void __launch_bounds__(256)
 k_cell_list(const int16_t *__restrict__ cbkt, int32_t *__restrict__ cbkt_cnt,
             long long *__restrict__ cnt, int32_t *__restrict__ clist, int64_t clist_len,
@@ -539,13 +562,17 @@ k_cell_list(const int16_t *__restrict__ cbkt, int32_t *__restrict__ cbkt_cnt,
 {
     static_assert(NB_CBKT <= 256, "one bucket per thread");
     __shared__ int32_t start[NB_CBKT + 1];
+    __shared__ int32_t local[NB_CBKT];
+    const int t = threadIdx.x;
     {
-        const int t = threadIdx.x;
         const int32_t sz = t < NB_CBKT ? cbkt_cnt[t] : 0;
         const int32_t padded = (sz + NB_WARP - 1) / NB_WARP * NB_WARP;
         int32_t all;
         const int32_t st = nb_block_scan256(padded, &all);
-        if (t < NB_CBKT) start[t] = st;
+        if (t < NB_CBKT) {
+            start[t] = st;
+            local[t] = 0;
+        }
         if (t == 0) start[NB_CBKT] = all;
         if (blockIdx.x == 0 && t == 0) cnt[CNT_MOM_CHUNKS] = all / NB_WARP;
         // block 0 marks each bucket's padding (at most 31 slots): no cell
@@ -555,29 +582,33 @@ k_cell_list(const int16_t *__restrict__ cbkt, int32_t *__restrict__ cbkt_cnt,
         __syncthreads();
     }
     const int32_t total = (int32_t)cnt[CNT_NODES];
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const int32_t nw = gridDim.x * (blockDim.x >> 5);
-    for (int32_t base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * NB_WARP;
-         base < total; base += nw * NB_WARP) {
-        const int32_t b = base + lane;
-        int k = b < total ? (int)cbkt[b] : -1;
-        if (k >= NB_CBKT) {
-            nb_bad(cnt, err, SITE_MOMENTS, b);
-            k = -1;
+    const int64_t tile0 = (int64_t)blockIdx.x * CL_TILE;
+    if (tile0 >= total) return;
+    int k[CL_I], rank[CL_I];
+#pragma unroll
+    for (int r = 0; r < CL_I; r++) {
+        const int64_t b = tile0 + r * 256 + t;
+        k[r] = b < total ? (int)cbkt[b] : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < CL_I; r++) {
+        if (k[r] >= NB_CBKT) {
+            nb_bad(cnt, err, SITE_MOMENTS, tile0 + r * 256 + t);
+            k[r] = -1;
         }
-        const int key = k >= 0 ? k : NB_CBKT + lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(peers) - 1;
-        int32_t got = 0;
-        if (k >= 0 && lane == leader) got = atomicAdd(&cbkt_cnt[NB_CBKT + k], __popc(peers));
-        got = __shfl_sync(0xffffffffu, got, leader);
-        if (k < 0) continue;
-        const int32_t pos = start[k] + got + __popc(peers & lt);
-        if (!nb_in(pos >= 0 && pos < start[k + 1] && pos < clist_len, cnt, err, SITE_MOMENTS,
+        rank[r] = k[r] >= 0 ? atomicAdd(&local[k[r]], 1) : 0;
+    }
+    __syncthreads();
+    if (t < NB_CBKT && local[t] > 0) local[t] = atomicAdd(&cbkt_cnt[NB_CBKT + t], local[t]);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < CL_I; r++) {
+        if (k[r] < 0) continue;
+        const int32_t pos = start[k[r]] + local[k[r]] + rank[r];
+        if (!nb_in(pos >= 0 && pos < start[k[r] + 1] && pos < clist_len, cnt, err, SITE_MOMENTS,
                    pos))
             continue;
-        clist[pos] = b;
+        clist[pos] = (int32_t)(tile0 + r * 256 + t);
     }
 }
 
@@ -915,8 +946,9 @@ static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t 
         c->keys, c->root, sys_sorted, c->p_hi, c->p_lo, c->p_x64, c->cnt, c->wrec, c->b_mass,
         c->b_mx, c->b_com, c->b_up, c->lcount, c->cbkt, c->cbkt_cnt, n, c->err);
     nb_launched(c, "k_bfs_records");
-    k_cell_list<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(c->cbkt, c->cbkt_cnt, c->cnt,
-                                                                 c->clist, c->clist_len, c->err);
+    const int cl_blocks = (int)((c->max_nodes + CL_TILE - 1) / CL_TILE);
+    k_cell_list<<<cl_blocks > 0 ? cl_blocks : 1, 256, 0, s>>>(c->cbkt, c->cbkt_cnt, c->cnt,
+                                                               c->clist, c->clist_len, c->err);
     nb_launched(c, "k_cell_list");
     static int mblocks = 0;
     if (mblocks == 0) {
