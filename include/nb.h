@@ -168,6 +168,20 @@ int nb_forces(nb_ctx *ctx, float eps, float *acc_dev, float *pot_dev,
 int nb_leapfrog_step(nb_ctx *ctx, double *pos_dev, double *vel_dev,
                      const float *mass_dev, int64_t n, double dt);
 int nb_leapfrog_reset(nb_ctx *ctx);
+/* nb_leapfrog_step on HOST buffers (pinned memory lets the copies run
+ * asynchronously): the library copies pos_host, vel_host (n x 3 FP64) and
+ * mass_host (n FP32) into device buffers of its own (allocated at the first
+ * such call, 52 B per particle of cfg.max_n), runs the step there and writes
+ * the new positions and velocities back into pos_host and vel_host.  The
+ * positions leave on a second stream as soon as the drift has written them,
+ * overlapping the tree build, walk and force; the velocities follow the
+ * closing kick.  With sync_checks the call returns after both copies; without,
+ * they complete in stream order on cfg.stream and the host buffers must stay
+ * valid until that stream is synchronised.  The kept a(x) is for the state the
+ * previous step returned: after changing the host state otherwise, call
+ * nb_leapfrog_reset.  Errors: as nb_leapfrog_step, NOMEM. */
+int nb_leapfrog_step_host(nb_ctx *ctx, double *pos_host, double *vel_host,
+                          const float *mass_host, int64_t n, double dt);
 /* The accelerations (n x 3 FP32, caller order) kept by the last step. */
 int nb_leapfrog_acc(nb_ctx *ctx, float *acc_dev);
 

@@ -37,6 +37,7 @@ EXPORTED = [
     "nb_walk_groups_learned", "nb_group_errors", "nb_theta_labels",
     "nb_copy_group_lengths", "nb_build_tree_batched", "nb_leapfrog_step_batched",
     "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune", "nb_selftest_wait",
+    "nb_leapfrog_step_host",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -84,6 +85,7 @@ def _load():
     L.nb_forces.argtypes = [vp, C.c_float, vp, vp, i32]
     L.nb_leapfrog_step.argtypes = [vp, vp, vp, vp, i64, C.c_double]
     L.nb_leapfrog_reset.argtypes = [vp]
+    L.nb_leapfrog_step_host.argtypes = [vp, vp, vp, vp, i64, C.c_double]
     L.nb_leapfrog_acc.argtypes = [vp, vp]
     L.nb_direct_sum.argtypes = [vp, vp, i64, C.c_double, vp, i64, vp, vp, vp]
     L.nb_sync_status.argtypes = [vp]
@@ -283,6 +285,26 @@ class NBody:
                                      _dptr(mass, torch.float32, None, "mass"),
                                      int(pos.shape[0]), float(dt)), "nb_leapfrog_step")
         self.n = int(pos.shape[0])
+
+    def leapfrog_step_host(self, pos, vel, mass, dt):
+        """One KDK step on host (CPU) tensors or arrays, pinned for overlap:
+        pos, vel (n x 3 float64) are updated in place by the library, which
+        does the host-device copies itself."""
+        def hp(t, dtype, cols, name):
+            a = t.numpy() if hasattr(t, "numpy") else t
+            if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+                raise TypeError(f"{name} must be a C-contiguous {np.dtype(dtype).name} host array")
+            if cols and (a.ndim != 2 or a.shape[1] != cols):
+                raise TypeError(f"{name} must be n x {cols}")
+            return a.ctypes.data, a.shape[0]
+        p, n = hp(pos, np.float64, 3, "pos")
+        v, nv = hp(vel, np.float64, 3, "vel")
+        m, nm = hp(mass, np.float32, None, "mass")
+        if nv != n or nm != n:
+            raise ValueError("pos, vel and mass must have the same length")
+        _check(_lib.nb_leapfrog_step_host(self._h, p, v, m, int(n), float(dt)),
+               "nb_leapfrog_step_host")
+        self.n = int(n)
 
     def leapfrog_reset(self):
         _check(_lib.nb_leapfrog_reset(self._h), "nb_leapfrog_reset")

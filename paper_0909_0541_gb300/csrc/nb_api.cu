@@ -53,11 +53,15 @@ static void free_all(nb_ctx *c)
 {
     // three device allocations: the context arena, the list storage, the
     // walk queues
-    void *ptrs[] = {c->arena, c->list_mem, c->wq};
+    void *ptrs[] = {c->arena, c->list_mem, c->wq, c->hstage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    c->arena = c->list_mem = nullptr;
+    c->arena = c->list_mem = c->hstage = nullptr;
     c->wq = nullptr;
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->ev_drift) cudaEventDestroy(c->ev_drift);
+    if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+    c->copy_stream = nullptr;
     if (c->cnt_host) cudaFreeHost(c->cnt_host);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->ev) {
@@ -628,8 +632,10 @@ static int force_pass(nb_ctx *c, const double *pos, const float *mass, int64_t n
     return nb_forces(c, c->cfg.eps, c->acc_cache, c->pot_cache, c->cfg.precision);
 }
 
+// pos_out: host buffer that receives the positions as soon as the drift has
+// written them, copied on the copy stream while the step goes on (host steps)
 static int leapfrog(nb_ctx *c, double *pos, double *vel, const float *mass, int64_t n,
-                    double dt, const int64_t *off, int64_t nsys)
+                    double dt, const int64_t *off, int64_t nsys, double *pos_out = nullptr)
 {
     if (!c || n < 0 || n > c->max_n || (n > 0 && (!pos || !vel || !mass)) || !isfinite(dt))
         return NB_ERR_INVALID_ARG;
@@ -645,6 +651,13 @@ static int leapfrog(nb_ctx *c, double *pos, double *vel, const float *mass, int6
     nb_launch_kick(c, vel, c->acc_cache, n, h);
     nb_launch_drift(c, pos, vel, n, dt);
     phase_end(c, tk, NB_PHASE_INTEGRATE);
+    if (pos_out) {
+        CK(cudaEventRecord(c->ev_drift, c->stream));
+        CK(cudaStreamWaitEvent(c->copy_stream, c->ev_drift, 0));
+        CK(cudaMemcpyAsync(pos_out, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+                           c->copy_stream));
+        CK(cudaEventRecord(c->ev_copied, c->copy_stream));
+    }
     rc = force_pass(c, pos, mass, n, off, nsys);
     if (rc) {
         c->acc_valid = 0;
@@ -660,6 +673,43 @@ int nb_leapfrog_step(nb_ctx *c, double *pos, double *vel, const float *mass, int
                      double dt)
 {
     return leapfrog(c, pos, vel, mass, n, dt, nullptr, 1);
+}
+
+int nb_leapfrog_step_host(nb_ctx *c, double *pos_host, double *vel_host, const float *mass_host,
+                          int64_t n, double dt)
+{
+    if (!c || n < 0 || n > c->max_n || (n > 0 && (!pos_host || !vel_host || !mass_host)) ||
+        !isfinite(dt))
+        return NB_ERR_INVALID_ARG;
+    if (n == 0) return NB_OK;
+    if (!c->copy_stream) {
+        if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return NB_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&c->ev_drift, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming) != cudaSuccess)
+            return NB_ERR_CUDA;
+    }
+    if (!c->hstage) {   // device copies of the state, for max_n particles
+        CK(cudaStreamSynchronize(c->stream));
+        if (!dmalloc(&c->hstage, (sizeof(double) * 6 + sizeof(float)) * (size_t)c->max_n))
+            return NB_ERR_NOMEM;
+    }
+    double *pos = (double *)c->hstage;
+    double *vel = pos + 3 * c->max_n;
+    float *mass = (float *)(vel + 3 * c->max_n);
+    CK(cudaMemcpyAsync(vel, vel_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(pos, pos_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(mass, mass_host, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+    // positions leave on the copy stream right after the drift; velocities
+    // after the closing kick; the stream then waits for both
+    const int rc = leapfrog(c, pos, vel, mass, n, dt, nullptr, 1, pos_host);
+    if (rc) {
+        cudaStreamSynchronize(c->copy_stream);
+        return rc;
+    }
+    CK(cudaMemcpyAsync(vel_host, vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_copied, 0));
+    return finish(c);
 }
 
 int nb_leapfrog_step_batched(nb_ctx *c, double *pos, double *vel, const float *mass,

@@ -216,6 +216,12 @@ struct nb_ctx {
     // captured leapfrog steps
     cudaGraphExec_t graph_exec;
 
+    // steps on host buffers: device copies of the state (one allocation, made
+    // at the first such step), a copy stream and its two events
+    void *hstage;
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_drift, ev_copied;
+
     // timing and launch accounting
     int timing;
     int ev_used;

@@ -193,6 +193,7 @@ k_rs_hist(const uint64_t *__restrict__ key, int64_t n, int shift,
 #define RS_AGG (1u << 30)
 #define RS_INC (2u << 30)
 #define RS_VAL ((1u << 30) - 1u)
+#define RS_LB 4   // look-back window: predecessor tiles read per round trip
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
 {
@@ -273,12 +274,33 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
             boff[t] = dbase;
         } else {
             st_relaxed(my, RS_AGG | run);
+            // look back RS_LB tiles per round trip: the window's words are
+            // loaded together, then taken in order until an inclusive prefix
+            // (done) or a tile not yet published (wait and reload from there)
             uint32_t excl = 0;
             int j = blk - 1;
             unsigned spins = 0;
-            while (j >= 0) {
-                const uint32_t sw = ld_relaxed(status + (int64_t)j * 256 + t);
-                if ((sw & ~RS_VAL) == 0u) {   // not published yet
+            bool done = false;
+            while (!done && j >= 0) {
+                uint32_t sw[RS_LB];
+#pragma unroll
+                for (int q = 0; q < RS_LB; q++)
+                    sw[q] = j - q >= 0 ? ld_relaxed(status + (int64_t)(j - q) * 256 + t) : 0u;
+                int used = 0;
+                bool wait = false;
+#pragma unroll
+                for (int q = 0; q < RS_LB; q++) {
+                    if (done || wait || j - q < 0) continue;
+                    if ((sw[q] & ~RS_VAL) == 0u) {   // not published yet
+                        wait = true;
+                        continue;
+                    }
+                    excl += sw[q] & RS_VAL;
+                    used++;
+                    if (sw[q] & RS_INC) done = true;
+                }
+                j -= used;
+                if (wait) {
                     if (++spins >= NB_SPIN_LIMIT) {
                         nb_bad(cnt, err, SITE_SORT_WAIT, j);
                         break;
@@ -287,11 +309,7 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                         (*(volatile unsigned *)err & NB_EF_BOUNDS) != 0u)
                         break;   // another block gave up
                     __nanosleep(32);
-                    continue;
                 }
-                excl += sw & RS_VAL;
-                if (sw & RS_INC) break;
-                j--;
             }
             st_relaxed(my, RS_INC | ((excl + run) & RS_VAL));
             boff[t] = dbase + excl;

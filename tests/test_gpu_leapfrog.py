@@ -68,3 +68,38 @@ def test_many_steps_conserve_energy(oracle_lib):
         ctx.leapfrog_step(pos, vel, mass, dt)
     assert np.max(np.abs(pos.cpu().numpy() - ps.pos)) < 1e-4
     ctx.close()
+
+
+def test_host_buffer_step_equals_device_step():
+    """nb_leapfrog_step_host (the library does the copies, positions leave on
+    a second stream after the drift) gives the same bits as nb_leapfrog_step
+    on device buffers, step after step, with and without synchronising
+    checks."""
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(20000, 31)
+    eps, theta, n_crit, dt = 1.0 / 64, 0.75, 64, 1.0 / 128
+    dev = torch.device("cuda")
+    pos = torch.from_numpy(ps.pos).to(dev)
+    vel = torch.from_numpy(ps.vel).to(dev)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    a = nb.NBody(ps.n, eps=eps, theta=theta, n_crit=n_crit, stream=stream)
+    b = nb.NBody(ps.n, eps=eps, theta=theta, n_crit=n_crit, stream=stream)
+    hpos = torch.from_numpy(ps.pos.copy()).pin_memory()
+    hvel = torch.from_numpy(ps.vel.copy()).pin_memory()
+    hmass = torch.from_numpy(ps.mass.copy()).pin_memory()
+    with torch.cuda.stream(stream):
+        for k in range(4):
+            if k == 2:
+                a.set_sync_checks(False)
+                b.set_sync_checks(False)
+            a.leapfrog_step(pos, vel, mass, dt)
+            b.leapfrog_step_host(hpos, hvel, hmass, dt)
+        stream.synchronize()
+        a.sync_status()
+        b.sync_status()
+    assert np.array_equal(pos.cpu().numpy(), hpos.numpy())
+    assert np.array_equal(vel.cpu().numpy(), hvel.numpy())
+    with pytest.raises(TypeError):
+        b.leapfrog_step_host(hpos.float(), hvel, hmass, dt)
