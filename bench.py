@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--n-crit", type=int, default=None)
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--fused", action="store_true",
+                    help="force passes walk and sum in one kernel, no interaction lists")
     ap.add_argument("--judge-targets", type=int, default=8192)
     ap.add_argument("--train-groups", type=int, default=6000,
                     help="learned4.19m: groups labelled for training")
@@ -136,14 +138,22 @@ def peaks():
         return {}
 
 
+def force_source_hash():
+    """sha256 prefix of the list force kernel's source (kernel and header)."""
+    csrc = os.path.join(ROOT, "paper_0909_0541_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("nb_force.cu", "nb_force.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def force_traffic_record():
     """DRAM bytes per force-kernel launch from the committed ncu summary,
     valid only while the kernel source is the one that was profiled."""
     path = os.path.join(ROOT, "profiles", "k_force_traffic.txt")
-    src = os.path.join(ROOT, "paper_0909_0541_gb300", "csrc", "nb_force.cu")
     try:
         rec = dict(l.split("=", 1) for l in open(path).read().split() if "=" in l)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = force_source_hash()
         if rec.get("source_sha256_16") != h:
             return None
         return float(rec["bytes_per_launch_scaled"])
@@ -227,6 +237,18 @@ def cpu_oracle_rate(ps, w, seconds, seed=7, name=WORKLOAD):
                 interactions=int(inter), seconds=t_total)
 
 
+def cpu_direct_rate(ps, w, targets=64, seed=5):
+    """Interactions/s of the oracle's FP64 direct sum (every source, a seeded
+    sample of targets), the judge's CPU counterpart."""
+    import oracle
+    tg = np.random.default_rng(seed).choice(ps.n, min(targets, ps.n), replace=False)
+    t0 = time.perf_counter()
+    oracle.direct(ps.pos, ps.mass, w["eps"], tg)
+    t = time.perf_counter() - t0
+    return {"value": len(tg) * (ps.n - 1) / t, "unit": "interactions/s",
+            "cores": oracle.num_threads(), "sample": f"{len(tg)} targets x {ps.n} sources, FP64"}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -300,6 +322,8 @@ def run_ours(args, ws, rank, local):
     # the copies above ran on torch's current stream; the context's stream
     # must not read pos / vel before they land
     stream.wait_stream(torch.cuda.current_stream(dev))
+    if args.fused:
+        ctx.set_fused(True)
     dt = w["dt"]
     with torch.cuda.stream(stream):
         # first step synchronises: sizes the interaction-list storage
@@ -407,11 +431,31 @@ def run_ours(args, ws, rank, local):
     achieved = FP32_OPS_PER_INTERACTION * inter_per_launch / t_launch / 1e12
     peak = sms * 128 * sm_max * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": force_traffic_record(),
-                "kernel": "k_force", "ops": "FP32-pipe lane ops (13 per interaction)",
+                "frac": achieved / peak,
+                "traffic": None if args.fused else force_traffic_record(),
+                "kernel": "k_walk_force (walk included)" if args.fused else "k_force",
+                "ops": "FP32-pipe lane ops (13 per interaction)",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
                 "frac_at_sampled_clock": (achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
                                           if clocks.get("sm_mhz") else None)}
+    # the SM clock the measured bf16 GEMM settled at under the power cap; this
+    # kernel runs far below the cap (see "clocks"), so the max-clock fraction
+    # above is the one that describes it
+    gemm_mhz = (pk.get("clocks_under_load") or {}).get("sm_mhz_median")
+    if gemm_mhz:
+        roofline["frac_at_gemm_load_clock"] = achieved / (sms * 128 * gemm_mhz * 1e6 / 1e12)
+        roofline["gemm_load_clock_mhz"] = gemm_mhz
+    # the walk (with group formation): interaction-list bytes it writes per
+    # call against the measured copy bandwidth; it is latency-bound
+    walk_ms, walk_calls = timing["walk"]
+    list_bytes = 0 if args.fused else st1["list_entries"] * 20
+    hbm = float(pk.get("hbm_gbs") or 6783.5)
+    walk_gbs = list_bytes / (walk_ms / 1e3 / max(walk_calls, 1)) / 1e9 if walk_ms > 0 else 0.0
+    secondary = {"walk": {"bound": "latency", "bytes_written_per_call": list_bytes,
+                          "achieved_gbs": walk_gbs, "hbm_peak_gbs": hbm,
+                          "frac": walk_gbs / hbm,
+                          "note": "list records (16 B) and node ids (4 B); the 64-byte node "
+                                  "reads come mostly from L2"}}
 
     phases = {k: {"ms_per_call": v[0] / max(v[1], 1), "calls": v[1]}
               for k, v in timing.items() if k != "launches"}
@@ -419,6 +463,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(ps, w, args.cpu_seconds, name=args.workload)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["direct_sum"] = cpu_direct_rate(ps, w)
 
     if rank == 0:
         line = {
@@ -427,6 +472,7 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "theta": w["theta"], "eps": w["eps"],
                        "n_crit": w["n_crit"], "dt": dt, "precision": args.precision,
+                       "force_path": "fused walk+force" if args.fused else "lists",
                        "step": "KDK leapfrog: tree build + group walk + force + kicks/drift",
                        "l2": "inputs larger than L2 (positions+velocities 138 MB, lists "
                              f"{st1['list_entries'] * 20 / 1e9:.2f} GB per step)",
@@ -439,6 +485,7 @@ def run_ours(args, ws, rank, local):
             "phases_ms": phases,
             "gpu_launches": int(timing["launches"]),
             "roofline": roofline,
+            "secondary_rooflines": secondary,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,

@@ -159,6 +159,24 @@ int nb_walk_groups(nb_ctx *ctx, float theta, int n_crit,
 int nb_forces(nb_ctx *ctx, float eps, float *acc_dev, float *pot_dev,
               int precision);
 
+/* Groups, walk and force sum in one pass without interaction lists in
+ * device memory: the fused walk-and-sum design of Fig. "treegpu" (Sec. "Our
+ * GPU implementation") in group form.  After nb_build_tree: forms the groups
+ * of n_crit (as nb_walk_groups) and, per force work item, walks the group with
+ * the opening angle theta and sums Eq. (gravity) on the fly through a small
+ * shared-memory buffer.  acc_dev / pot_dev / precision as nb_forces; the
+ * results equal nb_walk_groups + nb_forces bit for bit.  The walk is repeated
+ * for each 64-target item of a group larger than 64.  Afterwards there are no
+ * lists to export (nb_forces and nb_copy_lists return NB_ERR_STATE until the
+ * next nb_walk_groups).  Interaction counts go to nb_get_stats as for the list
+ * path.  Errors: STATE (no tree), INVALID_ARG, CAPACITY (a walk frontier
+ * outgrew the queues with sync_checks off), WALK_LIMIT, CUDA, NOMEM. */
+int nb_forces_fused(nb_ctx *ctx, float theta, int n_crit, float eps, float *acc_dev,
+                    float *pot_dev, int precision);
+/* on != 0: the force passes of nb_leapfrog_step (and its batched, host and
+ * graph forms) use nb_forces_fused instead of nb_walk_groups + nb_forces. */
+int nb_set_fused(nb_ctx *ctx, int on);
+
 /* One kick-drift-kick leapfrog step of size dt in FP64 ("integrate orbits
  * ... and repeat", Sec. Introduction): v += a dt/2; x += v dt; rebuild the
  * tree, walk and force with cfg.eps, cfg.theta, cfg.n_crit, cfg.precision;

@@ -37,7 +37,7 @@ EXPORTED = [
     "nb_walk_groups_learned", "nb_group_errors", "nb_theta_labels",
     "nb_copy_group_lengths", "nb_build_tree_batched", "nb_leapfrog_step_batched",
     "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune", "nb_selftest_wait",
-    "nb_leapfrog_step_host",
+    "nb_leapfrog_step_host", "nb_forces_fused", "nb_set_fused",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -83,6 +83,8 @@ def _load():
     L.nb_build_tree.argtypes = [vp, vp, vp, i64]
     L.nb_walk_groups.argtypes = [vp, C.c_float, i32, vp]
     L.nb_forces.argtypes = [vp, C.c_float, vp, vp, i32]
+    L.nb_forces_fused.argtypes = [vp, C.c_float, i32, C.c_float, vp, vp, i32]
+    L.nb_set_fused.argtypes = [vp, i32]
     L.nb_leapfrog_step.argtypes = [vp, vp, vp, vp, i64, C.c_double]
     L.nb_leapfrog_reset.argtypes = [vp]
     L.nb_leapfrog_step_host.argtypes = [vp, vp, vp, vp, i64, C.c_double]
@@ -277,6 +279,19 @@ class NBody:
         _check(_lib.nb_forces(self._h, float(eps), _dptr(acc, torch.float32, 3, "acc"),
                               _dptr(pot, torch.float32, None, "pot"),
                               PRECISION.get(precision, precision)), "nb_forces")
+
+    def set_fused(self, on: bool):
+        """Leapfrog force passes without interaction lists (nb_set_fused)."""
+        _check(_lib.nb_set_fused(self._h, 1 if on else 0), "nb_set_fused")
+
+    def forces_fused(self, theta, n_crit, eps, acc, pot=None, precision="fp32"):
+        """Groups, walk and force in one pass with no interaction lists in
+        device memory (same results as walk_groups + forces)."""
+        import torch
+        _check(_lib.nb_forces_fused(self._h, float(theta), int(n_crit), float(eps),
+                                    _dptr(acc, torch.float32, 3, "acc"),
+                                    _dptr(pot, torch.float32, None, "pot"),
+                                    PRECISION.get(precision, precision)), "nb_forces_fused")
 
     def leapfrog_step(self, pos, vel, mass, dt):
         import torch

@@ -606,6 +606,47 @@ int nb_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision)
     return finish(c);
 }
 
+int nb_forces_fused(nb_ctx *c, float theta, int n_crit, float eps, float *acc, float *pot,
+                    int precision)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!(theta >= 0.f) || n_crit < 1 || !(eps >= 0.f) || precision < 0 || precision > 2 ||
+        (c->n > 0 && !acc))
+        return NB_ERR_INVALID_ARG;
+    if (!c->has_tree) return NB_ERR_STATE;
+    c->has_lists = 0;   // the fused pass leaves no lists behind
+    if (c->n == 0) return NB_OK;
+    const int tk = phase_begin(c);
+    nb_launch_groups(c, theta, n_crit, nullptr);
+    c->has_groups = 1;
+    if (!c->wq) {
+        CK(cudaStreamSynchronize(c->stream));
+        if (!alloc_queues(c, c->wq_cap > 0 ? c->wq_cap : 4096)) return NB_ERR_NOMEM;
+    }
+    int rc = NB_OK;
+    for (int attempt = 0; attempt < 4; attempt++) {
+        nb_launch_fused(c, eps, acc, pot, precision);
+        if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
+        if (!c->sync_checks) break;
+        unsigned bits = 0;
+        rc = sync_read_bits(c, &bits);
+        if (rc) return rc;
+        rc = err_code(bits);
+        if (!(bits & NB_EF_QUEUE)) break;
+        // a frontier outgrew the walk queues: grow them and sum again
+        rc = read_counters(c);
+        if (rc) return rc;
+        const int64_t want = 2 * (c->cnt_host[CNT_QMAX] > c->wq_cap ? c->cnt_host[CNT_QMAX]
+                                                                    : c->wq_cap);
+        CK(cudaStreamSynchronize(c->stream));
+        if (!alloc_queues(c, want)) return NB_ERR_NOMEM;
+        rc = NB_ERR_CAPACITY;
+    }
+    phase_end(c, tk, NB_PHASE_FORCE);
+    if (rc) return rc;
+    return finish(c);
+}
+
 int nb_leapfrog_reset(nb_ctx *c)
 {
     if (!c) return NB_ERR_INVALID_ARG;
@@ -627,9 +668,19 @@ static int force_pass(nb_ctx *c, const double *pos, const float *mass, int64_t n
 {
     int rc = off ? nb_build_tree_batched(c, pos, mass, off, nsys, n) : nb_build_tree(c, pos, mass, n);
     if (rc) return rc;
+    if (c->fused)
+        return nb_forces_fused(c, c->cfg.theta, c->cfg.n_crit, c->cfg.eps, c->acc_cache,
+                               c->pot_cache, c->cfg.precision);
     rc = nb_walk_groups(c, c->cfg.theta, c->cfg.n_crit, nullptr);
     if (rc) return rc;
     return nb_forces(c, c->cfg.eps, c->acc_cache, c->pot_cache, c->cfg.precision);
+}
+
+int nb_set_fused(nb_ctx *c, int on)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    c->fused = on ? 1 : 0;
+    return NB_OK;
 }
 
 // pos_out: host buffer that receives the positions as soon as the drift has
@@ -724,7 +775,8 @@ int nb_graph_capture_leapfrog(nb_ctx *c, double *pos, double *vel, const float *
                               int nsteps)
 {
     if (!c || !c->stream || nsteps < 1 || n < 1 || (offsets && nsys < 1)) return NB_ERR_INVALID_ARG;
-    if (!c->acc_valid || c->n != n || c->list_cap < 1 || !c->list_id) return NB_ERR_STATE;
+    if (!c->acc_valid || c->n != n || (!c->fused && (c->list_cap < 1 || !c->list_id)))
+        return NB_ERR_STATE;
     CK(cudaStreamSynchronize(c->stream));
     const int sync = c->sync_checks, timing = c->timing;
     c->sync_checks = 0;

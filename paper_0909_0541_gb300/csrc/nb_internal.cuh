@@ -224,6 +224,7 @@ struct nb_ctx {
 
     // timing and launch accounting
     int timing;
+    int fused;               // leapfrog force passes use the fused walk and force
     int ev_used;
     cudaEvent_t *ev;         // NB_EV_POOL pairs
     int *ev_phase;
@@ -278,6 +279,7 @@ int nb_launch_direct(const double *pos, const float *mass, int64_t n, double eps
 // nb_step.cu
 void nb_launch_kick(nb_ctx *c, double *vel, const float *acc, int64_t n, double h);
 void nb_launch_wait_probe(nb_ctx *c, unsigned limit);
+void nb_launch_fused(nb_ctx *c, float eps, float *acc, float *pot, int precision);
 void nb_launch_drift(nb_ctx *c, double *pos, const double *vel, int64_t n, double dt);
 
 __device__ __forceinline__ long long nb_atomic_add(long long *p, long long v)

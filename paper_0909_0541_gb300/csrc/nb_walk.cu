@@ -22,31 +22,10 @@
 // kernel reads: position relative to the group's box centre from the
 // two-float split of the FP64 centre of mass, fl32(fl32(hi - c) + lo), and
 // the FP32 mass.
-#include "nb_internal.cuh"
+#include "nb_walk.cuh"
 
 #define WALK_T 256
 #define WALK_WARPS (WALK_T / NB_WARP)
-// the first WQ_SMEM positions of each frontier queue live in shared memory
-// (8 warps x 2 queues x 768 x 4 B = 48 KB per block); longer frontiers
-// continue at the same positions in the warp's global queue
-#define WQ_SMEM 768
-
-// Eq. (mac) for a group: squared FP32 distance from the cell's centre of
-// mass to the group box against (l / theta + s)^2, every operation rounded
-// on its own in the order the oracle uses.
-__device__ __forceinline__ bool far_enough(const float4 &a, float l, float s,
-                                           const float4 &lo, const float4 &hi,
-                                           float invth)
-{
-    const float ex = fmaxf(fmaxf(__fsub_rn(lo.x, a.x), __fsub_rn(a.x, hi.x)), 0.0f);
-    const float ey = fmaxf(fmaxf(__fsub_rn(lo.y, a.y), __fsub_rn(a.y, hi.y)), 0.0f);
-    const float ez = fmaxf(fmaxf(__fsub_rn(lo.z, a.z), __fsub_rn(a.z, hi.z)), 0.0f);
-    float d2 = __fmul_rn(ex, ex);
-    d2 = __fadd_rn(d2, __fmul_rn(ey, ey));
-    d2 = __fadd_rn(d2, __fmul_rn(ez, ez));
-    const float w = __fadd_rn(__fmul_rn(l, invth), s);
-    return d2 > __fmul_rn(w, w);
-}
 
 // PROBE: walk without writing lists and turn the list statistics into the
 // group's features for the learned opening angle (16 floats per group):
@@ -54,36 +33,6 @@ __device__ __forceinline__ bool far_enough(const float4 &a, float l, float s,
 //   5 ln(|box centre - root centre| / L + 1e-6);  6 ln(list length + 1)
 //   7 accepted cells / list length;  8-10 ln(min, mean, max distance from the
 //   box centre to accepted cells' centres of mass / L + 1e-7);  11 depth / 22
-// one frontier node's level-order records
-struct NodeRec {
-    int32_t b;
-    bool valid;
-    int4 wb;     // preorder id, preorder next, first child, children
-    float4 a;    // centre of mass (hi), mass
-    float2 wc;   // l, s
-    float4 d;    // centre of mass (lo)
-};
-
-template <bool PROBE>
-__device__ __forceinline__ NodeRec load_node(int32_t i, int32_t na, const int32_t *qin_s,
-                                             const int32_t *qin,
-                                             const nb_wrec *__restrict__ wrec, int32_t total,
-                                             long long *cnt, unsigned *err)
-{
-    NodeRec r;
-    r.b = 0;
-    if (i < na) r.b = i < WQ_SMEM ? qin_s[i] : qin[i];
-    r.valid = i < na && nb_in(r.b >= 0 && r.b < total, cnt, err, SITE_WALK_NODE, r.b);
-    if (r.valid) {
-        const nb_wrec *w = wrec + r.b;     // one 64-byte line
-        r.wb = w->b;
-        r.a = w->a;
-        r.wc = w->c;
-        if (!PROBE) r.d = w->d;
-    }
-    return r;
-}
-
 // the opening test of one chunk of 32 frontier nodes (one per lane): emit
 // particles and accepted cells to the list (ballot + popc), queue the
 // children of opened cells (warp prefix sum)

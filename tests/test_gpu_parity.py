@@ -268,3 +268,68 @@ def test_bounded_wait_gives_up_and_context_survives(oracle_lib):
     ctx.build_tree(torch.from_numpy(ps.pos).to(dev), torch.from_numpy(ps.mass).to(dev))
     ctx.sync_status()
     assert_tree_equal(dict(tree=ctx.copy_tree()), oracle_lib.Tree(ps.pos, ps.mass))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fused_walk_force_equals_list_path(name):
+    """The fused walk-and-force pass (no lists in device memory) sums the same
+    sources in the same 32-record tiles as the list path: accelerations,
+    potentials and interaction counts agree bit for bit."""
+    import paper_0909_0541_gb300 as nb
+    ps, theta, n_crit, eps = CASES[name]()
+    g = gpu_run(ps.pos, ps.mass, theta=theta, n_crit=n_crit, eps=eps, lists=False)
+    dev = torch.device("cuda")
+    ctx = nb.NBody(ps.n)
+    ctx.build_tree(torch.from_numpy(ps.pos).to(dev), torch.from_numpy(ps.mass).to(dev))
+    acc = torch.zeros((ps.n, 3), dtype=torch.float32, device=dev)
+    pot = torch.zeros(ps.n, dtype=torch.float32, device=dev)
+    ctx.forces_fused(theta, n_crit, eps, acc, pot)
+    st = ctx.stats()
+    assert np.array_equal(acc.cpu().numpy(), g["acc"])
+    assert np.array_equal(pot.cpu().numpy(), g["pot"])
+    assert st["n_pp"] == g["stats"]["n_pp"] and st["n_pc"] == g["stats"]["n_pc"]
+    with pytest.raises(nb.NBError) as ei:   # no lists were left behind
+        ctx.forces(eps, acc)
+    assert ei.value.code == -6
+
+
+@pytest.mark.parametrize("precision", ["fp32_comp", "fp64acc"])
+def test_fused_precision_modes_equal_list_path(precision):
+    import paper_0909_0541_gb300 as nb
+    ps, theta, n_crit, eps = CASES["halomix20000"]()
+    g = gpu_run(ps.pos, ps.mass, theta=theta, n_crit=n_crit, eps=eps, precision=precision,
+                lists=False)
+    dev = torch.device("cuda")
+    ctx = nb.NBody(ps.n)
+    ctx.build_tree(torch.from_numpy(ps.pos).to(dev), torch.from_numpy(ps.mass).to(dev))
+    acc = torch.zeros((ps.n, 3), dtype=torch.float32, device=dev)
+    ctx.forces_fused(theta, n_crit, eps, acc, None, precision)
+    assert np.array_equal(acc.cpu().numpy(), g["acc"])
+
+
+def test_fused_leapfrog_steps_equal_list_steps():
+    """nb_set_fused: leapfrog steps through the fused pass give the same bits
+    as through lists, eager and captured in a CUDA graph."""
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(16384, nbsynth.BASE_SEED + 1)
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    out = []
+    for fused in (False, True):
+        P = torch.from_numpy(ps.pos).to(dev)
+        V = torch.from_numpy(ps.vel).to(dev)
+        M = torch.from_numpy(ps.mass).to(dev)
+        stream.wait_stream(torch.cuda.current_stream())
+        ctx = nb.NBody(ps.n, eps=1 / 64, theta=0.75, n_crit=64, stream=stream)
+        ctx.set_fused(fused)
+        with torch.cuda.stream(stream):
+            ctx.leapfrog_step(P, V, M, 1 / 128)
+            ctx.set_sync_checks(False)
+            ctx.graph_capture_leapfrog(P, V, M, 1 / 128, 3)
+            ctx.graph_launch()
+            ctx.leapfrog_step(P, V, M, 1 / 128)
+            stream.synchronize()
+            ctx.sync_status()
+        out.append((P.cpu().numpy(), V.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
