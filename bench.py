@@ -162,14 +162,20 @@ def force_traffic_record():
 
 
 def dist_init(args):
+    """Ranks from the launcher's environment.  Replicas only: the process
+    group carries the barrier and the scalar reductions of the timings, never
+    data of the path (NCCL on GPUs, gloo on CPU)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        backend = "nccl" if dist.is_nccl_available() else "gloo"
+        if torch.cuda.is_available() and dist.is_nccl_available():
+            torch.cuda.set_device(local)
+            backend = "nccl"
+        else:
+            backend = "gloo"
         dist.init_process_group(backend=backend)
     return ws, rank, local
 
@@ -180,24 +186,30 @@ def barrier(ws):
         dist.barrier()
 
 
-def allreduce_max(x, ws):
+def _allreduce(x, ws, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op))
     return float(t.item())
+
+
+def allreduce_max(x, ws):
+    return _allreduce(x, ws, "MAX")
 
 
 def allreduce_sum(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _allreduce(x, ws, "SUM")
+
+
+def job_rate(units, ms, ws):
+    """Whole-job rate: the units every rank processed over the slowest rank's
+    time (ms), and that time."""
+    ms_max = allreduce_max(ms, ws)
+    return allreduce_sum(float(units), ws) / (ms_max / 1e3), ms_max
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -355,9 +367,7 @@ def run_ours(args, ws, rank, local):
         st1 = ctx.stats()
     ms_total = e0.elapsed_time(e1)
     inter = (st1["n_pp_total"] - st0["n_pp_total"]) + (st1["n_pc_total"] - st0["n_pc_total"])
-    ms_max = allreduce_max(ms_total, ws)
-    inter_all = allreduce_sum(float(inter), ws)
-    value = inter_all / (ms_max / 1e3)
+    value, ms_max = job_rate(inter, ms_total, ws)
     ms_per_step = ms_max / args.steps
 
     # ---- end to end: the C-ABI step on pinned HOST buffers; the library does
