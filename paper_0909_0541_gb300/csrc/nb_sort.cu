@@ -237,12 +237,11 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     const int wbase = w * (RS_TILE / RS_WARPS);
     const unsigned lt = (1u << lane) - 1u;
     uint64_t key[RS_I];
-    uint32_t val[RS_I], rnk[RS_I];
+    uint32_t rnk[RS_I];
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
         const int e = wbase + r * NB_WARP + lane;
         key[r] = e < tn ? kin[tile0 + e] : 0ull;
-        val[r] = e < tn ? vin[tile0 + e] : 0u;
     }
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
@@ -330,6 +329,14 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     for (int ww = 0; ww < RS_WARPS; ww++) wpre += ww < w ? wtot[ww] : 0u;
     lstart[t] = wpre + x - run;
     __syncthreads();
+    // values are loaded only now (they need no ranking): fewer registers
+    // held through the ranking rounds
+    uint32_t val[RS_I];
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        const int e = wbase + r * NB_WARP + lane;
+        val[r] = e < tn ? vin[tile0 + e] : 0u;
+    }
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
         if (wbase + r * NB_WARP + lane < tn) {

@@ -1008,28 +1008,45 @@ __device__ __forceinline__ int32_t item_count(int32_t m, int iblock)
 }
 
 // group box over the members' FP32 positions, its FP32 centre, FP32
-// 1/theta, and the number of force work items of the group
+// 1/theta, and the number of force work items of the group; one warp per
+// group, the members strided over the lanes and the box reduced by shuffles
+// (min and max are exact, so the order does not matter)
 __global__ void __launch_bounds__(256)
 k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gcount,
               const float4 *__restrict__ p_hi, long long *__restrict__ cnt,
               float theta, const float *__restrict__ theta_g, float4 *__restrict__ gbox,
               int32_t *__restrict__ item_cnt, int iblock, int64_t n, unsigned *__restrict__ err)
 {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
-    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G;
-         g += gridDim.x * blockDim.x) {
+    const int32_t nw = gridDim.x * (blockDim.x >> 5);
+    for (int32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += nw) {
         const int32_t f = gfirst[g], m = gcount[g];
-        if (!nb_in(f >= 0 && m >= 1 && (int64_t)f + m <= n, cnt, err, SITE_GROUPS, g)) {
-            item_cnt[g] = 0;
+        if (!(f >= 0 && m >= 1 && (int64_t)f + m <= n)) {
+            if (lane == 0) {
+                nb_bad(cnt, err, SITE_GROUPS, g);
+                item_cnt[g] = 0;
+            }
             continue;
         }
-        float4 p = p_hi[f];
-        float lx = p.x, ly = p.y, lz = p.z, hx = p.x, hy = p.y, hz = p.z;
-        for (int32_t k = 1; k < m; k++) {
-            p = p_hi[f + k];
+        float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+        float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+        for (int32_t k = lane; k < m; k += NB_WARP) {
+            const float4 p = p_hi[f + k];
             lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
             hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = fminf(lx, __shfl_xor_sync(FULL, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(FULL, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(FULL, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(FULL, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(FULL, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(FULL, hz, o));
+        }
+        if (lane != 0) continue;
         const float th = theta_g ? theta_g[g] : theta;
         const float invth = __double2float_rn(__ddiv_rn(1.0, (double)th));
         const float cx = __double2float_rn(__dmul_rn(0.5, __dadd_rn((double)lx, (double)hx)));
@@ -1087,7 +1104,7 @@ void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
     k_group_scatter<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
         c->gflag, c->n_first, c->n_count, c->cnt, c->gnode, c->gfirst, c->gcount, c->n, c->err);
     nb_launched(c, "k_group_scatter");
-    k_group_boxes<<<nb_grid(c->max_n, 256, gcap), 256, 0, s>>>(
+    k_group_boxes<<<c->num_sms * 16, 256, 0, s>>>(
         c->gfirst, c->gcount, c->p_hi, c->cnt, theta, theta_g, c->gbox, c->item_cnt,
         c->item_rows * NB_WARP, c->n, c->err);
     nb_launched(c, "k_group_boxes");
