@@ -621,8 +621,8 @@ def run_batch(args, ws, rank, local):
     ctx = nb.NBody(n, eps=eps, theta=theta, n_crit=64, max_systems=len(systems),
                    sync_checks=True, stream=stream)
     with torch.cuda.stream(stream):
-        best, rows, table = ctx.autotune(P, M, eps, theta, n_crits=(32, 64, 128, 256, 512),
-                                         reps=2, offsets=O)
+        pick, table = ctx.autotune(P, M, eps, theta, n_crits=(32, 64, 128, 256, 512),
+                                   reps=2, offsets=O)
         ctx.leapfrog_step_batched(P, V, M, O, dt)      # sizes the lists, caches a(x)
         ctx.set_sync_checks(False)
         ctx.get_timing()                               # resets the launch counter
@@ -656,9 +656,11 @@ def run_batch(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch512", "n": n, "systems": len(systems), "theta": theta,
                    "eps": eps, "dt": dt, "graph_steps": nsteps,
-                   "autotuned": {"n_crit": best, "item_targets": 32 * rows},
+                   "autotuned": {"n_crit": pick["n_crit"], "item_targets": 32 * pick["rows"],
+                                 "j_tile": pick["tile"], "block": pick["block"]},
                    "l2": "inputs larger than L2"},
-        "autotune_ms": {f"{k[0]}/{32 * k[1]}": v for k, v in table.items()},
+        "autotune_ms": {f"n_crit {k[0]}, {32 * k[1]} targets, tile {k[2]}, block {k[3]}": v
+                        for k, v in table.items()},
         "interactions_per_step": inter / kdk,
         "particle_steps_per_s": n * kdk / (ms / 1e3),
         "gpu_launches": graph_kernels * args.steps,

@@ -219,16 +219,19 @@ int nb_graph_launch(nb_ctx *ctx);
 /* Autotuner: builds the tree of (pos_dev, mass_dev) -- a forest of n_systems
  * independent systems when offsets_dev (device, n_systems + 1 row offsets)
  * is given, as nb_build_tree_batched; one system when it is NULL -- then
- * times `reps` walk +
- * force passes for every n_crit of the list and both force work-item widths
- * (32 or 64 targets per warp) with CUDA events, keeps the fastest pair in
- * the context (cfg.n_crit and the item width used from then on) and returns
- * it; ms_host (nullable, 2 x ncand) receives the mean times (item width 32,
- * then 64, per candidate). */
+ * times `reps` walk + FP32 force passes with CUDA events for every n_crit of
+ * the list x force work-item width (32 or 64 targets per warp) x j-tile depth
+ * (32 or 64 list records staged per tile) x force block size (256 or 128
+ * threads), keeps the fastest combination in the context (cfg.n_crit and the
+ * FP32 force shape used from then on) and returns it in the best_* outputs
+ * (each nullable); ms_host (nullable, 8 x ncand) receives the mean times,
+ * index ((candidate x 2 + width index) x 2 + tile index) x 2 + block index,
+ * with the indices in the orders listed above. */
 int nb_autotune(nb_ctx *ctx, const double *pos_dev, const float *mass_dev,
                 const int64_t *offsets_dev, int64_t n_systems, int64_t n, float eps,
                 float theta, const int *n_crit_host, int ncand, int reps,
-                int *best_n_crit_host, int *best_rows_host, float *ms_host);
+                int *best_n_crit_host, int *best_rows_host, int *best_tile_host,
+                int *best_block_host, float *ms_host);
 
 /* FP64 direct sum of Eq. (gravity) for the targets listed in targets_dev
  * (nt indices into 0..n-1; NULL = all n), used as the accuracy judge.

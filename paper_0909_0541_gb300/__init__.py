@@ -105,7 +105,7 @@ def _load():
     L.nb_graph_capture_leapfrog.argtypes = [vp, vp, vp, vp, vp, i64, i64, C.c_double, i32]
     L.nb_graph_launch.argtypes = [vp]
     L.nb_autotune.argtypes = [vp, vp, vp, vp, i64, i64, C.c_float, C.c_float, vp, i32, i32, vp, vp,
-                              vp]
+                              vp, vp, vp]
     L.nb_leapfrog_step_batched.argtypes = [vp, vp, vp, vp, vp, i64, i64, C.c_double]
     L.nb_copy_group_lengths.argtypes = [vp, vp, i64]
     L.nb_walk_groups_learned.argtypes = [vp, i32, vp, C.c_float, vp]
@@ -250,22 +250,33 @@ class NBody:
 
     def autotune(self, pos, mass, eps, theta, n_crits=(32, 64, 128, 256, 512), reps=3,
                  offsets=None):
-        """(best n_crit, best item rows, {(n_crit, rows): ms}); offsets (int64
-        CUDA tensor of n_systems + 1 row offsets) tunes a batch of systems."""
+        """Times walk + FP32 force over n_crit x item rows (1, 2: 32 or 64
+        targets per warp) x j-tile depth (32, 64) x block size (256, 128) and
+        keeps the fastest.  Returns ({"n_crit", "rows", "tile", "block"},
+        {(n_crit, rows, tile, block): ms}); offsets (int64 CUDA tensor of
+        n_systems + 1 row offsets) tunes a batch of systems."""
         import torch
         cand = np.asarray(n_crits, np.int32)
-        ms = np.zeros(2 * len(cand), np.float32)
-        bn, br = C.c_int(0), C.c_int(0)
+        ms = np.zeros(8 * len(cand), np.float32)
+        bn, br, bt, bb = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
         nsys = 1 if offsets is None else int(offsets.shape[0]) - 1
         _check(_lib.nb_autotune(self._h, _dptr(pos, torch.float64, 3, "pos"),
                                 _dptr(mass, torch.float32, None, "mass"),
                                 _dptr(offsets, torch.int64, None, "offsets"), nsys,
                                 int(pos.shape[0]),
                                 float(eps), float(theta), _hptr(cand), len(cand), int(reps),
-                                C.byref(bn), C.byref(br), _hptr(ms)), "nb_autotune")
-        table = {(int(c), r + 1): float(ms[2 * k + r]) for k, c in enumerate(cand) for r in range(2)}
+                                C.byref(bn), C.byref(br), C.byref(bt), C.byref(bb), _hptr(ms)),
+               "nb_autotune")
+        table = {}
+        for k, c in enumerate(cand):
+            for r in range(2):
+                for ti, tile in enumerate((32, 64)):
+                    for bi, block in enumerate((256, 128)):
+                        table[(int(c), r + 1, tile, block)] = float(
+                            ms[((k * 2 + r) * 2 + ti) * 2 + bi])
         self.cfg.n_crit = bn.value
-        return bn.value, br.value, table
+        return {"n_crit": bn.value, "rows": br.value, "tile": bt.value,
+                "block": bb.value}, table
 
     def walk_groups(self, theta, n_crit, theta_per_group=None):
         import torch

@@ -816,7 +816,8 @@ int nb_graph_launch(nb_ctx *c)
 
 int nb_autotune(nb_ctx *c, const double *pos, const float *mass, const int64_t *offsets,
                 int64_t nsys, int64_t n, float eps, float theta, const int *n_crit, int ncand,
-                int reps, int *best_n_crit, int *best_rows, float *ms_out)
+                int reps, int *best_n_crit, int *best_rows, int *best_tile, int *best_block,
+                float *ms_out)
 {
     if (!c || !pos || !mass || !n_crit || ncand < 1 || reps < 1 || n < 1) return NB_ERR_INVALID_ARG;
     int rc = offsets ? nb_build_tree_batched(c, pos, mass, offsets, nsys, n)
@@ -826,42 +827,60 @@ int nb_autotune(nb_ctx *c, const double *pos, const float *mass, const int64_t *
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int sync = c->sync_checks, rows0 = c->item_rows;
+    const int tile0 = c->force_tile, block0 = c->force_block;
+    const int tiles[2] = {32, 64}, blocks[2] = {256, 128};
     float best = INFINITY;
-    int bn = n_crit[0], br = rows0;
+    int bn = n_crit[0], br = rows0, bt = 32, bb = 256;
     for (int k = 0; k < ncand && rc == NB_OK; k++)
-        for (int rows = 1; rows <= 2 && rc == NB_OK; rows++) {
-            c->item_rows = rows;
-            c->sync_checks = 1;
-            rc = nb_walk_groups(c, theta, n_crit[k], nullptr);   // sizes the lists
-            if (rc) break;
-            rc = nb_forces(c, eps, c->acc_cache, nullptr, NB_FP32);
-            if (rc) break;
-            c->sync_checks = 0;
-            cudaEventRecord(e0, c->stream);
-            for (int r = 0; r < reps && rc == NB_OK; r++) {
-                rc = nb_walk_groups(c, theta, n_crit[k], nullptr);
-                if (!rc) rc = nb_forces(c, eps, c->acc_cache, nullptr, NB_FP32);
-            }
-            cudaEventRecord(e1, c->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = NB_ERR_CUDA;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= reps;
-            if (ms_out) ms_out[2 * k + rows - 1] = ms;
-            if (ms < best) { best = ms; bn = n_crit[k]; br = rows; }
-        }
+        for (int rows = 1; rows <= 2 && rc == NB_OK; rows++)
+            for (int ti = 0; ti < 2 && rc == NB_OK; ti++)
+                for (int bi = 0; bi < 2 && rc == NB_OK; bi++) {
+                    c->item_rows = rows;
+                    c->force_tile = tiles[ti];
+                    c->force_block = blocks[bi];
+                    c->sync_checks = 1;
+                    rc = nb_walk_groups(c, theta, n_crit[k], nullptr);   // sizes the lists
+                    if (rc) break;
+                    rc = nb_forces(c, eps, c->acc_cache, nullptr, NB_FP32);
+                    if (rc) break;
+                    c->sync_checks = 0;
+                    cudaEventRecord(e0, c->stream);
+                    for (int r = 0; r < reps && rc == NB_OK; r++) {
+                        rc = nb_walk_groups(c, theta, n_crit[k], nullptr);
+                        if (!rc) rc = nb_forces(c, eps, c->acc_cache, nullptr, NB_FP32);
+                    }
+                    cudaEventRecord(e1, c->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = NB_ERR_CUDA;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= reps;
+                    if (ms_out) ms_out[((k * 2 + rows - 1) * 2 + ti) * 2 + bi] = ms;
+                    if (ms < best) {
+                        best = ms;
+                        bn = n_crit[k];
+                        br = rows;
+                        bt = tiles[ti];
+                        bb = blocks[bi];
+                    }
+                }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->sync_checks = sync;
     if (rc) {
         c->item_rows = rows0;
+        c->force_tile = tile0;
+        c->force_block = block0;
         return rc;
     }
     c->item_rows = br;
+    c->force_tile = bt;
+    c->force_block = bb;
     c->cfg.n_crit = bn;
     c->acc_valid = 0;
     if (best_n_crit) *best_n_crit = bn;
     if (best_rows) *best_rows = br;
+    if (best_tile) *best_tile = bt;
+    if (best_block) *best_block = bb;
     return sync_read(c);
 }
 

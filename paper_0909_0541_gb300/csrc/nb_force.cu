@@ -30,11 +30,10 @@
 #include "nb_force.cuh"
 
 #define F_T 256
-#define F_WARPS (F_T / NB_WARP)
 
 // R targets per lane (R = 2 only with S = 1); S source streams: lane l is
 // target row l % W of stream l / W, W = 32 / S
-template <int MODE, bool GUARD, int R, int S>
+template <int MODE, bool GUARD, int R, int S, int TILE>
 __device__ __forceinline__ void force_item(
     int32_t g, int32_t i0, float4 *tile, const int32_t *__restrict__ gfirst,
     const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
@@ -77,10 +76,10 @@ __device__ __forceinline__ void force_item(
         A[r].init();
         T[r].init();
     }
-    // (1) the list: sources outside the group, F_TILE records per tile
-    constexpr int TK = F_TILE / NB_WARP;   // records each lane stages per tile
+    // (1) the list: sources outside the group, TILE records per tile
+    constexpr int TK = TILE / NB_WARP;   // records each lane stages per tile
     const float4 *__restrict__ src = list_xm + (int64_t)g * cap;
-    for (int32_t j0 = 0; j0 < len; j0 += F_TILE) {
+    for (int32_t j0 = 0; j0 < len; j0 += TILE) {
 #pragma unroll
         for (int k = 0; k < TK; k++) {
             const int32_t jj = j0 + k * NB_WARP + lane;
@@ -207,8 +206,10 @@ k_item_order(const int32_t *__restrict__ items, const int32_t *__restrict__ gcou
     }
 }
 
-template <int MODE, bool GUARD>
-__global__ void __launch_bounds__(F_T, MODE == MODE_COMP ? 4 : 5)
+// TILE: list records staged per tile (the j-tile depth); BT: threads per
+// block.  Both are chosen by the autotuner for the FP32 mode.
+template <int MODE, bool GUARD, int TILE, int BT>
+__global__ void __launch_bounds__(BT, (MODE == MODE_COMP ? 4 : 5) * F_T / BT)
 k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
         const int32_t *__restrict__ gfirst,
         const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
@@ -218,7 +219,7 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
         long long *__restrict__ cnt, float eps2, float *__restrict__ acc, float *__restrict__ pot,
         unsigned *__restrict__ err, int64_t max_items)
 {
-    __shared__ float4 tiles[F_WARPS][F_TILE];
+    __shared__ float4 tiles[BT / NB_WARP][TILE];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t nitems = (int32_t)cnt[CNT_ITEMS];
@@ -244,8 +245,8 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
             continue;
         }
 #define NB_FORCE_ITEM(R, S)                                                                   \
-    force_item<MODE, GUARD, R, S>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo, perm, \
-                                  list_xm, cap, alloc, n, eps2, acc, pot, cnt, err)
+    force_item<MODE, GUARD, R, S, TILE>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo, \
+                                        perm, list_xm, cap, alloc, n, eps2, acc, pot, cnt, err)
         if (word & ITEM_R2) {
             NB_FORCE_ITEM(2, 1);
         } else {
@@ -262,19 +263,37 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
     }
 }
 
-template <int MODE, bool GUARD>
-static void launch_force(nb_ctx *c, float eps2, float *acc, float *pot)
+template <int MODE, bool GUARD, int TILE, int BT>
+static void launch_force_t(nb_ctx *c, float eps2, float *acc, float *pot)
 {
     static int blocks = 0;
     if (blocks == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_force<MODE, GUARD>, F_T, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_force<MODE, GUARD, TILE, BT>, BT,
+                                                      0);
         if (blocks < 1) blocks = 1;
     }
-    k_force<MODE, GUARD><<<c->num_sms * blocks, F_T, 0, c->stream>>>(
+    k_force<MODE, GUARD, TILE, BT><<<c->num_sms * blocks, BT, 0, c->stream>>>(
         c->items, c->item_order, c->gfirst, c->gcount, c->glen, c->gbox, c->p_hi, c->p_lo, c->perm,
         c->list_xm, c->list_cap, c->list_alloc, c->n, c->cnt, eps2, acc, pot, c->err,
         c->max_items);
     nb_launched(c, "k_force");
+}
+
+// FP32: the context's j-tile depth (32 or 64) and block size (256 or 128);
+// the compensated and FP64-accumulated modes use 32 and 256
+template <int MODE, bool GUARD>
+static void launch_force(nb_ctx *c, float eps2, float *acc, float *pot)
+{
+    if constexpr (MODE == MODE_FP32) {
+        switch ((c->force_tile == 64 ? 2 : 0) + (c->force_block == 128 ? 1 : 0)) {
+        case 0: launch_force_t<MODE, GUARD, 32, 256>(c, eps2, acc, pot); break;
+        case 1: launch_force_t<MODE, GUARD, 32, 128>(c, eps2, acc, pot); break;
+        case 2: launch_force_t<MODE, GUARD, 64, 256>(c, eps2, acc, pot); break;
+        default: launch_force_t<MODE, GUARD, 64, 128>(c, eps2, acc, pot); break;
+        }
+    } else {
+        launch_force_t<MODE, GUARD, F_TILE, F_T>(c, eps2, acc, pot);
+    }
 }
 
 void nb_launch_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision)

@@ -185,6 +185,8 @@ struct nb_ctx {
     float4 *gbox;     // 3 per group
     int32_t *items;   // force work items: (group, first member | one-warp-row flag)
     int item_rows;    // targets per item: 32 x item_rows (1 or 2)
+    int force_tile;   // FP32 force: list records per staged tile (32 or 64; 0 = 32)
+    int force_block;  // FP32 force: threads per block (256 or 128; 0 = 256)
     int32_t *item_cnt;
     int64_t max_items;
     int32_t *item_order;  // queue position -> item, costliest first (max_items)

@@ -122,14 +122,30 @@ def test_autotune_picks_a_candidate():
     P = torch.from_numpy(ps.pos).to(dev)
     M = torch.from_numpy(ps.mass).to(dev)
     ctx = nb.NBody(ps.n, eps=1 / 64, theta=0.7)
-    best, rows, table = ctx.autotune(P, M, 1 / 64, 0.7, n_crits=(16, 64, 256), reps=2)
-    assert best in (16, 64, 256) and rows in (1, 2)
-    assert table[(best, rows)] == min(table.values())
+    pick, table = ctx.autotune(P, M, 1 / 64, 0.7, n_crits=(16, 64, 256), reps=2)
+    best = pick["n_crit"]
+    assert best in (16, 64, 256) and pick["rows"] in (1, 2)
+    assert pick["tile"] in (32, 64) and pick["block"] in (256, 128)
+    assert len(table) == 3 * 8
+    assert table[(best, pick["rows"], pick["tile"], pick["block"])] == min(table.values())
+    # the chosen force shape gives the same accelerations as the default one
     ctx.build_tree(P, M)
     ctx.walk_groups(0.7, best)
     acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
     ctx.forces(1 / 64, acc)
     assert torch.isfinite(acc).all()
+    ref = nb.NBody(ps.n, eps=1 / 64, theta=0.7)
+    ref.build_tree(P, M)
+    ref.walk_groups(0.7, best)
+    acc0 = torch.empty_like(acc)
+    ref.forces(1 / 64, acc0)
+    # 64-target items with 32-record tiles sum in the default order (bit-equal);
+    # other shapes split the sources among streams differently
+    if pick["rows"] == 2 and pick["tile"] == 32:
+        assert torch.equal(acc, acc0)
+    else:
+        scale = acc0.norm(dim=1).max().item()
+        assert (acc - acc0).norm(dim=1).max().item() <= 1e-5 * scale
 
 
 def test_autotune_a_forest(oracle_lib):
@@ -145,9 +161,10 @@ def test_autotune_a_forest(oracle_lib):
     M = torch.from_numpy(mass).to(dev)
     O = torch.from_numpy(off).to(dev)
     ctx = nb.NBody(len(pos), eps=eps, theta=theta, n_crit=64, max_systems=len(systems))
-    best, rows, table = ctx.autotune(P, M, eps, theta, n_crits=(16, 64, 256), reps=2, offsets=O)
-    assert best in (16, 64, 256) and rows in (1, 2)
-    assert table[(best, rows)] == min(table.values())
+    pick, table = ctx.autotune(P, M, eps, theta, n_crits=(16, 64, 256), reps=2, offsets=O)
+    best = pick["n_crit"]
+    assert best in (16, 64, 256) and pick["rows"] in (1, 2)
+    assert table[(best, pick["rows"], pick["tile"], pick["block"])] == min(table.values())
     ctx.leapfrog_step_batched(P, V, M, O, dt)
     for k, ps in enumerate(systems):
         xo, vo, ao = oracle_lib.leapfrog(ps.pos, ps.vel, ps.mass, eps, dt, 1, use_tree=True,
