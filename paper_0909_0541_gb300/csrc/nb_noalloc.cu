@@ -24,7 +24,7 @@
 #include "nb_internal.cuh"
 
 #define NA_MAX_N ((int64_t)NB_NOALLOC_MAX_N)
-#define NA_TILES ((NA_MAX_N + 4095) / 4096)
+#define NA_TILES ((NA_MAX_N + NB_RS_TILE - 1) / NB_RS_TILE)
 #define NA_HIST (256 * NA_TILES + 1)
 #define NA_BSUM ((NA_HIST + 2047) / 2048 + 2)
 #define NA_BBOX_BLOCKS 512

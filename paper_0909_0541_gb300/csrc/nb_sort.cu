@@ -2,7 +2,7 @@
 // (63-bit Morton key, particle index) pairs that puts particles in Morton
 // order (Sec. "Test and Optimization": depth-first leaf order of the tree).
 //
-// Radix sort: 8 passes of 8-bit digits over tiles of 4096 keys.  The
+// Radix sort: 8 passes of 8-bit digits over tiles of NB_RS_TILE keys.  The
 // context's sort is single-pass per digit (Onesweep, see k_rs_scatter): one
 // histogram of all eight digits, then one scatter launch per pass whose
 // tiles find their offsets by a bounded decoupled look-back.  The sort on
@@ -149,8 +149,8 @@ void nb_exclusive_scan(nb_ctx *c, const int32_t *in, int32_t *out, int64_t n_max
 
 // ------------------------------------------------------------ radix sort
 #define RS_T 256
-#define RS_I 16
-#define RS_TILE (RS_T * RS_I)
+#define RS_I (NB_RS_TILE / RS_T)
+#define RS_TILE NB_RS_TILE
 #define RS_WARPS (RS_T / NB_WARP)
 
 __global__ void __launch_bounds__(RS_T)
@@ -453,7 +453,7 @@ void nb_exclusive_scan_raw(const int32_t *in, int32_t *out, int64_t n_max, int32
 }
 
 // keys/idx hold the input and, after the 8 passes, the sorted output;
-// hist needs 256 * ceil(n / 4096) + 1 entries, bsum the scan's tile sums.
+// hist needs 256 * ceil(n / NB_RS_TILE) + 1 entries, bsum the scan's tile sums.
 void nb_radix_sort_raw(uint64_t *keys, uint64_t *keys_alt, uint32_t *idx, uint32_t *idx_alt,
                        uint32_t *hist, int32_t *bsum, int64_t n, cudaStream_t s)
 {

@@ -334,8 +334,8 @@ k_parents(const int4 *__restrict__ node_c, long long *__restrict__ cnt,
 // histograms, one scan of the depth-major table, then a stable scatter with
 // warp match/rank (the same scheme as the radix sort's scatter).
 #define DS_T 256
-#define DS_I 16
-#define DS_TILE (DS_T * DS_I)
+#define DS_I (NB_DS_TILE / DS_T)
+#define DS_TILE NB_DS_TILE
 
 __global__ void __launch_bounds__(DS_T)
 k_depth_hist(const int8_t *__restrict__ depth, const long long *__restrict__ cnt,
