@@ -91,12 +91,19 @@ __device__ __forceinline__ void visit_node(
         if (lane >= o) incl += y;
     }
     const int32_t start = nb + incl - nch;
-    if (open)
-        for (int32_t k = 0; k < nch; k++) {
-            const int32_t pos = start + k;
-            if (pos < WQ_SMEM) qout_s[pos] = fc + k;
-            else if (pos < wq_cap) qout[pos] = fc + k;
+    if (open) {
+        if (start + nch <= WQ_SMEM) {   // the common case: all in shared memory
+#pragma unroll
+            for (int k = 0; k < 8; k++)   // a cell has at most 8 children
+                if (k < nch) qout_s[start + k] = fc + k;
+        } else {
+            for (int32_t k = 0; k < nch; k++) {
+                const int32_t pos = start + k;
+                if (pos < WQ_SMEM) qout_s[pos] = fc + k;
+                else if (pos < wq_cap) qout[pos] = fc + k;
+            }
         }
+    }
     nb += __shfl_sync(FULL, incl, 31);
 }
 
