@@ -333,3 +333,33 @@ def test_fused_leapfrog_steps_equal_list_steps():
             ctx.sync_status()
         out.append((P.cpu().numpy(), V.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_wide_frontier_grows_the_walk_queues(oracle_lib):
+    """theta = 0 opens every cell, so on a 40,000-particle cube a frontier
+    holds all 32,768 nodes of depth 5: more than the 4096-entry queues a
+    context of this size starts with.  The walk reports the overflow, the
+    queues grow and the walk is redone; the list path and the fused pass
+    then both reproduce the direct sum."""
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.uniform_cube(40000, 17)
+    dev = torch.device("cuda")
+    P = torch.from_numpy(ps.pos).to(dev)
+    M = torch.from_numpy(ps.mass).to(dev)
+    eps = 1e-3
+    ctx = nb.NBody(ps.n)
+    ctx.build_tree(P, M)
+    ctx.walk_groups(0.0, 4096)
+    st = ctx.stats()
+    assert st["list_entries"] == sum(ps.n - c for c in ctx.copy_groups()["gcount"])
+    acc = torch.zeros((ps.n, 3), dtype=torch.float32, device=dev)
+    ctx.forces(eps, acc)
+    fresh = nb.NBody(ps.n)   # the fused pass grows its own context's queues
+    fresh.build_tree(P, M)
+    accf = torch.zeros_like(acc)
+    fresh.forces_fused(0.0, 4096, eps, accf)
+    assert torch.equal(acc, accf)
+    tg = np.random.default_rng(3).choice(ps.n, 400, replace=False)
+    ad, _, am = oracle_lib.direct(ps.pos, ps.mass, eps, tg, with_amag=True)
+    d = np.linalg.norm(acc.cpu().numpy()[tg].astype(np.float64) - ad, axis=1)
+    assert np.all(d <= 1e-5 * am)
