@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--judge-targets", type=int, default=8192)
     ap.add_argument("--train-groups", type=int, default=6000,
                     help="learned4.19m: groups labelled for training")
+    ap.add_argument("--learned-form", default="tree", choices=["tree", "probe"],
+                    help="learned4.19m: tree-only features and labels from predicted "
+                         "curves (tree), or probe-walk features and labels from the "
+                         "measured curves (probe)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -532,8 +536,27 @@ def run_learned(args, ws, rank, local):
     tpos = torch.from_numpy(tr.pos).to(dev)
     tmass = torch.from_numpy(tr.mass).to(dev)
     tctx = nb.NBody(tr.n, eps=eps, n_crit=n_crit)
+    mode = 1 if args.learned_form == "tree" else 0
+    # the walk's time per list entry in units of the force's time per
+    # interaction, measured on the training draw at theta 0.6: the cost of a
+    # group's theta counts both
+    tctx.build_tree(tpos, tmass)
+    tacc0 = torch.empty((tr.n, 3), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        tctx.set_timing(True)
+        tctx.get_timing()
+        tctx.walk_groups(0.6, n_crit)
+        tctx.forces(eps, tacc0)
+        tm = tctx.get_timing()
+        tctx.set_timing(False)
+    st = tctx.stats()
+    walk_weight = ((tm["walk"][0] / max(st["list_entries"], 1)) /
+                   (tm["force"][0] / max(st["n_pp"] + st["n_pc"], 1))) if mode == 1 else 0.0
+    del tacc0
     X, y, info = learn.make_dataset(tpos, tmass, eps, n_crit, args.train_groups, seed=1,
-                                    ctx=tctx)
+                                    ctx=tctx, feature_mode=mode,
+                                    label_rule="predicted" if mode == 1 else "measured",
+                                    walk_weight=walk_weight)
     params, hist = learn.train(X, y, epochs=150, batch=256, lr=2e-3)
     g = torch.Generator().manual_seed(98)
     ttg = torch.randperm(tr.n, generator=g)[: args.judge_targets].to(dev)
@@ -547,6 +570,7 @@ def run_learned(args, ws, rank, local):
     pos = torch.from_numpy(ps.pos).to(dev)
     mass = torch.from_numpy(ps.mass).to(dev)
     ctx = nb.NBody(ps.n, eps=eps, n_crit=n_crit)
+    ctx.set_feature_mode(mode)
     ctx.build_tree(pos, mass)
     g = torch.Generator().manual_seed(99)
     tg = torch.randperm(ps.n, generator=g)[: args.judge_targets].to(dev)
@@ -558,12 +582,25 @@ def run_learned(args, ws, rank, local):
         inter, _ = learn.step_cost(ctx, n_crit, eps, acc, theta=theta, params=prm)
         err = learn.median_error(acc, ref, tg)
         ctx.set_sync_checks(False)           # device time only in the timed repetitions
-        ms = [learn.step_cost(ctx, n_crit, eps, acc, theta=theta, params=prm)[1]
-              for _ in range(reps)]
+        ms, wk, fo = [], [], []
+        for _ in range(reps):
+            ctx.set_timing(True)
+            ctx.get_timing()
+            if prm is None:
+                ctx.walk_groups(theta, n_crit)
+            else:
+                ctx.walk_groups_learned(n_crit, prm, 0.6)
+            ctx.forces(eps, acc)
+            tm = ctx.get_timing()
+            ctx.set_timing(False)
+            wk.append(tm["walk"][0])
+            fo.append(tm["force"][0])
+            ms.append(tm["walk"][0] + tm["force"][0])
         ctx.sync_status()
         ctx.set_sync_checks(True)
         ms = statistics.median(ms)
         return {"interactions": int(inter), "median_rel_err": err, "walk_force_ms": ms,
+                "walk_ms": statistics.median(wk), "force_ms": statistics.median(fo),
                 "force_evals_per_s": inter / (ms / 1e3)}
 
     learned = measure(prm=params)
@@ -580,7 +617,11 @@ def run_learned(args, ws, rank, local):
                    "train_set": "halo mix 4,194,304 (3000 halos, another seed)",
                    "train_groups": int(X.shape[0]),
                    "train_samples": int(X.shape[0]) * len(learn.THETA_GRID),
-                   "error_budget": learn.BUDGET, "step": "walk + force (learned probe included)"},
+                   "error_budget": learn.BUDGET,
+                   "learned_form": ("tree-only features, labels from predicted curves"
+                                    if mode == 1 else
+                                    "probe-walk features, labels from measured curves"),
+                   "step": "walk + force (feature pass and network included)"},
         "learned": learned,
         "fixed_theta_matched": dict(fixed, theta=th_star),
         "fixed_theta_0.6": fixed06,
@@ -588,6 +629,7 @@ def run_learned(args, ws, rank, local):
         "time_gain_vs_matched": 1.0 - learned["walk_force_ms"] / fixed["walk_force_ms"],
         "training": {"labelled_median_error": info["labelled_error"], "lambda": info["lam"],
                      "calibration_logit_shift": shift,
+                     "walk_weight_interactions_per_list_entry": walk_weight,
                      "loss_first_last": [float(hist[0]), float(hist[-1])],
                      "seconds_incl_labels": t_train},
         "judge": {"targets": int(args.judge_targets), "kind": "nb_direct_sum (FP64)"},

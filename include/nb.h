@@ -304,6 +304,10 @@ int nb_copy_lists(nb_ctx *ctx, int64_t *offsets_host, int32_t *entries_host,
  * (nullable, synchronises) receives G.  Lists are invalidated. */
 int nb_group_features(nb_ctx *ctx, int n_crit, float *feat_dev, int64_t cap_rows,
                       int64_t *n_groups_host);
+/* Feature mode of nb_group_features and nb_walk_groups_learned: 0 (the
+ * default) the probe-walk features above; 1 tree-only features, which need no
+ * walk: features 0-5 and 11 as above (the same formulas), 6-10 zero. */
+int nb_set_feature_mode(nb_ctx *ctx, int mode);
 /* Walk with a per-group theta from the network (params_dev, layout below)
  * evaluated on the probe features; a non-finite output becomes
  * theta_fallback.  theta_out_dev (nullable, n floats) receives the group

@@ -37,7 +37,7 @@ EXPORTED = [
     "nb_walk_groups_learned", "nb_group_errors", "nb_theta_labels",
     "nb_copy_group_lengths", "nb_build_tree_batched", "nb_leapfrog_step_batched",
     "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune", "nb_selftest_wait",
-    "nb_leapfrog_step_host", "nb_forces_fused", "nb_set_fused",
+    "nb_leapfrog_step_host", "nb_forces_fused", "nb_set_fused", "nb_set_feature_mode",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -85,6 +85,7 @@ def _load():
     L.nb_forces.argtypes = [vp, C.c_float, vp, vp, i32]
     L.nb_forces_fused.argtypes = [vp, C.c_float, i32, C.c_float, vp, vp, i32]
     L.nb_set_fused.argtypes = [vp, i32]
+    L.nb_set_feature_mode.argtypes = [vp, i32]
     L.nb_leapfrog_step.argtypes = [vp, vp, vp, vp, i64, C.c_double]
     L.nb_leapfrog_reset.argtypes = [vp]
     L.nb_leapfrog_step_host.argtypes = [vp, vp, vp, vp, i64, C.c_double]
@@ -290,6 +291,10 @@ class NBody:
         _check(_lib.nb_forces(self._h, float(eps), _dptr(acc, torch.float32, 3, "acc"),
                               _dptr(pot, torch.float32, None, "pot"),
                               PRECISION.get(precision, precision)), "nb_forces")
+
+    def set_feature_mode(self, mode: int):
+        """Learned-theta features: 0 from the probe walk, 1 tree-only (no walk)."""
+        _check(_lib.nb_set_feature_mode(self._h, int(mode)), "nb_set_feature_mode")
 
     def set_fused(self, on: bool):
         """Leapfrog force passes without interaction lists (nb_set_fused)."""

@@ -458,7 +458,9 @@ int nb_build_tree_batched(nb_ctx *c, const double *pos, const float *mass,
     return finish(c);
 }
 
-int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
+// the walk over groups of n_crit; `formed`: the groups (and their items)
+// are already in place and only each box's 1/theta is set from theta_g
+static int walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g, bool formed)
 {
     if (!c) return NB_ERR_INVALID_ARG;
     if (!c->has_tree) return NB_ERR_STATE;
@@ -471,7 +473,8 @@ int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
         return NB_OK;
     }
     const int tk = phase_begin(c);
-    nb_launch_groups(c, theta, n_crit, theta_g);
+    if (formed) nb_launch_group_theta(c, theta_g);
+    else nb_launch_groups(c, theta, n_crit, theta_g);
     c->has_groups = 1;
     if (c->sync_checks) {
         int rc = read_counters(c);
@@ -528,9 +531,18 @@ int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
 
 // the probe walk over groups formed with theta = NB_PROBE_THETA; in the
 // synchronising mode a frontier that outgrows the walk queues grows them
+int nb_walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
+{
+    return walk_groups(c, theta, n_crit, theta_g, false);
+}
+
 static int probe(nb_ctx *c, int n_crit)
 {
     nb_launch_groups(c, NB_PROBE_THETA, n_crit, nullptr);
+    if (c->feature_mode == 1) {   // tree-only features: no walk
+        nb_launch_features_tree(c, c->gfeat);
+        return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+    }
     for (int attempt = 0; attempt < 4; attempt++) {
         nb_launch_probe(c, c->gfeat);
         if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
@@ -590,7 +602,8 @@ int nb_walk_groups_learned(nb_ctx *c, int n_crit, const float *params, float fal
         CK(cudaMemcpyAsync(theta_out, c->gtheta, sizeof(float) * c->n, cudaMemcpyDeviceToDevice,
                            c->stream));
     }
-    return nb_walk_groups(c, fallback, n_crit, c->gtheta);
+    // the feature pass formed these groups: only their 1/theta changes
+    return walk_groups(c, fallback, n_crit, c->gtheta, true);
 }
 
 int nb_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision)
@@ -674,6 +687,13 @@ static int force_pass(nb_ctx *c, const double *pos, const float *mass, int64_t n
     rc = nb_walk_groups(c, c->cfg.theta, c->cfg.n_crit, nullptr);
     if (rc) return rc;
     return nb_forces(c, c->cfg.eps, c->acc_cache, c->pot_cache, c->cfg.precision);
+}
+
+int nb_set_feature_mode(nb_ctx *c, int mode)
+{
+    if (!c || mode < 0 || mode > 1) return NB_ERR_INVALID_ARG;
+    c->feature_mode = mode;
+    return NB_OK;
 }
 
 int nb_set_fused(nb_ctx *c, int on)

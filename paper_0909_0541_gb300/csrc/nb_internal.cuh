@@ -229,6 +229,7 @@ struct nb_ctx {
     // timing and launch accounting
     int timing;
     int fused;               // leapfrog force passes use the fused walk and force
+    int feature_mode;        // learned theta: 0 probe-walk features, 1 tree-only features
     int ev_used;
     cudaEvent_t *ev;         // NB_EV_POOL pairs
     int *ev_phase;
@@ -284,6 +285,8 @@ int nb_launch_direct(const double *pos, const float *mass, int64_t n, double eps
 void nb_launch_kick(nb_ctx *c, double *vel, const float *acc, int64_t n, double h);
 void nb_launch_wait_probe(nb_ctx *c, unsigned limit);
 void nb_launch_fused(nb_ctx *c, float eps, float *acc, float *pot, int precision);
+void nb_launch_features_tree(nb_ctx *c, float *feat);
+void nb_launch_group_theta(nb_ctx *c, const float *theta_g);
 void nb_launch_drift(nb_ctx *c, double *pos, const double *vel, int64_t n, double dt);
 
 __device__ __forceinline__ long long nb_atomic_add(long long *p, long long v)

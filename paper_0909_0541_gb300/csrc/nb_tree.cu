@@ -1092,6 +1092,24 @@ k_items(const int32_t *__restrict__ item_off, const int32_t *__restrict__ gcount
     }
 }
 
+// 1/theta of every formed group's box from a per-group theta (the same
+// rounding as k_group_boxes)
+__global__ void __launch_bounds__(256)
+k_group_theta(const float *__restrict__ theta_g, const long long *__restrict__ cnt,
+              float4 *__restrict__ gbox)
+{
+    const int32_t G = (int32_t)cnt[CNT_GROUPS];
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        gbox[3 * (int64_t)g + 2].w = __double2float_rn(__ddiv_rn(1.0, (double)theta_g[g]));
+}
+
+void nb_launch_group_theta(nb_ctx *c, const float *theta_g)
+{
+    k_group_theta<<<nb_grid(c->max_n, 256, c->num_sms * 8), 256, 0, c->stream>>>(theta_g, c->cnt,
+                                                                                c->gbox);
+    nb_launched(c, "k_group_theta");
+}
+
 void nb_launch_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g)
 {
     cudaStream_t s = c->stream;

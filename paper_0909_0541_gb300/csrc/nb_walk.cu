@@ -233,6 +233,54 @@ k_walk(const nb_wrec *__restrict__ wrec,
     }
 }
 
+// Tree-only features of every group: the probe's features that need no
+// walk (0-5 and 11, the same formulas), the walk-based ones (6-10) zero.
+// One thread per group.
+__global__ void __launch_bounds__(256)
+k_group_features_tree(const int32_t *__restrict__ gnode, const int32_t *__restrict__ gfirst,
+                      const int32_t *__restrict__ gcount, const float4 *__restrict__ gbox,
+                      const double *__restrict__ roots, const int8_t *__restrict__ n_depth,
+                      const int32_t *__restrict__ sys_sorted, long long *__restrict__ cnt,
+                      float *__restrict__ feat, int64_t n, unsigned *__restrict__ err)
+{
+    const int32_t G = (int32_t)cnt[CNT_GROUPS];
+    const int32_t total = (int32_t)cnt[CNT_NODES];
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        float *fo = feat + (int64_t)g * 16;
+        const int32_t f = gfirst[g], gpid = gnode[g];
+        if (!nb_in(f >= 0 && f < n && gpid >= 0 && gpid < total, cnt, err, SITE_GROUPS, g)) {
+            for (int k = 0; k < 16; k++) fo[k] = 0.0f;
+            continue;
+        }
+        const int32_t gsys = sys_sorted ? sys_sorted[f] : 0;
+        const double *root = roots + 8 * (int64_t)gsys;
+        const float L = (float)root[3];
+        const float ng = (float)gcount[g];
+        const float4 blo = gbox[3 * (int64_t)g], bhi = gbox[3 * (int64_t)g + 1],
+                     bc = gbox[3 * (int64_t)g + 2];
+        const float sx = (bhi.x - blo.x) / L, sy = (bhi.y - blo.y) / L, sz = (bhi.z - blo.z) / L;
+        const float cx = bc.x - (float)root[0], cy = bc.y - (float)root[1],
+                    cz = bc.z - (float)root[2];
+        fo[0] = logf(ng);
+        fo[1] = logf(sx + 1e-7f);
+        fo[2] = logf(sy + 1e-7f);
+        fo[3] = logf(sz + 1e-7f);
+        fo[4] = logf(ng) - logf(sx + 1e-4f) - logf(sy + 1e-4f) - logf(sz + 1e-4f);
+        fo[5] = logf(sqrtf(cx * cx + cy * cy + cz * cz) / L + 1e-6f);
+        for (int k = 6; k < 11; k++) fo[k] = 0.0f;
+        fo[11] = (float)n_depth[gpid] / 22.0f;
+        for (int k = 12; k < 16; k++) fo[k] = 0.0f;
+    }
+}
+
+void nb_launch_features_tree(nb_ctx *c, float *feat)
+{
+    k_group_features_tree<<<nb_grid(c->max_n, 256, c->num_sms * 8), 256, 0, c->stream>>>(
+        c->gnode, c->gfirst, c->gcount, c->gbox, c->root, c->n_depth,
+        c->nsys > 1 ? c->sys_sorted : nullptr, c->cnt, feat, c->n, c->err);
+    nb_launched(c, "k_group_features_tree");
+}
+
 // warps of one walk launch (the frontier queues are sized for them)
 int nb_walk_warps(nb_ctx *c)
 {

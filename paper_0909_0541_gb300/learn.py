@@ -73,16 +73,65 @@ def weighted_median(v, w):
     return float(v[o][np.searchsorted(cw, 0.5 * cw[-1])])
 
 
+TREE_COLS = [0, 1, 2, 3, 4, 5, 11]   # the features of feature mode 1 (no walk)
+
+
+def predicted_labels(X, E, C, size, grid=THETA_GRID, budget=BUDGET, cols=None):
+    """Labels from the error and cost curves the features predict.
+
+    E, C: (grid, S) measured median errors and interaction costs of the S
+    sampled groups.  Least squares on the features (columns `cols`) gives
+    each group's expected ln error and ln cost at every grid theta; the label
+    is the grid theta minimising predicted cost / n_g + lambda x predicted
+    ln error, with lambda bisected so that the n_g-weighted median of the
+    *measured* errors of the labelled thetas meets the budget.  Unlike the
+    labels of the measured curves, which carry each group's unpredictable
+    scatter, these are the best choice the features allow, and a smooth
+    function of them.  Returns (labels (S,), lambda, weighted median error)."""
+    F = np.asarray(X, np.float64)
+    F = F[:, cols] if cols is not None else F[:, :NIN]
+    A = np.c_[F, np.ones(len(F))]
+    T, S = E.shape
+    PE, PC = np.zeros((T, S)), np.zeros((T, S))
+    for t in range(T):
+        ce, *_ = np.linalg.lstsq(A, np.log(E[t] + 1e-15), rcond=None)
+        cc, *_ = np.linalg.lstsq(A, np.log(C[t] + 1.0), rcond=None)
+        PE[t], PC[t] = A @ ce, np.exp(A @ cc)
+    col = np.arange(S)
+
+    def pick(lam):
+        t = np.argmin(PC / size + lam * PE, axis=0)
+        return t, weighted_median(E[t, col], size)
+
+    lo, hi = 1e-3, 1e9           # ln-space bisection on the exchange rate
+    for _ in range(60):
+        mid = float(np.sqrt(lo * hi))
+        if pick(mid)[1] > budget:
+            lo = mid
+        else:
+            hi = mid
+    t, werr = pick(hi)
+    return np.asarray(grid, np.float32)[t], hi, werr
+
+
 def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget=BUDGET,
-                 ctx: NBody | None = None):
+                 ctx: NBody | None = None, feature_mode=0, label_rule="measured",
+                 walk_weight=0.0):
     """(features (S,16), labels (S,), info) for S seeded random groups of the
     particle set (pos, mass: CUDA tensors); info holds the error and cost
-    curves, the group sizes, the sampled groups and the exchange rate."""
+    curves, the group sizes, the sampled groups and the exchange rate.
+    feature_mode: 0 probe-walk features, 1 tree-only features.  label_rule:
+    "measured" (the argmin over each group's measured curves, on the GPU) or
+    "predicted" (predicted_labels).  A group's cost at a theta is its
+    interactions, n_g (list length + n_g), plus walk_weight x list length: the
+    walk's time per list entry in units of the force's time per interaction
+    (0: interactions only)."""
     import torch
     n = int(pos.shape[0])
     own = ctx is None
     ctx = ctx or NBody(n, eps=eps, n_crit=n_crit)
     ctx.build_tree(pos, mass)
+    ctx.set_feature_mode(feature_mode)
     feat = ctx.group_features(n_crit)
     G = int(feat.shape[0])
     rng = np.random.default_rng(seed)
@@ -100,7 +149,8 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
         ctx.walk_groups(float(th), n_crit)
         ctx.forces(eps, acc)
         errs[t] = group_errors(acc, ref, t_dev, o_dev)
-        cost[t] = size * (ctx.copy_group_lengths()[sel] + size)
+        ln = ctx.copy_group_lengths()[sel]
+        cost[t] = size * (ln + size) + walk_weight * ln
     grid_d = torch.from_numpy(np.asarray(grid, np.float32)).to(dev)
     cost_d = torch.from_numpy(cost).to(dev)
     size_d = torch.from_numpy(size).to(dev)
@@ -112,15 +162,22 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
         ti = np.searchsorted(np.asarray(grid, np.float32), lab.cpu().numpy())
         return lab, weighted_median(E[np.minimum(ti, len(grid) - 1), col], size)
 
-    lo, hi = 1.0, 1e6          # ln-space bisection on the exchange rate
-    for _ in range(40):
-        mid = float(np.sqrt(lo * hi))
-        if labelled_error(mid)[1] > budget:
-            lo = mid
-        else:
-            hi = mid
-    labels, werr = labelled_error(hi)
     X = feat[torch.from_numpy(sel).to(dev)].contiguous()
+    if label_rule == "predicted":
+        cols = TREE_COLS if feature_mode == 1 else None
+        lab, hi, werr = predicted_labels(X.cpu().numpy(), E.astype(np.float64),
+                                         cost.astype(np.float64), size.astype(np.float64),
+                                         grid, budget, cols)
+        labels = torch.from_numpy(lab).to(dev)
+    else:
+        lo, hi = 1.0, 1e6          # ln-space bisection on the exchange rate
+        for _ in range(40):
+            mid = float(np.sqrt(lo * hi))
+            if labelled_error(mid)[1] > budget:
+                lo = mid
+            else:
+                hi = mid
+        labels, werr = labelled_error(hi)
     if own:
         ctx.close()
     info = dict(errors=E, cost=cost, size=size, groups=sel, lam=hi, labelled_error=werr)

@@ -39,6 +39,19 @@ def test_probe_features_match_oracle(oracle_lib):
     assert np.allclose(feat[sel, :12], ref, rtol=0, atol=2e-5)
 
 
+def test_tree_features_match_oracle(oracle_lib):
+    """Feature mode 1: the features that need no walk, for every group,
+    against the oracle's tree_features; the walk-based slots are zero."""
+    nb, ps, pos, mass, ctx = setup()
+    ctx.set_feature_mode(1)
+    feat = ctx.group_features(64).cpu().numpy()
+    T = oracle_lib.Tree(ps.pos, ps.mass)
+    ref = ofeat.tree_features(T, 64)
+    assert feat.shape[0] == ref.shape[0]
+    assert np.all(feat[:, 6:11] == 0) and np.all(feat[:, 12:] == 0)
+    assert np.allclose(feat[:, :12], ref, rtol=0, atol=2e-5)
+
+
 def test_per_group_theta_lists_bit_exact(oracle_lib):
     nb, ps, pos, mass, ctx = setup(20000, 62, 30)
     T = oracle_lib.Tree(ps.pos, ps.mass)
