@@ -309,7 +309,9 @@ int nb_group_features(nb_ctx *ctx, int n_crit, float *feat_dev, int64_t cap_rows
  * walk: features 0-5 and 11 as above (the same formulas), 6-10 zero. */
 int nb_set_feature_mode(nb_ctx *ctx, int mode);
 /* Walk with a per-group theta from the network (params_dev, layout below)
- * evaluated on the probe features; a non-finite output becomes
+ * evaluated on the features of the context's feature mode (the probe walk's,
+ * or the tree-only ones, whose groups the walk then reuses, setting only
+ * each box's 1/theta); a non-finite output becomes
  * theta_fallback.  theta_out_dev (nullable, n floats) receives the group
  * thetas (G of them are meaningful). */
 int nb_walk_groups_learned(nb_ctx *ctx, int n_crit, const float *params_dev,
