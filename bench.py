@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--n-crit", type=int, default=None)
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every kernel of the timed steps from the host instead of "
+                         "replaying them from one CUDA graph")
     ap.add_argument("--fused", action="store_true",
                     help="force passes walk and sum in one kernel, no interaction lists")
     ap.add_argument("--judge-targets", type=int, default=8192)
@@ -315,6 +318,13 @@ def run_reference(args, ws, rank):
 
 
 # ----------------------------------------------------------------- GPU arm
+def graph_shape(steps, most=100):
+    """(steps per captured graph, launches): the largest divisor of `steps`
+    not above `most`, so that the launches time exactly `steps` KDK steps."""
+    g = max(d for d in range(1, min(steps, most) + 1) if steps % d == 0)
+    return g, steps // g
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -348,8 +358,15 @@ def run_ours(args, ws, rank, local):
         for _ in range(args.warmup):
             ctx.leapfrog_step(pos, vel, mass, dt)
         ctx.sync_status()
-        st0 = ctx.stats()
         ctx.set_timing(True)
+        graph_steps, graph_runs = graph_shape(args.steps)
+        if not args.eager:
+            # the K timed steps as graph_runs launches of one captured graph of
+            # graph_steps KDK steps; one more launch, untimed, warms it up
+            ctx.graph_capture_leapfrog(pos, vel, mass, dt, graph_steps)
+            ctx.graph_launch()
+            ctx.sync_status()
+        st0 = ctx.stats()
         ctx.get_timing()
         sampler = ClockSampler(local)
         sampler.start()
@@ -358,8 +375,12 @@ def run_ours(args, ws, rank, local):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = sampler.mark()
         e0.record(stream)
-        for _ in range(args.steps):
-            ctx.leapfrog_step(pos, vel, mass, dt)
+        if args.eager:
+            for _ in range(args.steps):
+                ctx.leapfrog_step(pos, vel, mass, dt)
+        else:
+            for _ in range(graph_runs):
+                ctx.graph_launch()
         e1.record(stream)
         torch.cuda.synchronize()
         t1 = sampler.mark()
@@ -487,6 +508,9 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": args.workload, "n": n, "theta": w["theta"], "eps": w["eps"],
                        "n_crit": w["n_crit"], "dt": dt, "precision": args.precision,
                        "force_path": "fused walk+force" if args.fused else "lists",
+                       "launch": ("eager: every kernel launched from the host" if args.eager
+                                  else f"CUDA graph of {graph_steps} KDK steps, launched "
+                                       f"{graph_runs}x"),
                        "step": "KDK leapfrog: tree build + group walk + force + kicks/drift",
                        "l2": "inputs larger than L2 (positions+velocities 138 MB, lists "
                              f"{st1['list_entries'] * 20 / 1e9:.2f} GB per step)",
@@ -667,13 +691,12 @@ def run_batch(args, ws, rank, local):
                                    reps=2, offsets=O)
         ctx.leapfrog_step_batched(P, V, M, O, dt)      # sizes the lists, caches a(x)
         ctx.set_sync_checks(False)
-        ctx.get_timing()                               # resets the launch counter
         ctx.graph_capture_leapfrog(P, V, M, dt, nsteps, offsets=O)
-        graph_kernels = ctx.get_timing()["launches"]   # kernel nodes in the graph
         for _ in range(args.warmup):
             ctx.graph_launch()
         ctx.sync_status()
         st0 = ctx.stats()
+        ctx.get_timing()                               # resets the launch counter
         sampler = ClockSampler(local)
         sampler.start()
         torch.cuda.synchronize()
@@ -688,6 +711,8 @@ def run_batch(args, ws, rank, local):
         clocks = sampler.stop(t0, t1)
         ctx.sync_status()
         st1 = ctx.stats()
+        gpu_launches = ctx.get_timing()["launches"]   # graph launches x kernel nodes
+    graph_kernels = gpu_launches // max(args.steps, 1)
     ms = e0.elapsed_time(e1)
     inter = (st1["n_pp_total"] - st0["n_pp_total"]) + (st1["n_pc_total"] - st0["n_pc_total"])
     kdk = args.steps * nsteps
@@ -705,7 +730,7 @@ def run_batch(args, ws, rank, local):
                         for k, v in table.items()},
         "interactions_per_step": inter / kdk,
         "particle_steps_per_s": n * kdk / (ms / 1e3),
-        "gpu_launches": graph_kernels * args.steps,
+        "gpu_launches": gpu_launches,
         "graph_kernel_nodes": graph_kernels,
         "clocks": clocks,
     }

@@ -210,7 +210,11 @@ int nb_leapfrog_acc(nb_ctx *ctx, float *acc_dev);
  * made with sync_checks on, which sizes the list storage; during replay
  * nothing synchronises or allocates, and a list that outgrows its slot is
  * latched as NB_ERR_CAPACITY for nb_sync_status.  pos/vel/mass are the
- * buffers every replay reads and updates. */
+ * buffers every replay reads and updates.  With timing on (nb_set_timing) at
+ * capture, the phase events are captured as event-record nodes that every
+ * launch records again, and nb_get_timing reports the phases of the last
+ * launch times the launches since its previous call; kernels launched by the
+ * graph count in its `launches` output. */
 int nb_graph_capture_leapfrog(nb_ctx *ctx, double *pos_dev, double *vel_dev,
                               const float *mass_dev, const int64_t *offsets_dev,
                               int64_t n_systems, int64_t n, double dt, int nsteps);

@@ -278,19 +278,27 @@ static int finish(nb_ctx *c)
     return sync_read(c);
 }
 
-// phase timing: a pair of events on the context's stream around each phase
+// phase timing: a pair of events on the context's stream around each phase.
+// Under stream capture an event must be recorded as external to become an
+// event-record node that every launch of the graph records.
+static void record_event(nb_ctx *c, cudaEvent_t e)
+{
+    if (c->capturing) cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, c->stream);
+}
+
 static int phase_begin(nb_ctx *c)
 {
-    if (!c->timing || !c->ev || c->ev_used >= NB_EV_POOL) return -1;
-    const int k = c->ev_used++;
-    cudaEventRecord(c->ev[2 * k], c->stream);
+    if (!c->timing || !c->ev || c->ev_graph + c->ev_used >= NB_EV_POOL) return -1;
+    const int k = c->ev_graph + c->ev_used++;
+    record_event(c, c->ev[2 * k]);
     return k;
 }
 
 static void phase_end(nb_ctx *c, int k, int phase)
 {
     if (k < 0) return;
-    cudaEventRecord(c->ev[2 * k + 1], c->stream);
+    record_event(c, c->ev[2 * k + 1]);
     c->ev_phase[k] = phase;
 }
 
@@ -798,30 +806,44 @@ int nb_graph_capture_leapfrog(nb_ctx *c, double *pos, double *vel, const float *
     if (!c->acc_valid || c->n != n || (!c->fused && (c->list_cap < 1 || !c->list_id)))
         return NB_ERR_STATE;
     CK(cudaStreamSynchronize(c->stream));
-    const int sync = c->sync_checks, timing = c->timing;
+    const int sync = c->sync_checks;
     c->sync_checks = 0;
-    c->timing = 0;
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
     }
+    // with timing on, the phase events become event-record nodes of the
+    // graph (pairs [0, ev_graph) of the pool), recorded again by every launch;
+    // eager phases recorded before the capture are dropped
+    c->ev_graph = 0;
+    c->ev_used = 0;
+    c->graph_runs = 0;
+    const int64_t launches0 = c->launches;
     int rc = NB_OK;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         rc = NB_ERR_CUDA;
     } else {
+        c->capturing = 1;
         for (int k = 0; k < nsteps && rc == NB_OK; k++)
             rc = leapfrog(c, pos, vel, mass, n, dt, offsets, offsets ? nsys : 1);
+        c->capturing = 0;
         if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess && rc == NB_OK) rc = NB_ERR_CUDA;
         if (rc == NB_OK && cudaGraphInstantiate(&c->graph_exec, graph, 0) != cudaSuccess)
             rc = NB_ERR_CUDA;
     }
     if (graph) cudaGraphDestroy(graph);
     c->sync_checks = sync;
-    c->timing = timing;
+    c->graph_launches = c->launches - launches0;
+    c->launches = launches0;   // the captured kernels count when the graph runs
     if (rc) {
         cudaGetLastError();
         c->graph_exec = nullptr;
+        c->ev_used = 0;
+        c->graph_launches = 0;
+    } else {
+        c->ev_graph = c->ev_used;
+        c->ev_used = 0;
     }
     return rc;
 }
@@ -831,6 +853,8 @@ int nb_graph_launch(nb_ctx *c)
     if (!c) return NB_ERR_INVALID_ARG;
     if (!c->graph_exec) return NB_ERR_STATE;
     CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    c->graph_runs++;
+    c->launches += c->graph_launches;
     return finish(c);
 }
 
@@ -935,7 +959,17 @@ int nb_get_timing(nb_ctx *c, double *ms, int64_t *calls, int64_t *launches)
     CK(cudaStreamSynchronize(c->stream));
     double t[NB_NPHASE] = {0, 0, 0, 0};
     int64_t k[NB_NPHASE] = {0, 0, 0, 0};
-    for (int i = 0; i < c->ev_used; i++) {
+    // the graph's events hold its last launch: scaled by the launches since
+    // the last call
+    if (c->graph_runs > 0)
+        for (int i = 0; i < c->ev_graph; i++) {
+            float e = 0.f;
+            CK(cudaEventElapsedTime(&e, c->ev[2 * i], c->ev[2 * i + 1]));
+            t[c->ev_phase[i]] += (double)e * (double)c->graph_runs;
+            k[c->ev_phase[i]] += c->graph_runs;
+        }
+    c->graph_runs = 0;
+    for (int i = c->ev_graph; i < c->ev_graph + c->ev_used; i++) {
         float e = 0.f;
         CK(cudaEventElapsedTime(&e, c->ev[2 * i], c->ev[2 * i + 1]));
         t[c->ev_phase[i]] += e;

@@ -8,12 +8,16 @@
 // and the streams' sums are combined with shuffles at the end -- so small
 // groups keep every lane busy.  One warp takes one item from a global queue;
 // targets are FP32 coordinates relative to the group centre.  Sources are
-// staged 32 at a time: one coalesced 16-byte load per lane into a per-warp
-// shared-memory tile, then broadcast reads.  Per interaction:
+// staged TILE at a time: one coalesced 16-byte load per lane into a per-warp
+// shared-memory tile, then broadcast reads.  The tile holds record
+// pairs interleaved (x_j, x_j+1, y_j, y_j+1 | z_j, z_j+1, m_j, m_j+1) so that
+// each step below runs on two records at once with the packed FP32
+// instructions (add/mul/fma .f32x2).  Per interaction:
 //   dx = xj - xi (3 FADD); r2 = eps^2 + dx.dx (3 FFMA); ri = rsqrt(r2) (MUFU);
 //   mr = mj ri; mr3 = mr ri ri (3 FMUL); a += mr3 dx (3 FFMA); phi -= mr (FADD)
-// i.e. 13 FP32-pipe instructions and one MUFU.  This stays on the CUDA
-// cores: there is no dense contraction to hand to the tensor cores.
+// i.e. 13 FP32-pipe operations and one MUFU, issued as 6.5 packed
+// instructions.  This stays on the CUDA cores: there is no dense contraction
+// to hand to the tensor cores.
 //
 // Two phases per item: (1) the group's list (particles and accepted cells
 // outside the group), unmasked; (2) the group's own members, read from the
@@ -59,10 +63,11 @@ __device__ __forceinline__ void force_item(
     const int32_t len = glen[g] < lim ? glen[g] : (int32_t)lim;
     const float4 bc = gbox[3 * (int64_t)g + 2];
     const float4 pad = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-    float xi[R], yi[R], zi[R];
+    Tgt t[R];
     int32_t kk[R], slot[R];
     bool ok[R];
-    Acc<MODE> A[R], T[R];
+    Acc<MODE> A[R];
+    Sum2 P[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int32_t k = i0 + r * W + row;
@@ -70,11 +75,9 @@ __device__ __forceinline__ void force_item(
         kk[r] = k;
         slot[r] = f + (ok[r] ? k : ng - 1);
         const float4 h = p_hi[slot[r]], lo = p_lo[slot[r]];
-        xi[r] = nb_rel(h.x, lo.x, bc.x);
-        yi[r] = nb_rel(h.y, lo.y, bc.y);
-        zi[r] = nb_rel(h.z, lo.z, bc.z);
+        t[r].set(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y), nb_rel(h.z, lo.z, bc.z));
         A[r].init();
-        T[r].init();
+        P[r].init();
     }
     // (1) the list: sources outside the group, TILE records per tile
     constexpr int TK = TILE / NB_WARP;   // records each lane stages per tile
@@ -83,28 +86,29 @@ __device__ __forceinline__ void force_item(
 #pragma unroll
         for (int k = 0; k < TK; k++) {
             const int32_t jj = j0 + k * NB_WARP + lane;
-            tile[k * NB_WARP + lane] = jj < len ? src[jj] : pad;
+            put_rec(tile, k * NB_WARP + lane, jj < len ? src[jj] : pad);
         }
         __syncwarp();
-        tile_pass<MODE, GUARD, false, R, W * TK>(tile + stream * W * TK, j0 + stream * W * TK, xi,
-                                                 yi, zi, kk, eps2, A, T);
+        tile_pass<MODE, GUARD, false, R, W * TK>(tile, stream * W * TK, j0 + stream * W * TK, t,
+                                                 kk, eps2, A, P);
         __syncwarp();
     }
     // (2) the group's own members, j != i
     for (int32_t j0 = 0; j0 < ng; j0 += NB_WARP) {
         const int32_t jj = j0 + lane;
+        float4 v = pad;
         if (jj < ng) {
             const float4 h = p_hi[f + jj], lo = p_lo[f + jj];
-            tile[lane] = make_float4(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y),
-                                     nb_rel(h.z, lo.z, bc.z), h.w);
-        } else {
-            tile[lane] = pad;
+            v = make_float4(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y),
+                            nb_rel(h.z, lo.z, bc.z), h.w);
         }
+        put_rec(tile, lane, v);
         __syncwarp();
-        tile_pass<MODE, GUARD, true, R, W>(tile + stream * W, j0 + stream * W, xi, yi, zi, kk,
-                                           eps2, A, T);
+        tile_pass<MODE, GUARD, true, R, W>(tile, stream * W, j0 + stream * W, t, kk, eps2, A, P);
         __syncwarp();
     }
+#pragma unroll
+    for (int r = 0; r < R; r++) pair_fold<MODE>(A[r], P[r]);
     if constexpr (S > 1) {
 #pragma unroll
         for (int o = W; o < NB_WARP; o <<= 1) stream_sum<MODE>(A[0], o);
@@ -209,7 +213,7 @@ k_item_order(const int32_t *__restrict__ items, const int32_t *__restrict__ gcou
 // TILE: list records staged per tile (the j-tile depth); BT: threads per
 // block.  Both are chosen by the autotuner for the FP32 mode.
 template <int MODE, bool GUARD, int TILE, int BT>
-__global__ void __launch_bounds__(BT, (MODE == MODE_COMP ? 4 : 5) * F_T / BT)
+__global__ void __launch_bounds__(BT, (MODE == MODE_F64 ? 5 : 4) * F_T / BT)
 k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
         const int32_t *__restrict__ gfirst,
         const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,

@@ -58,10 +58,11 @@ __device__ __forceinline__ void fused_item(
     const float4 bc = gbox[3 * (int64_t)g + 2];
     const float invth = bc.w;
     const float4 pad = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-    float xi[R], yi[R], zi[R];
+    Tgt t[R];
     int32_t kk[R], slot[R];
     bool ok[R];
-    Acc<MODE> A[R], T[R];
+    Acc<MODE> A[R];
+    Sum2 P[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int32_t k = i0 + r * W + row;
@@ -69,11 +70,9 @@ __device__ __forceinline__ void fused_item(
         kk[r] = k;
         slot[r] = f + (ok[r] ? k : ng - 1);
         const float4 h = p_hi[slot[r]], lo = p_lo[slot[r]];
-        xi[r] = nb_rel(h.x, lo.x, bc.x);
-        yi[r] = nb_rel(h.y, lo.y, bc.y);
-        zi[r] = nb_rel(h.z, lo.z, bc.z);
+        t[r].set(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y), nb_rel(h.z, lo.z, bc.z));
         A[r].init();
-        T[r].init();
+        P[r].init();
     }
     // (1) walk, summing every 32 buffered sources
     const int32_t gpid = gnode[g];
@@ -109,9 +108,9 @@ __device__ __forceinline__ void fused_item(
             }
             const unsigned em = __ballot_sync(FULL, emit);
             if (emit)
-                buf[nbuf + __popc(em & lt)] =
-                    make_float4(nb_rel(r.a.x, r.d.x, bc.x), nb_rel(r.a.y, r.d.y, bc.y),
-                                nb_rel(r.a.z, r.d.z, bc.z), r.a.w);
+                put_rec(buf, nbuf + __popc(em & lt),
+                        make_float4(nb_rel(r.a.x, r.d.x, bc.x), nb_rel(r.a.y, r.d.y, bc.y),
+                                    nb_rel(r.a.z, r.d.z, bc.z), r.a.w));
             nbuf += __popc(em);
             len += __popc(em);
             ncell += __popc(__ballot_sync(FULL, cell_emit));
@@ -131,10 +130,11 @@ __device__ __forceinline__ void fused_item(
             nb += __shfl_sync(FULL, incl, 31);
             __syncwarp();
             if (nbuf >= NB_WARP) {   // one full tile: sum it, keep the rest
-                tile_pass<MODE, GUARD, false, R, W, FW_UNROLL>(buf + stream * W, 0, xi, yi, zi, kk, eps2, A,
-                                                    T);
+                tile_pass<MODE, GUARD, false, R, W, FW_UNROLL>(buf, stream * W, 0, t, kk, eps2, A,
+                                                               P);
                 __syncwarp();
-                if (lane < nbuf - NB_WARP) buf[lane] = buf[NB_WARP + lane];
+                // move the rest down by whole record pairs (NB_WARP is even)
+                if (lane < ((nbuf - NB_WARP + 1) & ~1)) buf[lane] = buf[NB_WARP + lane];
                 nbuf -= NB_WARP;
                 __syncwarp();
             }
@@ -154,26 +154,27 @@ __device__ __forceinline__ void fused_item(
         }
     }
     if (nbuf > 0) {   // the last, padded tile of the list
-        if (lane >= nbuf) buf[lane] = pad;
+        if (lane >= nbuf) put_rec(buf, lane, pad);
         __syncwarp();
-        tile_pass<MODE, GUARD, false, R, W, FW_UNROLL>(buf + stream * W, 0, xi, yi, zi, kk, eps2, A, T);
+        tile_pass<MODE, GUARD, false, R, W, FW_UNROLL>(buf, stream * W, 0, t, kk, eps2, A, P);
         __syncwarp();
     }
     // (2) the group's own members, j != i
     for (int32_t j0 = 0; j0 < ng; j0 += NB_WARP) {
         const int32_t jj = j0 + lane;
+        float4 v = pad;
         if (jj < ng) {
             const float4 h = p_hi[f + jj], lo = p_lo[f + jj];
-            buf[lane] = make_float4(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y),
-                                    nb_rel(h.z, lo.z, bc.z), h.w);
-        } else {
-            buf[lane] = pad;
+            v = make_float4(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y),
+                            nb_rel(h.z, lo.z, bc.z), h.w);
         }
+        put_rec(buf, lane, v);
         __syncwarp();
-        tile_pass<MODE, GUARD, true, R, W>(buf + stream * W, j0 + stream * W, xi, yi, zi, kk,
-                                           eps2, A, T);
+        tile_pass<MODE, GUARD, true, R, W>(buf, stream * W, j0 + stream * W, t, kk, eps2, A, P);
         __syncwarp();
     }
+#pragma unroll
+    for (int r = 0; r < R; r++) pair_fold<MODE>(A[r], P[r]);
     if (lane == 0) {   // interaction counts of this item's targets
         const int32_t mi = ng - i0 < R * W ? ng - i0 : R * W;
         fc.pp += (long long)mi * (len - ncell) + (long long)mi * (ng - 1);

@@ -231,6 +231,10 @@ struct nb_ctx {
     int fused;               // leapfrog force passes use the fused walk and force
     int feature_mode;        // learned theta: 0 probe-walk features, 1 tree-only features
     int ev_used;
+    int ev_graph;            // event pairs [0, ev_graph) are nodes of the captured graph
+    int capturing;           // a graph capture is in progress on the stream
+    int64_t graph_runs;      // graph launches since the last nb_get_timing
+    int64_t graph_launches;  // kernels in one launch of the captured graph
     cudaEvent_t *ev;         // NB_EV_POOL pairs
     int *ev_phase;
     long long launches;

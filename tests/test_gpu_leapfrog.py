@@ -103,3 +103,51 @@ def test_host_buffer_step_equals_device_step():
     assert np.array_equal(vel.cpu().numpy(), hvel.numpy())
     with pytest.raises(TypeError):
         b.leapfrog_step_host(hpos.float(), hvel, hmass, dt)
+
+
+def test_graph_replay_times_its_phases_and_equals_eager_steps():
+    """Three KDK steps captured in a CUDA graph with timing on: two launches
+    give the same bits as six eager steps; nb_get_timing reports each phase
+    of the last launch twice (build, walk, force once per step, integrate
+    twice) and the captured kernels twice; eager phases after that are timed
+    on their own."""
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(20000, 33)
+    eps, theta, n_crit, dt = 1.0 / 64, 0.75, 64, 1.0 / 128
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    out = []
+    for graph in (False, True):
+        pos = torch.from_numpy(ps.pos).to(dev)
+        vel = torch.from_numpy(ps.vel).to(dev)
+        mass = torch.from_numpy(ps.mass).to(dev)
+        stream.wait_stream(torch.cuda.current_stream())
+        ctx = nb.NBody(ps.n, eps=eps, theta=theta, n_crit=n_crit, stream=stream)
+        with torch.cuda.stream(stream):
+            ctx.leapfrog_step(pos, vel, mass, dt)
+            ctx.set_sync_checks(False)
+            if graph:
+                ctx.set_timing(True)
+                ctx.graph_capture_leapfrog(pos, vel, mass, dt, 3)
+                ctx.get_timing()
+                ctx.graph_launch()
+                ctx.graph_launch()
+                tm = ctx.get_timing()
+                assert tm["launches"] > 0 and tm["launches"] % 2 == 0
+                for phase, calls in (("build", 6), ("walk", 6), ("force", 6),
+                                     ("integrate", 12)):
+                    assert tm[phase][1] == calls, (phase, tm[phase])
+                    assert tm[phase][0] > 0.0
+                ctx.leapfrog_step(pos, vel, mass, dt)
+                tm = ctx.get_timing()
+                assert tm["force"][1] == 1 and tm["integrate"][1] == 2
+                assert tm["launches"] > 0
+                ctx.set_timing(False)
+            else:
+                for _ in range(7):
+                    ctx.leapfrog_step(pos, vel, mass, dt)
+            stream.synchronize()
+            ctx.sync_status()
+        out.append((pos.cpu().numpy(), vel.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
