@@ -208,7 +208,7 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
 }
 
 template <bool ONESWEEP>
-__global__ void __launch_bounds__(RS_T, 2)
+__global__ void __launch_bounds__(RS_T, 3)
 k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
              const uint32_t *__restrict__ offs, int64_t n, int shift, int nb,

@@ -512,7 +512,11 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
             cbkt[b] = (int16_t)k;
             atomicAdd(&hb[k], 1);
             const double *root = roots + (sys ? 8 * (int64_t)sys[slot] : 0);
+            // geometric centre corner + (q + 1/2) l, written as (2q + 1)(l / 2): the
+            // same real product (scaling by 2^-k is exact for a normal l), rounded
+            // once either way, with one FP64 add fewer per axis
             const double lc = __dmul_rn(root[3], pow2_neg(depth));
+            const double lh = __dmul_rn(root[3], pow2_neg(depth + 1));
             const uint64_t kf = key[slot];
             const uint32_t cq[3] = {compact3(kf >> 2) >> (NB_LEVELS - depth),
                                     compact3(kf >> 1) >> (NB_LEVELS - depth),
@@ -520,7 +524,7 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
 #pragma unroll
             for (int d = 0; d < 3; d++)
                 b_com[3 * (int64_t)b + d] =
-                    __dadd_rn(root[4 + d], __dmul_rn(__dadd_rn((double)cq[d], 0.5), lc));
+                    __dadd_rn(root[4 + d], __dmul_rn((double)(2u * cq[d] + 1u), lh));
             nb_wrec_put_hi(&wrec[b], wb, __double2float_rn(lc), 0.0f);
         }
     }
