@@ -258,7 +258,8 @@ def cpu_oracle_rate(ps, w, seconds, seed=7, name=WORKLOAD):
 
 def cpu_direct_rate(ps, w, targets=64, seed=5):
     """Interactions/s of the oracle's FP64 direct sum (every source, a seeded
-    sample of targets), the judge's CPU counterpart."""
+    sample of targets): the CPU counterpart of the GPU's FP64 direct-sum
+    accuracy reference."""
     import oracle
     tg = np.random.default_rng(seed).choice(ps.n, min(targets, ps.n), replace=False)
     t0 = time.perf_counter()

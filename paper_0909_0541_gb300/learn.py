@@ -203,7 +203,7 @@ def train(X, y, epochs=150, batch=256, lr=2e-3, seed=5):
 
 
 def median_error(acc, ref, targets):
-    """Median |da|/|a| of acc at targets against the judge ref."""
+    """Median |da|/|a| of acc at targets against the FP64 direct-sum reference ref."""
     import torch
     d = (acc[targets].double() - ref).norm(dim=1) / ref.norm(dim=1)
     return float(torch.median(d).item()) if d.numel() else 0.0
