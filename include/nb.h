@@ -214,7 +214,9 @@ int nb_leapfrog_acc(nb_ctx *ctx, float *acc_dev);
  * capture, the phase events are captured as event-record nodes that every
  * launch records again, and nb_get_timing reports the phases of the last
  * launch times the launches since its previous call; kernels launched by the
- * graph count in its `launches` output. */
+ * graph count in its `launches` output.  The event pool holds 2048 phases: a
+ * capture longer than that times only its first 2048 phases, and the pool's
+ * remainder serves eager phases until the next capture. */
 int nb_graph_capture_leapfrog(nb_ctx *ctx, double *pos_dev, double *vel_dev,
                               const float *mass_dev, const int64_t *offsets_dev,
                               int64_t n_systems, int64_t n, double dt, int nsteps);

@@ -370,7 +370,9 @@ class NBody:
 
     def get_timing(self) -> dict:
         """Per-phase device milliseconds and call counts since the last call,
-        and the number of libnb kernel launches in that time."""
+        and the number of libnb kernel launches in that time.  Phases inside a
+        graph captured with timing on count once per graph launch (the last
+        launch's times, scaled by the launches since the last call)."""
         ms = np.zeros(4)
         calls = np.zeros(4, np.int64)
         launches = np.zeros(1, np.int64)
