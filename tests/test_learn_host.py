@@ -1,9 +1,12 @@
 """Host logic of the learned opening angle (no GPU): the labels computed from
 predicted error and cost curves, on synthetic curves whose best allocation
-is known."""
+is known, and the flat parameter layout the host hands to the network's
+kernels."""
 import numpy as np
 
-from paper_0909_0541_gb300 import learn
+import nbsynth
+from oracle import mlp
+from paper_0909_0541_gb300 import MLP_NPARAM, learn
 
 
 def curves(S=400, seed=0):
@@ -45,3 +48,26 @@ def test_weighted_median():
     v = np.array([5.0, 1.0, 3.0])
     assert learn.weighted_median(v, np.array([1.0, 1.0, 1.0])) == 3.0
     assert learn.weighted_median(v, np.array([1.0, 10.0, 1.0])) == 1.0
+
+
+def test_host_parameter_packing_matches_the_oracle_layout():
+    """learn.pack_params (what the product hands to nb_mlp_*) and the
+    oracle's pack_params write the same flat layout; a zero spread becomes 1
+    so the normalisation never divides by zero."""
+    w = nbsynth.mlp_initial_weights(7)
+    rng = np.random.default_rng(8)
+    b = {k: rng.normal(0, 0.1, 64) for k in ("b1", "b2", "b3")}
+    mu = rng.normal(0, 1, 12)
+    sigma = rng.uniform(0.5, 2.0, 12)
+    w_all = dict(w, **b, b4=0.25)
+    host = learn.pack_params(w_all, mu, sigma)
+    ref = mlp.pack_params(w["W1"], b["b1"], w["W2"], b["b2"], w["W3"], b["b3"], w["w4"],
+                          0.25, mu, sigma)
+    assert host.dtype == np.float32 and host.shape == (MLP_NPARAM,) == ref.shape
+    assert np.array_equal(host, ref)
+    sigma0 = sigma.copy()
+    sigma0[[2, 5]] = 0.0
+    packed = mlp.unpack(learn.pack_params(w_all, mu, sigma0))
+    assert np.all(packed["sigma"][[2, 5]] == 1.0)
+    assert np.all(packed["sigma"][12:] == 1.0) and np.all(packed["mu"][12:] == 0.0)
+    assert np.all(packed["W1"][:, 12:] == 0.0)
