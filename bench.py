@@ -361,12 +361,17 @@ def run_ours(args, ws, rank, local):
         ctx.sync_status()
         ctx.set_timing(True)
         graph_steps, graph_runs = graph_shape(args.steps)
+        graph_failed = None
         if not args.eager:
             # the K timed steps as graph_runs launches of one captured graph of
             # graph_steps KDK steps; one more launch, untimed, warms it up
-            ctx.graph_capture_leapfrog(pos, vel, mass, dt, graph_steps)
-            ctx.graph_launch()
-            ctx.sync_status()
+            try:
+                ctx.graph_capture_leapfrog(pos, vel, mass, dt, graph_steps)
+                ctx.graph_launch()
+                ctx.sync_status()
+            except nb.NBError as e:   # time the same steps launched eagerly
+                graph_failed = str(e)
+                args.eager = True
         st0 = ctx.stats()
         ctx.get_timing()
         sampler = ClockSampler(local)
@@ -509,7 +514,9 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": args.workload, "n": n, "theta": w["theta"], "eps": w["eps"],
                        "n_crit": w["n_crit"], "dt": dt, "precision": args.precision,
                        "force_path": "fused walk+force" if args.fused else "lists",
-                       "launch": ("eager: every kernel launched from the host" if args.eager
+                       "launch": ((f"eager (graph capture failed: {graph_failed})"
+                                   if graph_failed else
+                                   "eager: every kernel launched from the host") if args.eager
                                   else f"CUDA graph of {graph_steps} KDK steps, launched "
                                        f"{graph_runs}x"),
                        "step": "KDK leapfrog: tree build + group walk + force + kicks/drift",
