@@ -58,6 +58,7 @@ def lib():
             L.or_root_cube.argtypes = [i64, vp, vp]
             L.or_quantize.argtypes = [i64, vp, vp, vp]
             L.or_morton_keys.argtypes = [i64, vp, vp]
+            L.or_hilbert_keys.argtypes = [i64, vp, vp]
             L.or_tree_build.restype = vp
             L.or_tree_build.argtypes = [i64, vp, vp]
             L.or_tree_free.argtypes = [vp]
@@ -151,6 +152,14 @@ def morton_keys(q):
     q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1, 3)
     k = np.zeros(q.shape[0], dtype=np.uint64)
     lib().or_morton_keys(q.shape[0], _ptr(q), _ptr(k))
+    return k
+
+
+def hilbert_keys(q):
+    """Peano-Hilbert keys (63 bits, 21 levels) of grid coordinates."""
+    q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1, 3)
+    k = np.zeros(q.shape[0], dtype=np.uint64)
+    lib().or_hilbert_keys(q.shape[0], _ptr(q), _ptr(k))
     return k
 
 

@@ -331,3 +331,54 @@ def test_coords32_mode(oracle_lib):
     d = np.linalg.norm(a64 - a32, axis=1)
     assert np.all(d <= 1e-5 * am) and np.median(d / am) < 1e-7
     assert not np.array_equal(a64, a32)
+
+
+# ---- Peano-Hilbert keys (the alternative order of Sec. "Test and
+# Optimization"), pinned by the defining properties of the curve
+
+def _level_cells(lv):
+    g = np.arange(1 << lv)
+    return np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+
+
+@pytest.mark.parametrize("lv", [1, 2, 3, 4])
+def test_hilbert_keys_visit_every_cell_once_through_faces(oracle_lib, lv):
+    """At every level the top 3 lv key bits order the 8^lv cells as one path
+    from the origin that enters each cell once and steps across one face at
+    a time."""
+    L = 21
+    c = _level_cells(lv)
+    k = oracle_lib.hilbert_keys((c << (L - lv)).astype(np.int32))
+    top = (k >> np.uint64(3 * (L - lv))).astype(np.int64)
+    assert np.array_equal(np.sort(top), np.arange(8 ** lv))
+    path = c[np.argsort(top)]
+    assert np.array_equal(path[0], [0, 0, 0])
+    assert np.all(np.abs(np.diff(path, axis=0)).sum(1) == 1)
+
+
+def test_hilbert_keys_adjacent_at_full_resolution(oracle_lib):
+    """Around random grid points: the keys one above and one below a point's
+    key belong to two of its six face neighbours."""
+    L = 21
+    rng = np.random.default_rng(11)
+    q = rng.integers(1, (1 << L) - 1, (300, 3)).astype(np.int32)
+    k = oracle_lib.hilbert_keys(q).astype(np.int64)
+    steps = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
+    nb = oracle_lib.hilbert_keys((q[:, None, :] + steps[None]).reshape(-1, 3).astype(np.int32))
+    nb = nb.astype(np.int64).reshape(-1, 6)
+    for i in range(len(q)):
+        assert k[i] + 1 in nb[i] and k[i] - 1 in nb[i]
+
+
+def test_hilbert_keys_nest_by_level(oracle_lib):
+    """Points of one aligned sub-cube at level lv share their top 3 lv key
+    bits, so each sub-cube is one contiguous key range (what the tree build
+    needs of any key order)."""
+    L = 21
+    rng = np.random.default_rng(12)
+    for lv in (1, 3, 7, 12, 20):
+        base = rng.integers(0, 1 << lv, (40, 3)) << (L - lv)
+        off = rng.integers(0, 1 << (L - lv), (40, 5, 3))
+        q = (base[:, None, :] + off).reshape(-1, 3).astype(np.int32)
+        top = oracle_lib.hilbert_keys(q) >> np.uint64(3 * (L - lv))
+        assert np.all(top.reshape(40, 5) == top.reshape(40, 5)[:, :1])
