@@ -61,6 +61,9 @@ def lib():
             L.or_hilbert_keys.argtypes = [i64, vp, vp]
             L.or_tree_build.restype = vp
             L.or_tree_build.argtypes = [i64, vp, vp]
+            L.or_tree_build_order.restype = vp
+            L.or_tree_build_order.argtypes = [i64, vp, vp, C.c_int]
+            L.or_tree_corners.argtypes = [vp, vp]
             L.or_tree_free.argtypes = [vp]
             L.or_tree_nnodes.restype = i64
             L.or_tree_nnodes.argtypes = [vp]
@@ -164,13 +167,19 @@ def hilbert_keys(q):
 
 
 class Tree:
-    """The oracle's oct-tree over (pos, mass); nodes in depth-first preorder."""
+    """The oracle's oct-tree over (pos, mass); nodes in depth-first preorder.
+    order: "morton" visits children in octant order, "hilbert" in
+    Peano-Hilbert order (the same cells, numbered in another order)."""
 
-    def __init__(self, pos, mass):
+    ORDERS = {"morton": 0, "hilbert": 1}
+
+    def __init__(self, pos, mass, order="morton"):
         self.pos = _pos(pos)
         self.mass = _mass(mass)
         self.n = self.pos.shape[0]
-        self._h = lib().or_tree_build(self.n, _ptr(self.pos), _ptr(self.mass))
+        self.key_order = order
+        self._h = lib().or_tree_build_order(self.n, _ptr(self.pos), _ptr(self.mass),
+                                            self.ORDERS[order])
         if not self._h:
             raise MemoryError("oracle tree build failed")
         self.nnodes = int(lib().or_tree_nnodes(self._h))
@@ -185,6 +194,12 @@ class Tree:
         if h:
             lib().or_tree_free(h)
             self._h = None
+
+    def corners(self):
+        """Integer corner of every node at its level (zeros for particles)."""
+        c = np.zeros((self.nnodes, 3), np.int32)
+        lib().or_tree_corners(self._h, _ptr(c))
+        return c
 
     def export(self):
         if self._exp is None:

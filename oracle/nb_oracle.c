@@ -280,6 +280,10 @@ typedef struct {
     int64_t *first, *count, *next, *more, *parent;
     double *M, *mx, *com; /* mass, first moment sum(m x), centre of mass     */
     float *l, *s, *comf;
+    int korder;          /* 0: Morton order, 1: Peano-Hilbert order          */
+    uint64_t *hkey;      /* Peano-Hilbert key per particle (korder 1)        */
+    int8_t *corder;      /* cells: octants of the children in visiting order,
+                          * -1 past the last                                 */
 } or_tree;
 
 static int grow(or_tree *t)
@@ -308,6 +312,7 @@ static int grow(or_tree *t)
     GROW(l, float, 1);
     GROW(s, float, 1);
     GROW(comf, float, 3);
+    GROW(corder, int8_t, 8);
 #undef GROW
     t->cap = nc;
     return 0;
@@ -330,8 +335,10 @@ static int64_t build_rec(or_tree *t, int64_t lo, int64_t cnt, int level,
     if (id < 0)
         return -1;
     t->parent[id] = parent;
-    for (int o = 0; o < 8; o++)
+    for (int o = 0; o < 8; o++) {
         t->child[8 * id + o] = -1;
+        t->corder[8 * id + o] = -1;
+    }
     if (cnt == 1) {
         /* "a cell has ... one particle": a particle leaf */
         const int64_t p = t->work[lo];
@@ -379,9 +386,11 @@ static int64_t build_rec(or_tree *t, int64_t lo, int64_t cnt, int level,
                           ((t->q[3 * p + 2] >> b) & 1);
             c[o]++;
         }
+        int64_t base[8];
         off[0] = 0;
         for (int o = 1; o < 8; o++)
             off[o] = off[o - 1] + c[o - 1];
+        memcpy(base, off, sizeof(base));
         for (int64_t k = 0; k < cnt; k++) {   /* stable partition */
             const int64_t p = t->work[lo + k];
             const int o = (((t->q[3 * p] >> b) & 1) << 2) |
@@ -390,22 +399,41 @@ static int64_t build_rec(or_tree *t, int64_t lo, int64_t cnt, int level,
             t->tmp[lo + off[o]++] = p;
         }
         memcpy(t->work + lo, t->tmp + lo, (size_t)cnt * sizeof(int64_t));
-        int64_t start = lo;
-        for (int o = 0; o < 8; o++) {
-            if (c[o] == 0)
-                continue;
-            const int64_t ch = build_rec(t, start, c[o], level + 1,
+        /* the order the children are visited in: octant order, or the order
+         * of their Peano-Hilbert digit at this level (every particle of an
+         * aligned sub-cube has the same one) */
+        int vis[8], nv = 0;
+        for (int o = 0; o < 8; o++)
+            if (c[o] > 0)
+                vis[nv++] = o;
+        if (t->korder == 1) {
+            int dig[8];
+            for (int v = 0; v < nv; v++)
+                dig[v] = (int)((t->hkey[t->work[lo + base[vis[v]]]] >> (3 * b)) & 7u);
+            for (int v = 1; v < nv; v++)       /* insertion sort by digit */
+                for (int w = v; w > 0 && dig[w - 1] > dig[w]; w--) {
+                    const int td = dig[w], to = vis[w];
+                    dig[w] = dig[w - 1];
+                    vis[w] = vis[w - 1];
+                    dig[w - 1] = td;
+                    vis[w - 1] = to;
+                }
+        }
+        for (int v = 0; v < nv; v++) {
+            const int o = vis[v];
+            const int64_t ch = build_rec(t, lo + base[o], c[o], level + 1,
                                          2 * cx + ((o >> 2) & 1),
                                          2 * cy + ((o >> 1) & 1),
                                          2 * cz + (o & 1), id);
             if (ch < 0)
                 return -1;
             t->child[8 * id + o] = (int32_t)ch;
-            start += c[o];
+            t->corder[8 * id + v] = (int8_t)o;
         }
     }
     /* total mass and centre of mass (Sec. "Our GPU implementation"),
-     * folded over the children in octant order                           */
+     * folded over the children in the order they were visited (octant
+     * order for Morton keys)                                             */
     double M = 0.0, mx[3] = {0.0, 0.0, 0.0};
     int32_t nch = 0;
     for (int64_t ch = id + 1; ch < t->nnodes; ch = t->next[ch]) {
@@ -459,15 +487,22 @@ void or_tree_free(or_tree *t)
     free(t->l);
     free(t->s);
     free(t->comf);
+    free(t->hkey);
+    free(t->corder);
     free(t);
 }
 
-/* pos and mass must stay alive while the tree is used. */
-or_tree *or_tree_build(int64_t n, const double *pos, const float *mass)
+/* pos and mass must stay alive while the tree is used.  korder 0 visits
+ * children in octant order (leaves in Morton order), 1 in Peano-Hilbert
+ * order; the cells are the same either way.                               */
+or_tree *or_tree_build_order(int64_t n, const double *pos, const float *mass, int korder)
 {
     or_tree *t = (or_tree *)calloc(1, sizeof(or_tree));
-    if (!t || n < 0)
+    if (!t || n < 0 || korder < 0 || korder > 1) {
+        free(t);
         return NULL;
+    }
+    t->korder = korder;
     t->n = n;
     t->pos = pos;
     t->mass = mass;
@@ -483,6 +518,14 @@ or_tree *or_tree_build(int64_t n, const double *pos, const float *mass)
         return NULL;
     }
     or_quantize(n, pos, t->root, t->q);
+    if (korder == 1) {
+        t->hkey = (uint64_t *)malloc(nn * sizeof(uint64_t));
+        if (!t->hkey) {
+            or_tree_free(t);
+            return NULL;
+        }
+        or_hilbert_keys(n, t->q, t->hkey);
+    }
     for (int64_t i = 0; i < n; i++)
         t->work[i] = i;
     if (n > 0) {
@@ -496,6 +539,17 @@ or_tree *or_tree_build(int64_t n, const double *pos, const float *mass)
                 t->next[u] = -1;
     }
     return t;
+}
+
+or_tree *or_tree_build(int64_t n, const double *pos, const float *mass)
+{
+    return or_tree_build_order(n, pos, mass, 0);
+}
+
+/* the integer corner of every node at its level (zeros for particles) */
+void or_tree_corners(const or_tree *t, int32_t *corner)
+{
+    memcpy(corner, t->corner, (size_t)t->nnodes * 3 * sizeof(int32_t));
 }
 
 int64_t or_tree_nnodes(const or_tree *t) { return t->nnodes; }
@@ -553,9 +607,8 @@ static int64_t groups_rec(const or_tree *t, int64_t u, int64_t n_crit,
         }
         return g;
     }
-    for (int o = 0; o < 8; o++)
-        if (t->child[8 * u + o] >= 0)
-            g = groups_rec(t, t->child[8 * u + o], n_crit, gnode, g);
+    for (int v = 0; v < 8 && t->corder[8 * u + v] >= 0; v++)
+        g = groups_rec(t, t->child[8 * u + t->corder[8 * u + v]], n_crit, gnode, g);
     return g;
 }
 
@@ -635,7 +688,8 @@ static void emit(or_list *L, int64_t u)
     L->len++;
 }
 
-/* Fig. "treewalk": recursive, over sub-cells in octant order. */
+/* Fig. "treewalk": recursive, over sub-cells in the order they were built
+ * (octant order for Morton keys). */
 static void walk_rec(const or_tree *t, int64_t u, const float *box,
                      int64_t gfirst, float invth, or_list *L)
 {
@@ -652,9 +706,8 @@ static void walk_rec(const or_tree *t, int64_t u, const float *box,
             emit(L, u + 1 + k);
         return;
     }
-    for (int o = 0; o < 8; o++)
-        if (t->child[8 * u + o] >= 0)
-            walk_rec(t, t->child[8 * u + o], box, gfirst, invth, L);
+    for (int v = 0; v < 8 && t->corder[8 * u + v] >= 0; v++)
+        walk_rec(t, t->child[8 * u + t->corder[8 * u + v]], box, gfirst, invth, L);
 }
 
 /* Fig. "treewalk_iterative": the same walk on next/more pointers. */

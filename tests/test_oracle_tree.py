@@ -382,3 +382,85 @@ def test_hilbert_keys_nest_by_level(oracle_lib):
         q = (base[:, None, :] + off).reshape(-1, 3).astype(np.int32)
         top = oracle_lib.hilbert_keys(q) >> np.uint64(3 * (L - lv))
         assert np.all(top.reshape(40, 5) == top.reshape(40, 5)[:, :1])
+
+
+# ---- the oracle's tree in Peano-Hilbert order: the same octree, its nodes
+# visited in another order
+
+def _node_ids(T):
+    """A name for every node that does not depend on the visiting order:
+    (level, corner) for cells, the caller index for particles."""
+    e = T.export()
+    c = T.corners()
+    out = []
+    for u in range(T.nnodes):
+        if e["is_cell"][u]:
+            out.append(("c", int(e["level"][u]), *map(int, c[u])))
+        else:
+            out.append(("p", int(e["order"][e["first"][u]])))
+    return out
+
+
+@pytest.fixture(scope="module")
+def two_orders(oracle_lib):
+    pos, mass = clustered_small()
+    return (oracle_lib.Tree(pos, mass), oracle_lib.Tree(pos, mass, order="hilbert"))
+
+
+def test_hilbert_tree_has_the_same_cells_and_members(two_orders):
+    TM, TH = two_orders
+    assert TM.nnodes == TH.nnodes and TM.ncells == TH.ncells
+    em, eh = TM.export(), TH.export()
+    im, ih = _node_ids(TM), _node_ids(TH)
+    assert sorted(im) == sorted(ih)
+    where = {k: u for u, k in enumerate(im)}
+    for u, k in enumerate(ih):
+        v = where[k]
+        assert eh["count"][u] == em["count"][v] and eh["nchild"][u] == em["nchild"][v]
+        assert eh["l"][u] == em["l"][v]
+        mh = np.sort(eh["order"][eh["first"][u]: eh["first"][u] + eh["count"][u]])
+        mm = np.sort(em["order"][em["first"][v]: em["first"][v] + em["count"][v]])
+        assert np.array_equal(mh, mm)
+        # the masses and first moments are the same sums in another order
+        assert eh["M"][u] == pytest.approx(em["M"][v], rel=1e-14)
+        assert np.allclose(eh["com"][u], em["com"][v], rtol=0, atol=1e-13 * TM.L)
+
+
+def test_hilbert_leaf_order_is_sorted_hilbert_key_order(oracle_lib, two_orders):
+    """Depth-first leaf order = particles sorted by Peano-Hilbert key, ties
+    (particles in one depth-21 bucket) in input order."""
+    TM, TH = two_orders
+    e = TH.export()
+    k = oracle_lib.hilbert_keys(e["q"])
+    assert np.array_equal(e["order"], np.argsort(k, kind="stable"))
+    assert not np.array_equal(e["order"], TM.export()["order"])   # a different order
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.6, 1.0])
+def test_hilbert_lists_walk_the_same_cells(two_orders, theta):
+    """The recursive and iterative walks agree in Hilbert order too, and a
+    group's list names the same cells and particles as in Morton order."""
+    TM, TH = two_orders
+    im, ih = _node_ids(TM), _node_ids(TH)
+    gm, bm, om, lm = TM.all_lists(32, theta)
+    gh, bh, oh, lh = TH.all_lists(32, theta)
+    assert sorted(im[u] for u in gm) == sorted(ih[u] for u in gh)
+    where = {im[u]: g for g, u in enumerate(gm)}
+    rng = np.random.default_rng(3)
+    for g in rng.choice(len(gh), min(30, len(gh)), replace=False):
+        lst = lh[oh[g]: oh[g + 1]]
+        assert np.array_equal(lst, TH.walk_group(gh[g], bh[g], theta, mode=0))
+        assert np.all(np.diff(lst) > 0)
+        gmo = where[ih[gh[g]]]
+        assert np.array_equal(bh[g], bm[gmo])
+        assert sorted(ih[u] for u in lst) == sorted(im[u] for u in lm[om[gmo]: om[gmo + 1]])
+
+
+def test_hilbert_forces_match_morton(two_orders):
+    TM, TH = two_orders
+    am, pm, ppm, pcm = TM.forces(32, 0.6, 1e-3)
+    ah, ph, pph, pch = TH.forces(32, 0.6, 1e-3)
+    assert (ppm, pcm) == (pph, pch)
+    scale = np.linalg.norm(am, axis=1).max()
+    assert np.abs(ah - am).max() <= 1e-12 * scale
+    assert np.abs(ph - pm).max() <= 1e-12 * np.abs(pm).max()
