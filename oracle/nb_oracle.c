@@ -14,7 +14,10 @@
  *     particle, split recursively into eight sub-cells until a cell holds one
  *     particle;  cells carry total mass and centre of mass (Sec. "Our GPU
  *     implementation"), the cell size l and the offset s of Eq. (mac);
- *   - the depth-first (Morton) particle order of Sec. "Test and Optimization";
+ *   - the depth-first (Morton) particle order of Sec. "Test and Optimization",
+ *     and, as an option, the Peano-Hilbert order that the same section names
+ *     as the better one for locality (the same cells, children visited in
+ *     the curve's order);
  *   - next/more threading of the tree (Sec. "Our GPU implementation", after
  *     Makino 1990) by a depth-first pass;
  *   - the recursive walk of Fig. "treewalk" and the iterative walk of Fig.
@@ -32,8 +35,10 @@
  *               the scale S = 2^21 / L rounded once in FP64;
  *               depth is capped at 21 levels: a level-21 cell holding several
  *               particles keeps them as particle children, in input order;
- *   octant      digit = 4*bit_x + 2*bit_y + bit_z, children in digit order;
- *   moments     M and sum(m x) folded over children in octant order in FP64;
+ *   octant      digit = 4*bit_x + 2*bit_y + bit_z, children in digit order
+ *               (in the Peano-Hilbert option: in the order of the curve's
+ *               digit at the child level);
+ *   moments     M and sum(m x) folded over children in visiting order in FP64;
  *               COM = sum(m x) / M (the geometric centre when M == 0);
  *   l, s        l = L / 2^level (full side), s = |COM - geometric centre|,
  *               both rounded to FP32;
