@@ -64,6 +64,10 @@ def lib():
             L.or_tree_build_order.restype = vp
             L.or_tree_build_order.argtypes = [i64, vp, vp, C.c_int]
             L.or_tree_corners.argtypes = [vp, vp]
+            L.or_neighbours.restype = i64
+            L.or_neighbours.argtypes = [vp, f64, C.c_int, i64, vp, vp, i64]
+            L.or_neighbours_brute.restype = i64
+            L.or_neighbours_brute.argtypes = [i64, vp, f64, vp, vp, i64]
             L.or_tree_free.argtypes = [vp]
             L.or_tree_nnodes.restype = i64
             L.or_tree_nnodes.argtypes = [vp]
@@ -158,6 +162,18 @@ def morton_keys(q):
     return k
 
 
+def neighbours_brute(pos, h):
+    """The definition of the neighbour sets, every pair tested: (offsets,
+    caller indices in ascending order)."""
+    pos = _pos(pos)
+    n = pos.shape[0]
+    off = np.zeros(n + 1, np.int64)
+    tot = int(lib().or_neighbours_brute(n, _ptr(pos), float(h), _ptr(off), None, 0))
+    idx = np.zeros(max(tot, 1), np.int64)
+    lib().or_neighbours_brute(n, _ptr(pos), float(h), _ptr(off), _ptr(idx), tot)
+    return off, idx[:tot]
+
+
 def hilbert_keys(q):
     """Peano-Hilbert keys (63 bits, 21 levels) of grid coordinates."""
     q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1, 3)
@@ -200,6 +216,19 @@ class Tree:
         c = np.zeros((self.nnodes, 3), np.int32)
         lib().or_tree_corners(self._h, _ptr(c))
         return c
+
+    def neighbours(self, h, group_form=False, n_crit=64):
+        """Fixed-radius neighbours by the general treewalk: (offsets n+1,
+        sorted caller indices), j != i with |x_j - x_i| <= h in FP64.
+        group_form walks once per group of <= n_crit particles."""
+        off = np.zeros(self.n + 1, np.int64)
+        tot = int(lib().or_neighbours(self._h, float(h), 1 if group_form else 0,
+                                      int(n_crit), _ptr(off), None, 0))
+        assert tot >= 0
+        idx = np.zeros(max(tot, 1), np.int64)
+        lib().or_neighbours(self._h, float(h), 1 if group_form else 0, int(n_crit),
+                            _ptr(off), _ptr(idx), tot)
+        return off, idx[:tot]
 
     def export(self):
         if self._exp is None:

@@ -827,6 +827,212 @@ static float rel32(double x, float c)
     return d + lo;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Neighbour search by the general treewalk (Sec. "General Treewalk", Fig.
+ * "general_treewalk"): the descent of the force walk with another distance
+ * test and no particle-cell term.  The neighbours of particle i are the
+ * j != i with |x_j - x_i|^2 <= h^2, the squared distance summed x, y, z in
+ * FP64 from the FP64 positions.  distance_test skips a cell whose cube,
+ * widened by 1e-9 L (far more than the rounding of the grid), lies farther
+ * than h from the target (per-particle form) or from the group's FP64
+ * bounding box (group form); proc_particle applies the definition.        */
+
+static double pair_d2(const double *a, const double *b)
+{
+    const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    return (dx * dx + dy * dy) + dz * dz;
+}
+
+/* squared gap between a cell's cube and the box [lo, hi] */
+static double cube_gap2(const or_tree *t, int64_t u, const double *lo, const double *hi)
+{
+    const double side = ldexp(t->root[3], -t->level[u]);
+    double d2 = 0.0;
+    for (int k = 0; k < 3; k++) {
+        const double c0 = t->root[4 + k] + (double)t->corner[3 * u + k] * side;
+        const double c1 = c0 + side;
+        double gap = 0.0;
+        if (lo[k] > c1)
+            gap = lo[k] - c1;
+        else if (c0 > hi[k])
+            gap = c0 - hi[k];
+        d2 += gap * gap;
+    }
+    return d2;
+}
+
+typedef struct {
+    int64_t *cand, len, cap;   /* candidate sorted slots */
+} or_cand;
+
+static int cand_push(or_cand *c, int64_t slot)
+{
+    if (c->len == c->cap) {
+        const int64_t nc = c->cap ? 2 * c->cap : 256;
+        int64_t *p = (int64_t *)realloc(c->cand, (size_t)nc * sizeof(int64_t));
+        if (!p)
+            return -1;
+        c->cand = p;
+        c->cap = nc;
+    }
+    c->cand[c->len++] = slot;
+    return 0;
+}
+
+/* the general treewalk: every particle of every cell that passes the test */
+static int near_rec(const or_tree *t, int64_t u, const double *lo, const double *hi,
+                    double reach2, or_cand *c)
+{
+    if (!t->is_cell[u])
+        return cand_push(c, t->first[u]);
+    if (cube_gap2(t, u, lo, hi) > reach2)
+        return 0;                                   /* too far: skipped */
+    if (t->level[u] == OR_LEVELS) {
+        for (int64_t k = 0; k < t->count[u]; k++)
+            if (cand_push(c, t->first[u] + k))
+                return -1;
+        return 0;
+    }
+    for (int v = 0; v < 8 && t->corder[8 * u + v] >= 0; v++)
+        if (near_rec(t, t->child[8 * u + t->corder[8 * u + v]], lo, hi, reach2, c))
+            return -1;
+    return 0;
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    const int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* One target's neighbours from a candidate list, as sorted caller indices.
+ * Returns the count; writes out[0 .. min(count, cap)).                    */
+static int64_t filter(const or_tree *t, int64_t i, double h2, const or_cand *c,
+                      int64_t *out, int64_t cap)
+{
+    int64_t m = 0;
+    for (int64_t k = 0; k < c->len; k++) {
+        const int64_t j = t->order[c->cand[k]];
+        if (j != i && pair_d2(t->pos + 3 * i, t->pos + 3 * j) <= h2) {
+            if (m < cap)
+                out[m] = j;
+            m++;
+        }
+    }
+    if (out && m <= cap)
+        qsort(out, (size_t)m, sizeof(int64_t), cmp_i64);
+    return m;
+}
+
+/* Neighbours of every particle (caller order) in CSR form: off has n + 1
+ * entries, idx the sorted caller indices of each target's neighbours (up to
+ * cap in all; NULL to count).  group_form 0 walks once per particle, 1 once
+ * per group of <= n_crit particles with the group's bounding box.  Returns
+ * the total, or -1 on allocation failure.                                 */
+int64_t or_neighbours(const or_tree *t, double h, int group_form, int64_t n_crit,
+                      int64_t *off, int64_t *idx, int64_t cap)
+{
+    const int64_t n = t->n;
+    const double h2 = h * h;
+    const double reach = h + 1e-9 * t->root[3];
+    const double reach2 = reach * reach;
+    int64_t *cnt = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    if (!cnt)
+        return -1;
+    or_cand c = {NULL, 0, 0};
+    int rc = 0;
+    for (int pass = 0; pass < 2 && rc == 0; pass++) {
+        if (pass == 1) {           /* offsets from the counts */
+            int64_t tot = 0;
+            for (int64_t i = 0; i < n; i++) {
+                off[i] = tot;
+                tot += cnt[i];
+            }
+            off[n] = tot;
+            if (!idx)
+                break;
+        }
+        if (!group_form) {
+            for (int64_t i = 0; i < n && rc == 0; i++) {
+                c.len = 0;
+                const double *x = t->pos + 3 * i;
+                if (n > 0 && near_rec(t, 0, x, x, reach2, &c)) {
+                    rc = -1;
+                    break;
+                }
+                if (pass == 0)
+                    cnt[i] = filter(t, i, h2, &c, NULL, 0);
+                else if (off[i + 1] <= cap)
+                    filter(t, i, h2, &c, idx + off[i], cnt[i]);
+            }
+        } else if (n > 0) {
+            const int64_t G = groups_rec(t, 0, n_crit, NULL, 0);
+            int64_t *gnode = (int64_t *)malloc((size_t)G * sizeof(int64_t));
+            if (!gnode) {
+                rc = -1;
+                break;
+            }
+            groups_rec(t, 0, n_crit, gnode, 0);
+            for (int64_t g = 0; g < G && rc == 0; g++) {
+                const int64_t u = gnode[g];
+                double lo[3], hi[3];
+                for (int k = 0; k < 3; k++) {
+                    lo[k] = INFINITY;
+                    hi[k] = -INFINITY;
+                }
+                for (int64_t s2 = t->first[u]; s2 < t->first[u] + t->count[u]; s2++)
+                    for (int k = 0; k < 3; k++) {
+                        const double x = t->pos[3 * t->order[s2] + k];
+                        if (x < lo[k])
+                            lo[k] = x;
+                        if (x > hi[k])
+                            hi[k] = x;
+                    }
+                c.len = 0;
+                if (near_rec(t, 0, lo, hi, reach2, &c)) {
+                    rc = -1;
+                    break;
+                }
+                for (int64_t s2 = t->first[u]; s2 < t->first[u] + t->count[u]; s2++) {
+                    const int64_t i = t->order[s2];
+                    if (pass == 0)
+                        cnt[i] = filter(t, i, h2, &c, NULL, 0);
+                    else if (off[i + 1] <= cap)
+                        filter(t, i, h2, &c, idx + off[i], cnt[i]);
+                }
+            }
+            free(gnode);
+        }
+    }
+    int64_t tot = 0;
+    for (int64_t i = 0; i < n; i++)
+        tot += cnt[i];
+    free(c.cand);
+    free(cnt);
+    return rc ? -1 : tot;
+}
+
+/* The definition itself, for the tests: every pair, same distance formula. */
+int64_t or_neighbours_brute(int64_t n, const double *pos, double h, int64_t *off,
+                            int64_t *idx, int64_t cap)
+{
+    const double h2 = h * h;
+    int64_t tot = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (off)
+            off[i] = tot;
+        for (int64_t j = 0; j < n; j++)
+            if (j != i && pair_d2(pos + 3 * i, pos + 3 * j) <= h2) {
+                if (idx && tot < cap)
+                    idx[tot] = j;
+                tot++;
+            }
+    }
+    if (off)
+        off[n] = tot;
+    return tot;
+}
+
 int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
                    const float *theta_g, double eps, int64_t nsel,
                    const int64_t *gsel, double *acc, double *pot,
