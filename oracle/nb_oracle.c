@@ -26,6 +26,8 @@
  *     "Oct-tree Method with GRAPE"), plus the per-particle walk of Fig.
  *     "treegpu";
  *   - forces over interaction lists in FP64;
+ *   - fixed-radius neighbours by the general treewalk of Sec. "General
+ *     Treewalk" (and by brute force, the definition);
  *   - a kick-drift-kick leapfrog for "integrate orbits" (Sec. Introduction).
  *
  * Readings where the paper is silent (the same ones the CUDA path follows):
