@@ -64,6 +64,10 @@ def lib():
             L.or_tree_build_order.restype = vp
             L.or_tree_build_order.argtypes = [i64, vp, vp, C.c_int]
             L.or_tree_corners.argtypes = [vp, vp]
+            L.or_tree_export_quad.restype = C.c_int
+            L.or_tree_export_quad.argtypes = [vp, vp]
+            L.or_tree_forces_quad.restype = C.c_int
+            L.or_tree_forces_quad.argtypes = [vp, i64, f64, f64, vp, vp, vp, vp]
             L.or_neighbours.restype = i64
             L.or_neighbours.argtypes = [vp, f64, C.c_int, i64, vp, vp, i64]
             L.or_neighbours_brute.restype = i64
@@ -216,6 +220,24 @@ class Tree:
         c = np.zeros((self.nnodes, 3), np.int32)
         lib().or_tree_corners(self._h, _ptr(c))
         return c
+
+    def quadrupoles(self):
+        """Traceless quadrupole of every node about its centre of mass,
+        (xx, yy, zz, xy, xz, yz), FP64; zeros for particles."""
+        Q = np.zeros((self.nnodes, 6))
+        assert lib().or_tree_export_quad(self._h, _ptr(Q)) == 0
+        return Q
+
+    def forces_quad(self, n_crit, theta, eps):
+        """forces() with the quadrupole term of every accepted cell:
+        (acc, pot, npp, npc)."""
+        acc = np.full((self.n, 3), np.nan)
+        pot = np.full(self.n, np.nan)
+        npp, npc = C.c_int64(0), C.c_int64(0)
+        rc = lib().or_tree_forces_quad(self._h, int(n_crit), float(theta), float(eps),
+                                       _ptr(acc), _ptr(pot), C.byref(npp), C.byref(npc))
+        assert rc == 0
+        return acc, pot, int(npp.value), int(npc.value)
 
     def neighbours(self, h, group_form=False, n_crit=64):
         """Fixed-radius neighbours by the general treewalk: (offsets n+1,

@@ -25,7 +25,8 @@
  *     once and shares one interaction list, the GRAPE list idea of Sec.
  *     "Oct-tree Method with GRAPE"), plus the per-particle walk of Fig.
  *     "treegpu";
- *   - forces over interaction lists in FP64;
+ *   - forces over interaction lists in FP64 (optionally with the cells'
+ *     quadrupole moments);
  *   - fixed-radius neighbours by the general treewalk of Sec. "General
  *     Treewalk" (and by brute force, the definition);
  *   - a kick-drift-kick leapfrog for "integrate orbits" (Sec. Introduction).
@@ -291,6 +292,8 @@ typedef struct {
     uint64_t *hkey;      /* Peano-Hilbert key per particle (korder 1)        */
     int8_t *corder;      /* cells: octants of the children in visiting order,
                           * -1 past the last                                 */
+    double *Q;           /* traceless quadrupole per node about its centre of
+                          * mass (xx, yy, zz, xy, xz, yz), made on demand     */
 } or_tree;
 
 static int grow(or_tree *t)
@@ -496,6 +499,7 @@ void or_tree_free(or_tree *t)
     free(t->comf);
     free(t->hkey);
     free(t->corder);
+    free(t->Q);
     free(t);
 }
 
@@ -1035,10 +1039,80 @@ int64_t or_neighbours_brute(int64_t n, const double *pos, double h, int64_t *off
     return tot;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Quadrupole moments ("any high order moment" of Sec. "Oct-tree Method"),
+ * straight from the definition: for every cell, over its members k,
+ *   Q_ab = sum_k m_k (3 d_a d_b - |d|^2 delta_ab),  d = x_k - COM,
+ * in FP64 (particles: Q = 0).  The particle-cell term with it, softened like
+ * Eq. (gravity) (R^2 = |r|^2 + eps^2, r = x_i - COM):
+ *   phi += -(1/2) r.Q.r / R^5,   a += Q r / R^5 - (5/2) (r.Q.r) r / R^7.   */
+int or_tree_quadrupoles(or_tree *t)
+{
+    if (t->Q)
+        return 0;
+    t->Q = (double *)calloc((size_t)(t->nnodes > 0 ? t->nnodes : 1) * 6, sizeof(double));
+    if (!t->Q)
+        return -1;
+    for (int64_t u = 0; u < t->nnodes; u++) {
+        if (!t->is_cell[u])
+            continue;
+        double q[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t s2 = t->first[u]; s2 < t->first[u] + t->count[u]; s2++) {
+            const int64_t j = t->order[s2];
+            const double m = (double)t->mass[j];
+            double d[3];
+            for (int k = 0; k < 3; k++)
+                d[k] = t->pos[3 * j + k] - t->com[3 * u + k];
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            q[0] += m * (3.0 * d[0] * d[0] - d2);
+            q[1] += m * (3.0 * d[1] * d[1] - d2);
+            q[2] += m * (3.0 * d[2] * d[2] - d2);
+            q[3] += m * 3.0 * d[0] * d[1];
+            q[4] += m * 3.0 * d[0] * d[2];
+            q[5] += m * 3.0 * d[1] * d[2];
+        }
+        memcpy(t->Q + 6 * u, q, sizeof(q));
+    }
+    return 0;
+}
+
+int or_tree_export_quad(or_tree *t, double *Q)
+{
+    if (or_tree_quadrupoles(t))
+        return -1;
+    memcpy(Q, t->Q, (size_t)t->nnodes * 6 * sizeof(double));
+    return 0;
+}
+
+static int tree_forces(const or_tree *t, int64_t n_crit, double theta,
+                       const float *theta_g, double eps, int64_t nsel,
+                       const int64_t *gsel, double *acc, double *pot,
+                       double *amag, int64_t *npp, int64_t *npc, int coords32,
+                       int quad);
+
 int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
                    const float *theta_g, double eps, int64_t nsel,
                    const int64_t *gsel, double *acc, double *pot,
                    double *amag, int64_t *npp, int64_t *npc, int coords32)
+{
+    return tree_forces(t, n_crit, theta, theta_g, eps, nsel, gsel, acc, pot, amag, npp,
+                       npc, coords32, 0);
+}
+
+/* the same with the quadrupole term of accepted cells (FP64 coordinates) */
+int or_tree_forces_quad(or_tree *t, int64_t n_crit, double theta, double eps,
+                        double *acc, double *pot, int64_t *npp, int64_t *npc)
+{
+    if (or_tree_quadrupoles(t))
+        return -1;
+    return tree_forces(t, n_crit, theta, NULL, eps, 0, NULL, acc, pot, NULL, npp, npc, 0, 1);
+}
+
+static int tree_forces(const or_tree *t, int64_t n_crit, double theta,
+                       const float *theta_g, double eps, int64_t nsel,
+                       const int64_t *gsel, double *acc, double *pot,
+                       double *amag, int64_t *npp, int64_t *npc, int coords32,
+                       int quad)
 {
     const int64_t G = or_groups(t, n_crit, NULL);
     int64_t *gnode = (int64_t *)malloc((size_t)(G > 0 ? G : 1) * sizeof(int64_t));
@@ -1119,6 +1193,22 @@ int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
                     az += mr3 * dz;
                     p -= mv * rinv;
                     am += mr3 * sqrt(dx * dx + dy * dy + dz * dz);
+                    if (quad && t->is_cell[v]) {
+                        /* r = x_i - COM = -(dx, dy, dz) */
+                        const double *Q = t->Q + 6 * v;
+                        const double rx = -dx, ry = -dy, rz = -dz;
+                        const double qx = Q[0] * rx + Q[3] * ry + Q[4] * rz;
+                        const double qy = Q[3] * rx + Q[1] * ry + Q[5] * rz;
+                        const double qz = Q[4] * rx + Q[5] * ry + Q[2] * rz;
+                        const double rqr = rx * qx + ry * qy + rz * qz;
+                        const double ri2 = rinv * rinv;
+                        const double ri5 = ri2 * ri2 * rinv;
+                        const double ri7 = ri5 * ri2;
+                        ax += qx * ri5 - 2.5 * rqr * rx * ri7;
+                        ay += qy * ri5 - 2.5 * rqr * ry * ri7;
+                        az += qz * ri5 - 2.5 * rqr * rz * ri7;
+                        p -= 0.5 * rqr * ri5;
+                    }
                 }
                 if (amag)
                     amag[i] = am;
