@@ -219,6 +219,16 @@ def job_rate(units, ms, ws):
     return allreduce_sum(float(units), ws) / (ms_max / 1e3), ms_max
 
 
+def workload_config(name, n, w, ws):
+    """The workload both arms run, with the same keys and values."""
+    return {"workload": name, "n": n, "theta": w["theta"], "eps": w["eps"],
+            "n_crit": w["n_crit"], "dt": w["dt"],
+            "step": "KDK leapfrog: tree build + group walk + force + kicks/drift",
+            "l2": "inputs larger than L2 (positions + velocities 138 MB; interaction lists "
+                  "about 2 GB per step)",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "1 replica"}
+
+
 # ----------------------------------------------------------------- CPU oracle
 def cpu_oracle_rate(ps, w, seconds, seed=7, name=WORKLOAD):
     """Force evaluations/s of the CPU oracle (tree build + group walk + FP64
@@ -307,8 +317,9 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": ps.n, "theta": w["theta"], "eps": w["eps"],
-                   "n_crit": w["n_crit"], "parallelism": "host cores (oracle)"},
+        "config": workload_config(args.workload, ps.n, w, ws),
+        "run": {"precision": "fp64 (oracle)", "force_path": "lists (oracle)",
+                "launch": "host cores (oracle)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle",
                          "sample": f"per step: full tree build (charged pro rata) + walk and "
@@ -479,13 +490,6 @@ def run_ours(args, ws, rank, local):
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
                 "frac_at_sampled_clock": (achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
                                           if clocks.get("sm_mhz") else None)}
-    # the SM clock the measured bf16 GEMM settled at under the power cap; this
-    # kernel runs far below the cap (see "clocks"), so the max-clock fraction
-    # above is the one that describes it
-    gemm_mhz = (pk.get("clocks_under_load") or {}).get("sm_mhz_median")
-    if gemm_mhz:
-        roofline["frac_at_gemm_load_clock"] = achieved / (sms * 128 * gemm_mhz * 1e6 / 1e12)
-        roofline["gemm_load_clock_mhz"] = gemm_mhz
     # the walk (with group formation): interaction-list bytes it writes per
     # call against the measured copy bandwidth; it is latency-bound
     walk_ms, walk_calls = timing["walk"]
@@ -511,18 +515,15 @@ def run_ours(args, ws, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "theta": w["theta"], "eps": w["eps"],
-                       "n_crit": w["n_crit"], "dt": dt, "precision": args.precision,
-                       "force_path": "fused walk+force" if args.fused else "lists",
-                       "launch": ((f"eager (graph capture failed: {graph_failed})"
-                                   if graph_failed else
-                                   "eager: every kernel launched from the host") if args.eager
-                                  else f"CUDA graph of {graph_steps} KDK steps, launched "
-                                       f"{graph_runs}x"),
-                       "step": "KDK leapfrog: tree build + group walk + force + kicks/drift",
-                       "l2": "inputs larger than L2 (positions+velocities 138 MB, lists "
-                             f"{st1['list_entries'] * 20 / 1e9:.2f} GB per step)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "config": workload_config(args.workload, n, w, ws),
+            "run": {"precision": args.precision,
+                    "force_path": "fused walk+force" if args.fused else "lists",
+                    "launch": ((f"eager (graph capture failed: {graph_failed})"
+                                if graph_failed else
+                                "eager: every kernel launched from the host") if args.eager
+                               else f"CUDA graph of {graph_steps} KDK steps, launched "
+                                    f"{graph_runs}x"),
+                    "lists_gb_per_step": st1["list_entries"] * 20 / 1e9},
             "gflops_38": value * FLOPS_CONVENTION / 1e9,
             "interactions_per_step": inter / args.steps,
             "particle_forces_per_s": ws * n * args.steps / (ms_max / 1e3),

@@ -372,21 +372,26 @@ int nb_copy_list(nb_ctx *ctx, int64_t group, int32_t *entries_host, float *xm_ho
                  int64_t cap, int64_t *len_host);
 
 /* Morton order without any device allocation, for callers that cannot call
- * cudaMalloc: it synchronises the device and is not allowed during stream
- * capture, and where another allocator already holds most of the device
- * memory it can fail.  The paper has no counterpart; this is the first part
- * of nb_build_tree (root cube, 63-bit Morton keys, stable radix sort) run on
+ * cudaMalloc (cudaFree synchronises the whole device, and where another
+ * allocator already holds most of the device memory a raw cudaMalloc can
+ * fail).  The paper has no counterpart; this is the first part of
+ * nb_build_tree (root cube, 63-bit Morton keys, stable radix sort) run on
  * caller buffers, with its scratch in one static device array of about
  * 12.9 MB that every GPU loading the library keeps until the process exits.
  * pos_dev: n x 3 FP64 (caller order).  keys_dev: n uint64, receives the
  * sorted keys.  perm_dev: n int32, receives sorted slot -> caller index.
+ * All three must be on the current device.
  * n <= NB_NOALLOC_MAX_N (1,048,576), else NB_ERR_INVALID_ARG with nothing
- * done.  The first call on each device looks up the scratch address on the
- * current device; make that first call before any stream capture.  The call
- * queues its work on `stream` and synchronises it before returning; it
- * returns NB_ERR_NONFINITE for a NaN or infinite coordinate.  All calls
- * share the scratch array and it keeps the last call's contents (each call
- * clears what it needs cleared); calls that overlap on the GPU race. */
+ * done.  The call queues its work on `stream` and synchronises that stream
+ * before returning (to read its error word); it returns NB_ERR_NONFINITE for
+ * a NaN or infinite coordinate.  The first call on each device also looks up
+ * the scratch array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it for the life of the process: make that first call
+ * before any stream capture begins, since a lookup while another thread
+ * captures in global mode can invalidate that capture, and do not call the
+ * entry point after a cudaDeviceReset of the device.  All calls share the
+ * scratch array and it keeps the last call's contents (each call clears what
+ * it needs cleared); calls that overlap on the GPU race. */
 #define NB_NOALLOC_MAX_N (1 << 20)
 int nb_morton_order_noalloc(const double *pos_dev, int64_t n, uint64_t *keys_dev,
                             int32_t *perm_dev, void *stream);

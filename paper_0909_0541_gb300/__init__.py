@@ -473,14 +473,25 @@ def direct_sum(pos, mass, eps, targets=None, stream=None):
 def morton_order_noalloc(pos, keys_out, perm_out, stream=None):
     """Sorted Morton keys and sorted slot -> caller index for n <= NOALLOC_MAX_N
     particles, computed without any device allocation (the library's static
-    scratch); keys_out (n,) int64 holding uint64 bits, perm_out (n,) int32."""
+    scratch); keys_out (n,) int64 holding uint64 bits, perm_out (n,) int32.
+    pos, keys_out and perm_out must be on one device; the call runs with that
+    device current, on `stream` (default: that device's current stream)."""
     import torch
     n = int(pos.shape[0])
-    _check(_lib.nb_morton_order_noalloc(_dptr(pos, torch.float64, 3, "pos"), n,
-                                        _dptr(keys_out, torch.int64, None, "keys_out"),
-                                        _dptr(perm_out, torch.int32, None, "perm_out"),
-                                        _stream_handle(stream)),
-           "nb_morton_order_noalloc")
+    for t, name, dt in ((keys_out, "keys_out", torch.int64), (perm_out, "perm_out", torch.int32)):
+        if not isinstance(t, torch.Tensor) or t.dim() != 1 or int(t.shape[0]) != n:
+            raise ValueError(f"{name} must be a 1-D tensor of {n} elements")
+    pp = _dptr(pos, torch.float64, 3, "pos")
+    kp = _dptr(keys_out, torch.int64, None, "keys_out")
+    qp = _dptr(perm_out, torch.int32, None, "perm_out")
+    if keys_out.device != pos.device or perm_out.device != pos.device:
+        raise ValueError("pos, keys_out and perm_out must be on the same device")
+    with torch.cuda.device(pos.device):
+        s = stream if stream is not None else torch.cuda.current_stream(pos.device)
+        if s.device != pos.device:
+            raise ValueError("stream must belong to the tensors' device")
+        _check(_lib.nb_morton_order_noalloc(pp, n, kp, qp, s.cuda_stream),
+               "nb_morton_order_noalloc")
 
 
 # ---------------------------------------------------------------- learned theta

@@ -3,9 +3,9 @@
 // runs first, with every scratch buffer taken from one file-scope device
 // array instead of a context.
 //
-// Who needs this: code that may not call cudaMalloc.  cudaMalloc/cudaFree
-// synchronise the whole device and are not allowed while a stream is being
-// captured, and in a process where another allocator (for example a deep-
+// Who needs this: code that may not call cudaMalloc.  cudaFree synchronises
+// the whole device, which a caller in the middle of other streams' work may
+// not allow, and in a process where another allocator (for example a deep-
 // learning framework's caching allocator) has already reserved most of the
 // device memory a raw cudaMalloc can fail.  Such callers hand in their
 // inputs and outputs and get the sort order back with no allocation.
@@ -14,11 +14,14 @@
 // the process runs (NB_NOALLOC_SCRATCH_BYTES, about 12.9 MB).  Host code
 // cannot use the array's name as a device address, so the first call on each
 // device looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it.  All calls share the array and it keeps the last
+// current) and caches it for the life of the process; a cudaDeviceReset of
+// that device invalidates the cached address, so the entry point must not be
+// called again after one.  All calls share the array and it keeps the last
 // call's contents: the error word is cleared at the start of each call and
 // every other buffer is fully written before it is read.  Calls that overlap
 // on the GPU (several host threads, or streams that run concurrently) race on
-// the array.
+// the array.  Each call ends by synchronising its stream, to read the error
+// word.
 #include <mutex>
 
 #include "nb_internal.cuh"

@@ -33,3 +33,21 @@ def test_error_strings():
     for code in range(-8, 1):
         assert nb._lib.nb_error_string(code) != b"unknown error"
         assert code == 0 or code in nb.NB_ERR
+
+
+def test_noalloc_rejects_short_outputs_before_any_call():
+    """The wrapper of nb_morton_order_noalloc checks that both outputs hold n
+    elements before it reaches the library (host tensors suffice: the check
+    raises before any pointer is taken or any kernel launched)."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    import paper_0909_0541_gb300 as nb
+    pos = torch.zeros((10, 3), dtype=torch.float64)
+    good_k = torch.empty(10, dtype=torch.int64)
+    good_p = torch.empty(10, dtype=torch.int32)
+    with pytest.raises(ValueError, match="keys_out"):
+        nb.morton_order_noalloc(pos, torch.empty(9, dtype=torch.int64), good_p)
+    with pytest.raises(ValueError, match="perm_out"):
+        nb.morton_order_noalloc(pos, good_k, torch.empty(9, dtype=torch.int32))
+    with pytest.raises(ValueError, match="keys_out"):
+        nb.morton_order_noalloc(pos, torch.empty((10, 1), dtype=torch.int64), good_p)
