@@ -671,6 +671,106 @@ def run_learned(args, ws, rank, local):
     ctx.close()
 
 
+# ----------------------------------------------------------------- tree vs brute force
+def run_crossover(args, ws, rank, local):
+    """T_total of one force evaluation against N on a uniform random sphere
+    (Sec. "Test and Optimization", Tables bench2 and Fig. time): the tree
+    (build + group walk + force, theta 0.6, the best n_crit of 32/64/128 at
+    each N) against the FP32 brute force (nb_direct_f32), both on the
+    library's stream with CUDA events, L2 flushed before every repetition;
+    the crossover N is interpolated in log N where the two times cross."""
+    import torch
+
+    import nbsynth
+    import paper_0909_0541_gb300 as nb
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    theta, eps, reps = 0.6, 1.0 / 64, 7
+    sizes = [1000, 2000, 4000, 8000, 16000, 32000, 64000, 128000, 256000]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    rows = []
+
+    def timed(fn):
+        out = []
+        for _ in range(reps):
+            flush.fill_(1)
+            stream.wait_stream(torch.cuda.current_stream(dev))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    for n in sizes:
+        ps = nbsynth.uniform_sphere(n, nbsynth.BASE_SEED + 20 + n)
+        pos = torch.from_numpy(ps.pos).to(dev)
+        mass = torch.from_numpy(ps.mass).to(dev)
+        torch.cuda.synchronize()
+        acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        pot = torch.empty(n, dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            work = torch.empty(nb.direct_f32_workspace_size(n), dtype=torch.uint8, device=dev)
+            bacc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            bpot = torch.empty(n, dtype=torch.float32, device=dev)
+            nb.direct_f32(pos, mass, eps, "fp32", bacc, bpot, work, stream)   # warm-up
+            t_brute = timed(lambda: nb.direct_f32(pos, mass, eps, "fp32", bacc, bpot, work,
+                                                   stream))
+            best = None
+            for n_crit in (32, 64, 128):
+                ctx = nb.NBody(n, eps=eps, theta=theta, n_crit=n_crit, stream=stream)
+                ctx.build_tree(pos, mass)          # synchronising: sizes the list storage
+                ctx.walk_groups(theta, n_crit)
+                ctx.forces(eps, acc, pot)
+                ctx.set_sync_checks(False)
+
+                def tree():
+                    ctx.build_tree(pos, mass)
+                    ctx.walk_groups(theta, n_crit)
+                    ctx.forces(eps, acc, pot)
+                t = timed(tree)
+                ctx.sync_status()
+                st = ctx.stats()
+                if best is None or t < best[0]:
+                    best = (t, n_crit, st["n_pp"] + st["n_pc"])
+                ctx.close()
+            # accuracy of this tree evaluation against the brute force
+            ctx = nb.NBody(n, eps=eps, theta=theta, n_crit=best[1], stream=stream)
+            ctx.build_tree(pos, mass)
+            ctx.walk_groups(theta, best[1])
+            ctx.forces(eps, acc, pot)
+            ctx.close()
+            torch.cuda.synchronize()
+        d = ((acc.double() - bacc.double()).norm(dim=1) / bacc.double().norm(dim=1)).cpu().numpy()
+        rows.append({"n": n, "tree_ms": best[0], "tree_n_crit": best[1],
+                     "tree_interactions": int(best[2]), "brute_ms": t_brute,
+                     "brute_interactions": n * (n - 1),
+                     "brute_interactions_per_s": n * (n - 1) / (t_brute / 1e3),
+                     "tree_median_rel_err_vs_brute": float(np.median(d))})
+    cross = None
+    for a, b in zip(rows, rows[1:]):
+        ra, rb = a["tree_ms"] / a["brute_ms"], b["tree_ms"] / b["brute_ms"]
+        if ra >= 1.0 > rb:
+            f = np.log(ra) / (np.log(ra) - np.log(rb))
+            cross = float(np.exp(np.log(a["n"]) + f * (np.log(b["n"]) - np.log(a["n"]))))
+            break
+    if rows[0]["tree_ms"] < rows[0]["brute_ms"]:
+        cross = f"below {rows[0]['n']}"
+    line = {
+        "metric": "T_total of one force evaluation vs N: tree (theta 0.6) against FP32 brute force",
+        "value": cross, "unit": "N at the crossover", "n_gpus": 1, "steps": reps, "warmup": 1,
+        "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uniform sphere, radius 1, equal masses", "theta": theta,
+                   "eps": eps, "tree": "build + group walk + force, eager launches",
+                   "brute": "nb_direct_f32 (FP32, all pairs)",
+                   "l2": "flushed (256 MB write) before every repetition"},
+        "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------- batched systems
 def run_batch(args, ws, rank, local):
     """512 independent Plummer / Hernquist systems (N log-uniform in
@@ -754,6 +854,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batch512":
         run_batch(args, ws, rank, local)
+    elif args.workload == "crossover":
+        run_crossover(args, ws, rank, local)
     elif args.workload == "learned4.19m":
         run_learned(args, ws, rank, local)
     else:

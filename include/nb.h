@@ -246,6 +246,26 @@ int nb_direct_sum(const double *pos_dev, const float *mass_dev, int64_t n,
                   double eps, const int64_t *targets_dev, int64_t nt,
                   double *acc_dev, double *pot_dev, void *stream);
 
+/* Brute-force FP32 sum of Eq. (gravity) over every pair j != i, O(n^2): the
+ * paper's bare many-body kernel (Sec. "A Bare Many-body Performance on RV770
+ * GPU"), against which the tree method is timed (Sec. "Test and
+ * Optimization": the tree wins except for N < 10,000).  Positions are
+ * rounded once to FP32 (the representation that kernel works on); every
+ * interaction is the tree force kernel's 13-operation FP32 step with a MUFU
+ * rsqrt; a pair with r^2 + eps^2 == 0 contributes nothing.
+ * pos_dev: n x 3 FP64; mass_dev: n FP32; acc_dev: n x 3 FP32 (required);
+ * pot_dev: n FP32 (nullable); precision: NB_FP32 or NB_FP32_COMP (Kahan-
+ * compensated per 256-source tile); NB_FP64ACC is INVALID_ARG (use
+ * nb_direct_sum).  work_dev: caller-owned device workspace, 256-byte
+ * aligned, of at least nb_direct_f32_workspace_size(n) bytes for the current
+ * device (it holds the FP32 copy of the particles and the partial sums of
+ * the source parts).  Work is queued on `stream`; nothing synchronises.
+ * Results are in caller order and do not depend on scheduling. */
+size_t nb_direct_f32_workspace_size(int64_t n);
+int nb_direct_f32(const double *pos_dev, const float *mass_dev, int64_t n, float eps,
+                  float *acc_dev, float *pot_dev, int precision, void *work_dev,
+                  size_t work_bytes, void *stream);
+
 /* Per-phase device timing: with timing on, every phase is bracketed by CUDA
  * events recorded on cfg.stream.  nb_get_timing synchronises and returns,
  * per phase, the summed milliseconds and the number of calls since the last

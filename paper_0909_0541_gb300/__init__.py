@@ -38,6 +38,7 @@ EXPORTED = [
     "nb_copy_group_lengths", "nb_build_tree_batched", "nb_leapfrog_step_batched",
     "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune", "nb_selftest_wait",
     "nb_leapfrog_step_host", "nb_forces_fused", "nb_set_fused", "nb_set_feature_mode",
+    "nb_direct_f32", "nb_direct_f32_workspace_size",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -91,6 +92,9 @@ def _load():
     L.nb_leapfrog_step_host.argtypes = [vp, vp, vp, vp, i64, C.c_double]
     L.nb_leapfrog_acc.argtypes = [vp, vp]
     L.nb_direct_sum.argtypes = [vp, vp, i64, C.c_double, vp, i64, vp, vp, vp]
+    L.nb_direct_f32_workspace_size.argtypes = [i64]
+    L.nb_direct_f32_workspace_size.restype = C.c_size_t
+    L.nb_direct_f32.argtypes = [vp, vp, i64, C.c_float, vp, vp, i32, vp, C.c_size_t, vp]
     L.nb_sync_status.argtypes = [vp]
     L.nb_selftest_wait.argtypes = [vp, C.c_uint]
     L.nb_get_stats.argtypes = [vp, C.POINTER(nb_stats)]
@@ -468,6 +472,36 @@ def direct_sum(pos, mass, eps, targets=None, stream=None):
                               acc.data_ptr(), pot.data_ptr(), _stream_handle(stream)),
            "nb_direct_sum")
     return acc, pot
+
+
+def direct_f32(pos, mass, eps, precision="fp32", acc=None, pot=None, work=None, stream=None):
+    """Brute-force FP32 sum of Eq. (gravity) over all pairs (nb_direct_f32).
+    Returns (acc (n,3) float32, pot (n,) float32) CUDA tensors; `work` (uint8
+    CUDA tensor of direct_f32_workspace_size(n) bytes) may be passed to reuse
+    a workspace, as may acc / pot."""
+    import torch
+    n = int(pos.shape[0])
+    dev = pos.device
+    if acc is None:
+        acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    if pot is None:
+        pot = torch.empty(n, dtype=torch.float32, device=dev)
+    need = direct_f32_workspace_size(n)
+    if work is None:
+        work = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    _check(_lib.nb_direct_f32(_dptr(pos, torch.float64, 3, "pos"),
+                              _dptr(mass, torch.float32, None, "mass"), n, float(eps),
+                              _dptr(acc, torch.float32, 3, "acc"),
+                              _dptr(pot, torch.float32, None, "pot"),
+                              PRECISION.get(precision, precision),
+                              _dptr(work, torch.uint8, None, "work"), int(work.numel()),
+                              _stream_handle(stream)), "nb_direct_f32")
+    return acc, pot
+
+
+def direct_f32_workspace_size(n) -> int:
+    """Workspace bytes nb_direct_f32 needs for n particles on the current device."""
+    return int(_lib.nb_direct_f32_workspace_size(int(n)))
 
 
 def morton_order_noalloc(pos, keys_out, perm_out, stream=None):
