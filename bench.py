@@ -736,34 +736,52 @@ def run_crossover(args, ws, rank, local):
                 if best is None or t < best[0]:
                     best = (t, n_crit, st["n_pp"] + st["n_pc"])
                 ctx.close()
-            # accuracy of this tree evaluation against the brute force
+            # the best n_crit again, its launches replayed from one CUDA graph
+            # (no host launch cost), and its accuracy against the brute force
             ctx = nb.NBody(n, eps=eps, theta=theta, n_crit=best[1], stream=stream)
             ctx.build_tree(pos, mass)
             ctx.walk_groups(theta, best[1])
             ctx.forces(eps, acc, pot)
+            ctx.set_sync_checks(False)
+            gt, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gt, stream=stream):
+                ctx.build_tree(pos, mass)
+                ctx.walk_groups(theta, best[1])
+                ctx.forces(eps, acc, pot)
+            with torch.cuda.graph(gb, stream=stream):
+                nb.direct_f32(pos, mass, eps, "fp32", bacc, bpot, work, stream)
+            gt.replay()
+            gb.replay()
+            t_tree_graph = timed(gt.replay)
+            t_brute_graph = timed(gb.replay)
+            ctx.sync_status()
             ctx.close()
             torch.cuda.synchronize()
         d = ((acc.double() - bacc.double()).norm(dim=1) / bacc.double().norm(dim=1)).cpu().numpy()
         rows.append({"n": n, "tree_ms": best[0], "tree_n_crit": best[1],
                      "tree_interactions": int(best[2]), "brute_ms": t_brute,
+                     "tree_graph_ms": t_tree_graph, "brute_graph_ms": t_brute_graph,
                      "brute_interactions": n * (n - 1),
                      "brute_interactions_per_s": n * (n - 1) / (t_brute / 1e3),
                      "tree_median_rel_err_vs_brute": float(np.median(d))})
-    cross = None
-    for a, b in zip(rows, rows[1:]):
-        ra, rb = a["tree_ms"] / a["brute_ms"], b["tree_ms"] / b["brute_ms"]
-        if ra >= 1.0 > rb:
-            f = np.log(ra) / (np.log(ra) - np.log(rb))
-            cross = float(np.exp(np.log(a["n"]) + f * (np.log(b["n"]) - np.log(a["n"]))))
-            break
-    if rows[0]["tree_ms"] < rows[0]["brute_ms"]:
-        cross = f"below {rows[0]['n']}"
+    def crossing(kt, kb):
+        if rows[0][kt] < rows[0][kb]:
+            return f"below {rows[0]['n']}"
+        for a, b in zip(rows, rows[1:]):
+            ra, rb = a[kt] / a[kb], b[kt] / b[kb]
+            if ra >= 1.0 > rb:
+                f = np.log(ra) / (np.log(ra) - np.log(rb))
+                return float(np.exp(np.log(a["n"]) + f * (np.log(b["n"]) - np.log(a["n"]))))
+        return None
+    cross = crossing("tree_graph_ms", "brute_graph_ms")
     line = {
         "metric": "T_total of one force evaluation vs N: tree (theta 0.6) against FP32 brute force",
         "value": cross, "unit": "N at the crossover", "n_gpus": 1, "steps": reps, "warmup": 1,
         "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+        "crossover_eager_launches": crossing("tree_ms", "brute_ms"),
         "config": {"workload": "uniform sphere, radius 1, equal masses", "theta": theta,
-                   "eps": eps, "tree": "build + group walk + force, eager launches",
+                   "eps": eps, "tree": "build + group walk + force, replayed from a CUDA "
+                                       "graph (value) and launched eagerly (rows' tree_ms)",
                    "brute": "nb_direct_f32 (FP32, all pairs)",
                    "l2": "flushed (256 MB write) before every repetition"},
         "rows": rows,

@@ -177,6 +177,19 @@ int nb_forces_fused(nb_ctx *ctx, float theta, int n_crit, float eps, float *acc_
  * graph forms) use nb_forces_fused instead of nb_walk_groups + nb_forces. */
 int nb_set_fused(nb_ctx *ctx, int on);
 
+/* Key order of the next tree build (nb_build_tree and its batched, leapfrog,
+ * host and graph forms): NB_ORDER_MORTON (the default; Sec. "Test and
+ * Optimization", Table bench2) or NB_ORDER_HILBERT, the Peano-Hilbert order
+ * the same section names as better for locality (63-bit keys by Skilling's
+ * transpose method).  The cells are the same in both orders; only the order
+ * of the sorted particles, of the nodes (depth-first preorder visits the
+ * children along the curve) and of the summation changes, and
+ * nb_copy_tree's keys are then Peano-Hilbert keys.  A graph captured
+ * before the change keeps the order it was captured with. */
+#define NB_ORDER_MORTON 0
+#define NB_ORDER_HILBERT 1
+int nb_set_key_order(nb_ctx *ctx, int order);
+
 /* One kick-drift-kick leapfrog step of size dt in FP64 ("integrate orbits
  * ... and repeat", Sec. Introduction): v += a dt/2; x += v dt; rebuild the
  * tree, walk and force with cfg.eps, cfg.theta, cfg.n_crit, cfg.precision;

@@ -22,6 +22,7 @@ NB_ERR = {
 }
 NB_FP32, NB_FP32_COMP, NB_FP64ACC = 0, 1, 2
 PRECISION = {"fp32": NB_FP32, "fp32_comp": NB_FP32_COMP, "fp64acc": NB_FP64ACC}
+KEY_ORDER = {"morton": 0, "hilbert": 1}
 
 # flops per interaction by the paper's convention (Sec. "A Bare Many-body
 # Performance on RV770 GPU")
@@ -38,7 +39,7 @@ EXPORTED = [
     "nb_copy_group_lengths", "nb_build_tree_batched", "nb_leapfrog_step_batched",
     "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune", "nb_selftest_wait",
     "nb_leapfrog_step_host", "nb_forces_fused", "nb_set_fused", "nb_set_feature_mode",
-    "nb_direct_f32", "nb_direct_f32_workspace_size",
+    "nb_direct_f32", "nb_direct_f32_workspace_size", "nb_set_key_order",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -86,6 +87,7 @@ def _load():
     L.nb_forces.argtypes = [vp, C.c_float, vp, vp, i32]
     L.nb_forces_fused.argtypes = [vp, C.c_float, i32, C.c_float, vp, vp, i32]
     L.nb_set_fused.argtypes = [vp, i32]
+    L.nb_set_key_order.argtypes = [vp, i32]
     L.nb_set_feature_mode.argtypes = [vp, i32]
     L.nb_leapfrog_step.argtypes = [vp, vp, vp, vp, i64, C.c_double]
     L.nb_leapfrog_reset.argtypes = [vp]
@@ -299,6 +301,10 @@ class NBody:
     def set_feature_mode(self, mode: int):
         """Learned-theta features: 0 from the probe walk, 1 tree-only (no walk)."""
         _check(_lib.nb_set_feature_mode(self._h, int(mode)), "nb_set_feature_mode")
+
+    def set_key_order(self, order: str):
+        """Particle order of the next builds: "morton" (default) or "hilbert"."""
+        _check(_lib.nb_set_key_order(self._h, KEY_ORDER[order]), "nb_set_key_order")
 
     def set_fused(self, on: bool):
         """Leapfrog force passes without interaction lists (nb_set_fused)."""

@@ -704,6 +704,14 @@ int nb_set_feature_mode(nb_ctx *c, int mode)
     return NB_OK;
 }
 
+int nb_set_key_order(nb_ctx *c, int order)
+{
+    if (!c || (order != NB_ORDER_MORTON && order != NB_ORDER_HILBERT)) return NB_ERR_INVALID_ARG;
+    if (order != c->key_order) c->acc_valid = 0;   // the kept a(x) was summed in the old order
+    c->key_order = order;
+    return NB_OK;
+}
+
 int nb_set_fused(nb_ctx *c, int on)
 {
     if (!c) return NB_ERR_INVALID_ARG;

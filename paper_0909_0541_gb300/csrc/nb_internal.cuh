@@ -230,6 +230,7 @@ struct nb_ctx {
     int timing;
     int fused;               // leapfrog force passes use the fused walk and force
     int feature_mode;        // learned theta: 0 probe-walk features, 1 tree-only features
+    int key_order;           // NB_ORDER_MORTON or NB_ORDER_HILBERT (next build)
     int ev_used;
     int ev_graph;            // event pairs [0, ev_graph) are nodes of the captured graph
     int capturing;           // a graph capture is in progress on the stream

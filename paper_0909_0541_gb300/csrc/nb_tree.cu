@@ -145,9 +145,73 @@ __device__ __forceinline__ uint32_t grid_coord(double x, double corner, double s
     return f < 0 ? 0u : (f > 2097151 ? 2097151u : (uint32_t)f);
 }
 
+// Peano-Hilbert index of a grid point, the order the paper names as better
+// than Morton order for locality (Sec. "Test and Optimization"), by
+// Skilling's transpose method (J. Skilling 2004, "Programming the Hilbert
+// curve", AIP Conf. Proc. 707).  Going down the bit planes, the lower bits
+// of every axis are mapped into the frame of the sub-cube the point lies in
+// (a reflection of axis 0 when the axis bit is set, else an exchange of the
+// lower bits of axis 0 and that axis); the three words are then Gray-coded
+// and the result interleaved from the top like a Morton key (x, y, z).
+// Every step is a select on integers, so lanes do not diverge.  Aligned
+// sub-cubes are contiguous key ranges, so cells are again the key prefixes
+// shared by >= 2 particles, and children come in the curve's order.
+__device__ __forceinline__ uint64_t hilbert_key(uint32_t x0, uint32_t x1, uint32_t x2)
+{
+    uint32_t X[3] = {x0, x1, x2};
+#pragma unroll
+    for (int b = NB_LEVELS - 1; b >= 1; b--) {
+        const uint32_t Q = 1u << b, P = Q - 1u;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const bool set = (X[i] & Q) != 0u;
+            const uint32_t t = set ? 0u : ((X[0] ^ X[i]) & P);
+            X[0] ^= set ? P : t;
+            if (i) X[i] ^= t;
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    // flip: the XOR of (Q - 1) over the set bits Q > 1 of X[2], i.e. bit k is
+    // the parity of X[2]'s bits above k
+    uint32_t flip = 0u;
+#pragma unroll
+    for (int b = NB_LEVELS - 1; b >= 1; b--)
+        flip ^= ((X[2] >> b) & 1u) ? ((1u << b) - 1u) : 0u;
+#pragma unroll
+    for (int i = 0; i < 3; i++) X[i] ^= flip;
+    return (spread3(X[0]) << 2) | (spread3(X[1]) << 1) | spread3(X[2]);
+}
+
+// the grid point of a Peano-Hilbert key (the inverse of hilbert_key): undo
+// the Gray code, then re-apply the frame changes from the lowest bit plane up
+__device__ __forceinline__ void hilbert_point(uint64_t key, uint32_t q[3])
+{
+    uint32_t X[3] = {compact3(key >> 2), compact3(key >> 1), compact3(key)};
+    const uint32_t t = X[2] >> 1;
+    X[2] ^= X[1];
+    X[1] ^= X[0];
+    X[0] ^= t;
+#pragma unroll
+    for (int b = 1; b < NB_LEVELS; b++) {
+        const uint32_t Q = 1u << b, P = Q - 1u;
+#pragma unroll
+        for (int i = 2; i >= 0; i--) {
+            const bool set = (X[i] & Q) != 0u;
+            const uint32_t u = set ? 0u : ((X[0] ^ X[i]) & P);
+            X[0] ^= set ? P : u;
+            if (i) X[i] ^= u;
+        }
+    }
+    q[0] = X[0];
+    q[1] = X[1];
+    q[2] = X[2];
+}
+
 __global__ void __launch_bounds__(256)
 k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ roots,
-       const int32_t *__restrict__ sys_of, uint64_t *__restrict__ key, uint32_t *__restrict__ idx)
+       const int32_t *__restrict__ sys_of, uint64_t *__restrict__ key, uint32_t *__restrict__ idx,
+       int hilbert)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -156,7 +220,8 @@ k_keys(const double *__restrict__ pos, int64_t n, const double *__restrict__ roo
     const uint32_t qx = grid_coord(pos[3 * i], root[4], sc);
     const uint32_t qy = grid_coord(pos[3 * i + 1], root[5], sc);
     const uint32_t qz = grid_coord(pos[3 * i + 2], root[6], sc);
-    key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    key[i] = hilbert ? hilbert_key(qx, qy, qz)
+                     : (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     idx[i] = (uint32_t)i;
 }
 
@@ -465,7 +530,7 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
               nb_wrec *__restrict__ wrec, double *__restrict__ b_mass, double *__restrict__ b_mx,
               double *__restrict__ b_com, int32_t *__restrict__ b_up,
               int32_t *__restrict__ lcount, int16_t *__restrict__ cbkt,
-              int32_t *__restrict__ cbkt_cnt, int64_t n, unsigned *__restrict__ err)
+              int32_t *__restrict__ cbkt_cnt, int64_t n, int hilbert, unsigned *__restrict__ err)
 {
     __shared__ int32_t hb[NB_CBKT];   // cells per moments bucket in this block
     for (int k = threadIdx.x; k < NB_CBKT; k += blockDim.x) hb[k] = 0;
@@ -517,10 +582,20 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
             // once either way, with one FP64 add fewer per axis
             const double lc = __dmul_rn(root[3], pow2_neg(depth));
             const double lh = __dmul_rn(root[3], pow2_neg(depth + 1));
+            // the cell's integer corner: its first member's grid point shifted
+            // down to the cell's level (read off the Morton key's bits, or
+            // recovered from the Peano-Hilbert key by the inverse transform)
             const uint64_t kf = key[slot];
-            const uint32_t cq[3] = {compact3(kf >> 2) >> (NB_LEVELS - depth),
-                                    compact3(kf >> 1) >> (NB_LEVELS - depth),
-                                    compact3(kf) >> (NB_LEVELS - depth)};
+            uint32_t cq[3];
+            if (hilbert) {
+                hilbert_point(kf, cq);
+            } else {
+                cq[0] = compact3(kf >> 2);
+                cq[1] = compact3(kf >> 1);
+                cq[2] = compact3(kf);
+            }
+#pragma unroll
+            for (int d = 0; d < 3; d++) cq[d] >>= NB_LEVELS - depth;
 #pragma unroll
             for (int d = 0; d < 3; d++)
                 b_com[3 * (int64_t)b + d] =
@@ -765,7 +840,8 @@ void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     nb_launched(c, "k_bbox");
     k_root<<<1, 256, 0, s>>>(c->bbox_part, c->bbox_blocks, c->root);
     nb_launched(c, "k_root");
-    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, nullptr, c->keys, c->idx);
+    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, nullptr, c->keys, c->idx,
+                                           c->key_order);
     nb_launched(c, "k_keys");
     nb_radix_sort(c, n);
     build_tail(c, pos, mass, n, nullptr);
@@ -888,7 +964,8 @@ void nb_launch_build_batched(nb_ctx *c, const double *pos, const float *mass, in
     nb_launched(c, "k_sys_of");
     k_roots_sys<<<gs, 256, 0, s>>>(pos, off, nsys, n, c->root, c->err);
     nb_launched(c, "k_roots_sys");
-    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, c->sys_of, c->keys, c->idx);
+    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, c->sys_of, c->keys, c->idx,
+                                           c->key_order);
     nb_launched(c, "k_keys");
     nb_radix_sort(c, n);
     // stable by system on top of the Morton order: (system, key) order
@@ -948,7 +1025,7 @@ static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t 
     k_bfs_records<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
         c->bfs2pid, c->pid2bfs, c->node_c, c->n_first, c->n_nchild, c->n_parent, c->n_depth,
         c->keys, c->root, sys_sorted, c->p_hi, c->p_lo, c->p_x64, c->cnt, c->wrec, c->b_mass,
-        c->b_mx, c->b_com, c->b_up, c->lcount, c->cbkt, c->cbkt_cnt, n, c->err);
+        c->b_mx, c->b_com, c->b_up, c->lcount, c->cbkt, c->cbkt_cnt, n, c->key_order, c->err);
     nb_launched(c, "k_bfs_records");
     const int cl_blocks = (int)((c->max_nodes + CL_TILE - 1) / CL_TILE);
     k_cell_list<<<cl_blocks > 0 ? cl_blocks : 1, 256, 0, s>>>(c->cbkt, c->cbkt_cnt, c->cnt,
@@ -1145,5 +1222,5 @@ void nb_launch_keys_raw(const double *pos, int64_t n, double *part, int nblk, do
 {
     k_bbox<<<nblk, 256, 0, s>>>(pos, n, part, err);
     k_root<<<1, 256, 0, s>>>(part, nblk, root);
-    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, root, nullptr, keys, idx);
+    k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, root, nullptr, keys, idx, 0);
 }

@@ -6,7 +6,7 @@ import numpy as np
 
 
 def gpu_run(pos, mass, *, theta, n_crit, eps, precision="fp32", max_n=None,
-            lists=True):
+            lists=True, key_order="morton"):
     import torch
 
     import paper_0909_0541_gb300 as nb
@@ -15,6 +15,7 @@ def gpu_run(pos, mass, *, theta, n_crit, eps, precision="fp32", max_n=None,
     p = torch.from_numpy(np.ascontiguousarray(pos, np.float64)).to(dev)
     m = torch.from_numpy(np.ascontiguousarray(mass, np.float32)).to(dev)
     ctx = nb.NBody(max_n or max(n, 1))
+    ctx.set_key_order(key_order)
     ctx.build_tree(p, m)
     ctx.walk_groups(theta, n_crit)
     acc = torch.zeros((n, 3), dtype=torch.float32, device=dev)
