@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--n-crit", type=int, default=None)
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--order", default="morton", choices=["morton", "hilbert"],
+                    help="particle / node order of the tree (Morton or Peano-Hilbert keys)")
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel of the timed steps from the host instead of "
                          "replaying them from one CUDA graph")
@@ -362,6 +364,7 @@ def run_ours(args, ws, rank, local):
     stream.wait_stream(torch.cuda.current_stream(dev))
     if args.fused:
         ctx.set_fused(True)
+    ctx.set_key_order(args.order)
     dt = w["dt"]
     with torch.cuda.stream(stream):
         # first step synchronises: sizes the interaction-list storage
@@ -516,7 +519,7 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args.workload, n, w, ws),
-            "run": {"precision": args.precision,
+            "run": {"precision": args.precision, "key_order": args.order,
                     "force_path": "fused walk+force" if args.fused else "lists",
                     "launch": ((f"eager (graph capture failed: {graph_failed})"
                                 if graph_failed else
