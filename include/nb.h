@@ -372,6 +372,59 @@ int nb_theta_labels(const float *err_dev, const float *cost_dev, const float *si
                     const float *grid_dev, int T, int64_t S, float budget, float lambda,
                     float *labels_dev, void *stream);
 
+/* The label rule of the learned theta with all its arithmetic on the
+ * device (the paper has one theta, Eq. mac; its cost / accuracy trade is
+ * Table theta).  S sampled groups, T grid thetas (ascending, T <= 64); err_dev
+ * (T x S FP32): each group's measured median |da|/|a| at each theta (FP64
+ * judge); cost_dev (T x S FP32): its cost there (interactions plus weighted
+ * list entries); size_dev (S FP32): group sizes n_g.
+ * nb_theta_fit_curves: the curves the features predict.  Least squares, in
+ * FP64, of ln(err + 1e-15) and of ln(cost + 1) at every theta on the
+ * feature columns cols_host[0..ncols) (ncols <= 16; feature rows of `stride`
+ * floats in feat_dev, S x stride) plus an intercept; columns are
+ * standardised first (a constant column drops out) and the normal equations
+ * are solved by Cholesky.  pred_lnerr_dev receives the fitted ln error,
+ * pred_cost_dev exp of the fitted ln(cost + 1) (both T x S FP64).  work_dev:
+ * caller-owned, 256-byte aligned, nb_theta_fit_workspace_size(S, ncols, T)
+ * bytes.  Queued on `stream`, no synchronisation. */
+size_t nb_theta_fit_workspace_size(int64_t S, int ncols, int T);
+int nb_theta_fit_curves(const float *feat_dev, int64_t S, int stride, const int32_t *cols_host,
+                        int ncols, const float *err_dev, const float *cost_dev, int T,
+                        double *pred_lnerr_dev, double *pred_cost_dev, void *work_dev,
+                        size_t work_bytes, void *stream);
+/* nb_theta_allocate: labels_dev (S FP32) receives each group's grid theta
+ * minimising cost / n_g + lambda * lnerr, where (lnerr, cost) are the
+ * predicted curves when pred_lnerr_dev / pred_cost_dev are given (T x S
+ * FP64, from nb_theta_fit_curves), else the measured ones (ln max(err,
+ * 1e-9) and cost_dev); ties go to the smaller theta.  lambda is bisected
+ * `iters` times in ln space on [lam_lo, lam_hi] so that the n_g-weighted
+ * median of the MEASURED errors at the chosen thetas is <= budget (weighted
+ * median: the smallest error u whose weight of errors <= u reaches half the
+ * total); the labels are those of the upper end.  result_dev (2 FP64)
+ * receives lambda and that weighted median.  work_dev: caller-owned,
+ * 256-byte aligned, nb_theta_allocate_workspace_size(S) bytes.  Queued on
+ * `stream`, no synchronisation. */
+size_t nb_theta_allocate_workspace_size(int64_t S);
+int nb_theta_allocate(const double *pred_lnerr_dev, const double *pred_cost_dev,
+                      const float *err_dev, const float *cost_dev, const float *size_dev,
+                      const float *grid_dev, int T, int64_t S, double budget, double lam_lo,
+                      double lam_hi, int iters, float *labels_dev, double *result_dev,
+                      void *work_dev, size_t work_bytes, void *stream);
+/* Mean and spread (population standard deviation, FP64, two passes) of the
+ * first ncols (<= 17) columns of S feature rows of `stride` floats: the
+ * network's input standardisation.  Queued on `stream`. */
+int nb_column_stats(const float *feat_dev, int64_t S, int stride, int ncols, double *mean_dev,
+                    double *sd_dev, void *stream);
+/* Relative force errors of nt targets against an FP64 reference and their
+ * statistics: err_dev (nt FP32, caller-owned) receives |a - ref| / |ref|
+ * (|ref| = 0 counts as 1) for a = acc_dev rows targets_dev[k] (n x 3 FP32;
+ * targets NULL: rows 0..nt-1) and ref_dev row k (nt x 3 FP64); out_dev (2
+ * FP64) receives the median (mean of the two middle values) and the
+ * nearest-rank q-quantile (the ceil(q nt)-th smallest).  Queued on `stream`,
+ * no synchronisation. */
+int nb_error_stats(const float *acc_dev, const double *ref_dev, const int64_t *targets_dev,
+                   int64_t nt, double q, double *out_dev, float *err_dev, void *stream);
+
 #define NB_MLP_NPARAM 9960
 #define NB_NFEAT 12
 #define NB_NFEAT_STRIDE 16

@@ -40,6 +40,8 @@ EXPORTED = [
     "nb_graph_capture_leapfrog", "nb_graph_launch", "nb_autotune", "nb_selftest_wait",
     "nb_leapfrog_step_host", "nb_forces_fused", "nb_set_fused", "nb_set_feature_mode",
     "nb_direct_f32", "nb_direct_f32_workspace_size", "nb_set_key_order",
+    "nb_theta_fit_workspace_size", "nb_theta_fit_curves", "nb_theta_allocate_workspace_size",
+    "nb_theta_allocate", "nb_error_stats", "nb_column_stats",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -118,6 +120,16 @@ def _load():
     L.nb_walk_groups_learned.argtypes = [vp, i32, vp, C.c_float, vp]
     L.nb_group_errors.argtypes = [vp, vp, vp, vp, i64, vp, vp]
     L.nb_theta_labels.argtypes = [vp, vp, vp, vp, i32, i64, C.c_float, C.c_float, vp, vp]
+    L.nb_theta_fit_workspace_size.argtypes = [i64, i32, i32]
+    L.nb_theta_fit_workspace_size.restype = C.c_size_t
+    L.nb_theta_fit_curves.argtypes = [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, vp,
+                                      C.c_size_t, vp]
+    L.nb_theta_allocate_workspace_size.argtypes = [i64]
+    L.nb_theta_allocate_workspace_size.restype = C.c_size_t
+    L.nb_theta_allocate.argtypes = [vp, vp, vp, vp, vp, vp, i32, i64, C.c_double, C.c_double,
+                                    C.c_double, i32, vp, vp, vp, C.c_size_t, vp]
+    L.nb_error_stats.argtypes = [vp, vp, vp, i64, C.c_double, vp, vp, vp]
+    L.nb_column_stats.argtypes = [vp, i64, i32, i32, vp, vp, vp]
     L.nb_mlp_workspace_size.argtypes = [i64]
     L.nb_mlp_workspace_size.restype = C.c_size_t
     L.nb_mlp_forward.argtypes = [vp, vp, i64, vp, C.c_float, vp, vp]
@@ -617,3 +629,81 @@ def theta_labels(err, grid, budget=1e-3, cost=None, size=None, lam=0.0, stream=N
                                 float(lam), lab.data_ptr(), _stream_handle(stream)),
            "nb_theta_labels")
     return lab
+
+
+def theta_fit_curves(feat, err, cost, cols, stream=None):
+    """Curves predicted from the feature columns `cols` of feat (S, stride)
+    float32 for err, cost (T, S) float32: (pred ln error, pred cost), each
+    (T, S) float64 CUDA tensors (nb_theta_fit_curves)."""
+    import torch
+    S, stride = int(feat.shape[0]), int(feat.shape[1])
+    T = int(err.shape[0])
+    c = np.ascontiguousarray(cols, np.int32)
+    dev = feat.device
+    pe = torch.empty((T, S), dtype=torch.float64, device=dev)
+    pc = torch.empty((T, S), dtype=torch.float64, device=dev)
+    need = int(_lib.nb_theta_fit_workspace_size(S, len(c), T))
+    work = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    _check(_lib.nb_theta_fit_curves(_dptr(feat, torch.float32, stride, "feat"), S, stride,
+                                    _hptr(c), len(c), _dptr(err.contiguous(), torch.float32,
+                                                            None, "err"),
+                                    _dptr(cost.contiguous(), torch.float32, None, "cost"), T,
+                                    pe.data_ptr(), pc.data_ptr(), work.data_ptr(),
+                                    int(work.numel()), _stream_handle(stream)),
+           "nb_theta_fit_curves")
+    return pe, pc
+
+
+def theta_allocate(err, cost, size, grid, budget, lam_lo, lam_hi, iters, pred=None,
+                   stream=None):
+    """Labels (S,) float32 and (lambda, weighted median error) of the
+    allocation rule (nb_theta_allocate); pred = (pred ln error, pred cost)
+    from theta_fit_curves, or None for the measured curves."""
+    import torch
+    T, S = int(err.shape[0]), int(err.shape[1])
+    dev = err.device
+    lab = torch.empty(S, dtype=torch.float32, device=dev)
+    res = torch.empty(2, dtype=torch.float64, device=dev)
+    need = int(_lib.nb_theta_allocate_workspace_size(S))
+    work = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    pe, pc = pred if pred is not None else (None, None)
+    _check(_lib.nb_theta_allocate(
+        None if pe is None else _dptr(pe.contiguous(), torch.float64, None, "pred_lnerr"),
+        None if pc is None else _dptr(pc.contiguous(), torch.float64, None, "pred_cost"),
+        _dptr(err.contiguous(), torch.float32, None, "err"),
+        _dptr(cost.contiguous(), torch.float32, None, "cost"),
+        _dptr(size, torch.float32, None, "size"), _dptr(grid, torch.float32, None, "grid"),
+        T, S, float(budget), float(lam_lo), float(lam_hi), int(iters), lab.data_ptr(),
+        res.data_ptr(), work.data_ptr(), int(work.numel()), _stream_handle(stream)),
+        "nb_theta_allocate")
+    r = res.cpu().numpy()
+    return lab, float(r[0]), float(r[1])
+
+
+def error_stats(acc, ref, targets=None, q=0.99, stream=None):
+    """(median, nearest-rank q-quantile) of |a - ref| / |ref| over the
+    targets (nb_error_stats): acc (n, 3) float32, ref (nt, 3) float64."""
+    import torch
+    nt = int(ref.shape[0])
+    out = torch.empty(2, dtype=torch.float64, device=ref.device)
+    err = torch.empty(max(nt, 1), dtype=torch.float32, device=ref.device)
+    _check(_lib.nb_error_stats(_dptr(acc, torch.float32, 3, "acc"),
+                               _dptr(ref, torch.float64, 3, "ref"),
+                               _dptr(targets, torch.int64, None, "targets"), nt, float(q),
+                               out.data_ptr(), err.data_ptr(), _stream_handle(stream)),
+           "nb_error_stats")
+    o = out.cpu().numpy()
+    return float(o[0]), float(o[1])
+
+
+def column_stats(feat, ncols, stream=None):
+    """(mean, spread) float64 CUDA tensors of the first ncols columns of feat
+    (nb_column_stats)."""
+    import torch
+    S, stride = int(feat.shape[0]), int(feat.shape[1])
+    mu = torch.empty(ncols, dtype=torch.float64, device=feat.device)
+    sd = torch.empty(ncols, dtype=torch.float64, device=feat.device)
+    _check(_lib.nb_column_stats(_dptr(feat, torch.float32, stride, "feat"), S, stride,
+                                int(ncols), mu.data_ptr(), sd.data_ptr(),
+                                _stream_handle(stream)), "nb_column_stats")
+    return mu, sd

@@ -17,16 +17,18 @@ error for all groups, so that groups whose error barely grows with theta
 and groups whose error grows fast keep a small theta.  lambda is bisected so
 that the n_g-weighted median of the labelled errors meets the budget (1e-3).
 (Requiring every group's own median to meet the budget costs as much as one
-fixed theta at the same global median error.)  The network maps the 12
-probe features to theta in [0.3, 1.2]; the fixed-theta walk is the fallback
-for non-finite output.
+fixed theta at the same global median error.)  The curves are the measured
+ones, or the ones the features predict (least squares); the fit, the choice,
+the weighted median and the bisection all run in libnb (nb_theta_fit_curves,
+nb_theta_allocate).  The network maps the features to theta in [0.3, 1.2];
+the fixed-theta walk is the fallback for non-finite output.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import (MLP_NPARAM, NFEAT_STRIDE, NBody, direct_sum, group_errors, mlp_train,
-               theta_labels)
+from . import (MLP_NPARAM, NBody, column_stats, direct_sum, error_stats, group_errors,
+               mlp_train, theta_allocate, theta_fit_curves)
 
 THETA_GRID = np.round(np.arange(0.30, 1.2001, 0.05), 2).astype(np.float32)
 BUDGET = 1e-3
@@ -67,51 +69,7 @@ def judge_targets(ctx: NBody, groups: np.ndarray):
     return targets, off
 
 
-def weighted_median(v, w):
-    o = np.argsort(v, kind="stable")
-    cw = np.cumsum(w[o])
-    return float(v[o][np.searchsorted(cw, 0.5 * cw[-1])])
-
-
 TREE_COLS = [0, 1, 2, 3, 4, 5, 11]   # the features of feature mode 1 (no walk)
-
-
-def predicted_labels(X, E, C, size, grid=THETA_GRID, budget=BUDGET, cols=None):
-    """Labels from the error and cost curves the features predict.
-
-    E, C: (grid, S) measured median errors and interaction costs of the S
-    sampled groups.  Least squares on the features (columns `cols`) gives
-    each group's expected ln error and ln cost at every grid theta; the label
-    is the grid theta minimising predicted cost / n_g + lambda x predicted
-    ln error, with lambda bisected so that the n_g-weighted median of the
-    *measured* errors of the labelled thetas meets the budget.  Unlike the
-    labels of the measured curves, which carry each group's unpredictable
-    scatter, these are the best choice the features allow, and a smooth
-    function of them.  Returns (labels (S,), lambda, weighted median error)."""
-    F = np.asarray(X, np.float64)
-    F = F[:, cols] if cols is not None else F[:, :NIN]
-    A = np.c_[F, np.ones(len(F))]
-    T, S = E.shape
-    PE, PC = np.zeros((T, S)), np.zeros((T, S))
-    for t in range(T):
-        ce, *_ = np.linalg.lstsq(A, np.log(E[t] + 1e-15), rcond=None)
-        cc, *_ = np.linalg.lstsq(A, np.log(C[t] + 1.0), rcond=None)
-        PE[t], PC[t] = A @ ce, np.exp(A @ cc)
-    col = np.arange(S)
-
-    def pick(lam):
-        t = np.argmin(PC / size + lam * PE, axis=0)
-        return t, weighted_median(E[t, col], size)
-
-    lo, hi = 1e-3, 1e9           # ln-space bisection on the exchange rate
-    for _ in range(60):
-        mid = float(np.sqrt(lo * hi))
-        if pick(mid)[1] > budget:
-            lo = mid
-        else:
-            hi = mid
-    t, werr = pick(hi)
-    return np.asarray(grid, np.float32)[t], hi, werr
 
 
 def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget=BUDGET,
@@ -121,8 +79,9 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
     particle set (pos, mass: CUDA tensors); info holds the error and cost
     curves, the group sizes, the sampled groups and the exchange rate.
     feature_mode: 0 probe-walk features, 1 tree-only features.  label_rule:
-    "measured" (the argmin over each group's measured curves, on the GPU) or
-    "predicted" (predicted_labels).  A group's cost at a theta is its
+    "measured" (the allocation over each group's measured curves) or
+    "predicted" (over the curves the features predict, least squares on the
+    features of the feature mode).  A group's cost at a theta is its
     interactions, n_g (list length + n_g), plus walk_weight x list length: the
     walk's time per list entry in units of the force's time per interaction
     (0: interactions only)."""
@@ -154,30 +113,15 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
     grid_d = torch.from_numpy(np.asarray(grid, np.float32)).to(dev)
     cost_d = torch.from_numpy(cost).to(dev)
     size_d = torch.from_numpy(size).to(dev)
-    E = errs.cpu().numpy()
-    col = np.arange(len(sel))
-
-    def labelled_error(lam):
-        lab = theta_labels(errs, grid_d, budget, cost_d, size_d, lam)
-        ti = np.searchsorted(np.asarray(grid, np.float32), lab.cpu().numpy())
-        return lab, weighted_median(E[np.minimum(ti, len(grid) - 1), col], size)
-
     X = feat[torch.from_numpy(sel).to(dev)].contiguous()
     if label_rule == "predicted":
-        cols = TREE_COLS if feature_mode == 1 else None
-        lab, hi, werr = predicted_labels(X.cpu().numpy(), E.astype(np.float64),
-                                         cost.astype(np.float64), size.astype(np.float64),
-                                         grid, budget, cols)
-        labels = torch.from_numpy(lab).to(dev)
+        cols = TREE_COLS if feature_mode == 1 else list(range(NIN))
+        pred = theta_fit_curves(X, errs, cost_d, cols)
+        labels, hi, werr = theta_allocate(errs, cost_d, size_d, grid_d, budget, 1e-3, 1e9, 60,
+                                          pred=pred)
     else:
-        lo, hi = 1.0, 1e6          # ln-space bisection on the exchange rate
-        for _ in range(40):
-            mid = float(np.sqrt(lo * hi))
-            if labelled_error(mid)[1] > budget:
-                lo = mid
-            else:
-                hi = mid
-        labels, werr = labelled_error(hi)
+        labels, hi, werr = theta_allocate(errs, cost_d, size_d, grid_d, budget, 1.0, 1e6, 40)
+    E = errs.cpu().numpy()
     if own:
         ctx.close()
     info = dict(errors=E, cost=cost, size=size, groups=sel, lam=hi, labelled_error=werr)
@@ -191,9 +135,9 @@ def train(X, y, epochs=150, batch=256, lr=2e-3, seed=5):
 
     import nbsynth
     S = int(X.shape[0])
-    Xh = X[:, :NIN].double().cpu().numpy()
-    params = torch.from_numpy(pack_params(nbsynth.mlp_initial_weights(seed), Xh.mean(0),
-                                          Xh.std(0))).to(X.device)
+    mu, sd = column_stats(X, NIN)
+    params = torch.from_numpy(pack_params(nbsynth.mlp_initial_weights(seed), mu.cpu().numpy(),
+                                          sd.cpu().numpy())).to(X.device)
     rng = np.random.default_rng(seed + 1)
     order = torch.from_numpy(np.stack([rng.permutation(S) for _ in range(epochs)])
                              .astype(np.int32)).to(X.device)
@@ -203,10 +147,9 @@ def train(X, y, epochs=150, batch=256, lr=2e-3, seed=5):
 
 
 def median_error(acc, ref, targets):
-    """Median |da|/|a| of acc at targets against the FP64 direct-sum reference ref."""
-    import torch
-    d = (acc[targets].double() - ref).norm(dim=1) / ref.norm(dim=1)
-    return float(torch.median(d).item()) if d.numel() else 0.0
+    """Median |da|/|a| of acc at targets against the FP64 direct-sum
+    reference ref (nb_error_stats)."""
+    return error_stats(acc, ref, targets)[0] if int(ref.shape[0]) else 0.0
 
 
 def step_cost(ctx: NBody, n_crit, eps, acc, theta=None, params=None, fallback=0.6):

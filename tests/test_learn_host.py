@@ -1,11 +1,11 @@
-"""Host logic of the learned opening angle (no GPU): the labels computed from
-predicted error and cost curves, on synthetic curves whose best allocation
-is known, and the flat parameter layout the host hands to the network's
-kernels."""
+"""The learned opening angle without a GPU: the oracle's label rule
+(oracle/labels.py) on synthetic curves whose best allocation is known, its
+least-squares fit and weighted median against closed forms, and the flat
+parameter layout the host hands to the network's kernels."""
 import numpy as np
 
 import nbsynth
-from oracle import mlp
+from oracle import labels, mlp
 from paper_0909_0541_gb300 import MLP_NPARAM, learn
 
 
@@ -27,10 +27,11 @@ def curves(S=400, seed=0):
 
 def test_predicted_labels_meet_the_budget_and_beat_one_theta():
     X, E, C, size, kind, grid = curves()
-    lab, lam, werr = learn.predicted_labels(X, E, C, size, cols=[0, 1])
+    PE, PC = labels.fit_curves(X, E, C, [0, 1])
+    lab, lam, werr = labels.allocate(E, C, size, grid, learn.BUDGET, 1e-3, 1e9, 60, PE, PC)
     t = np.searchsorted(learn.THETA_GRID, lab)
     cols = np.arange(len(lab))
-    assert learn.weighted_median(E[t, cols], size) <= learn.BUDGET
+    assert labels.weighted_median(E[t, cols], size) <= learn.BUDGET
     assert werr <= learn.BUDGET and lam > 0
     # groups with the same predicted curves get the same theta (up to a tie
     # between neighbouring grid points)
@@ -39,15 +40,32 @@ def test_predicted_labels_meet_the_budget_and_beat_one_theta():
     # and the allocation costs less than the best single theta within budget.
     # (Under a median budget the cheapest allocation may meet it with one kind
     # alone: the exchange rate trades the other kind's error for cost.)
-    ok = [k for k in range(len(grid)) if learn.weighted_median(E[k], size) <= learn.BUDGET]
+    ok = [k for k in range(len(grid)) if labels.weighted_median(E[k], size) <= learn.BUDGET]
     best_single = min(C[k].sum() for k in ok)
     assert C[t, cols].sum() < best_single
 
 
+def test_fit_curves_is_least_squares():
+    """Residuals of the fit are orthogonal to every column and the intercept
+    (the normal equations), on noisy data."""
+    rng = np.random.default_rng(4)
+    S, T = 300, 5
+    X = rng.normal(size=(S, 16))
+    E = np.exp(rng.normal(size=(T, S)) - 7.0)
+    C = np.exp(rng.normal(size=(T, S)) + 8.0)
+    PE, PC = labels.fit_curves(X, E, C, [1, 4, 9])
+    A = np.c_[X[:, [1, 4, 9]], np.ones(S)]
+    assert np.abs(A.T @ (np.log(E + 1e-15) - PE).T).max() < 1e-8
+    assert np.abs(A.T @ (np.log(C + 1.0) - np.log(PC)).T).max() < 1e-8
+
+
 def test_weighted_median():
     v = np.array([5.0, 1.0, 3.0])
-    assert learn.weighted_median(v, np.array([1.0, 1.0, 1.0])) == 3.0
-    assert learn.weighted_median(v, np.array([1.0, 10.0, 1.0])) == 1.0
+    assert labels.weighted_median(v, np.array([1.0, 1.0, 1.0])) == 3.0
+    assert labels.weighted_median(v, np.array([1.0, 10.0, 1.0])) == 1.0
+    # half the weight exactly at a value: that value
+    assert labels.weighted_median(np.array([1.0, 2.0, 3.0, 4.0]), np.ones(4)) == 2.0
+    assert labels.error_stats([4.0, 1.0, 3.0, 2.0], 0.75) == (2.5, 3.0)
 
 
 def test_host_parameter_packing_matches_the_oracle_layout():
