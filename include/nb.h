@@ -397,19 +397,26 @@ int nb_theta_fit_curves(const float *feat_dev, int64_t S, int stride, const int3
  * predicted curves when pred_lnerr_dev / pred_cost_dev are given (T x S
  * FP64, from nb_theta_fit_curves), else the measured ones (ln max(err,
  * 1e-9) and cost_dev); ties go to the smaller theta.  lambda is bisected
- * `iters` times in ln space on [lam_lo, lam_hi] so that the n_g-weighted
- * median of the MEASURED errors at the chosen thetas is <= budget (weighted
- * median: the smallest error u whose weight of errors <= u reaches half the
- * total); the labels are those of the upper end.  result_dev (2 FP64)
- * receives lambda and that weighted median.  work_dev: caller-owned,
- * 256-byte aligned, nb_theta_allocate_workspace_size(S) bytes.  Queued on
- * `stream`, no synchronisation. */
-size_t nb_theta_allocate_workspace_size(int64_t S);
+ * `iters` times in ln space on [lam_lo, lam_hi] so that a statistic of the
+ * MEASURED errors at the chosen thetas is <= budget; the labels are those of
+ * the bracket's upper end.  The statistic: without perr_dev, the n_g-weighted
+ * median of the groups' median errors (the smallest error u whose weight of
+ * errors <= u reaches half the total); with perr_dev (T x P FP32: every judged
+ * particle's own |da|/|a| at each theta, group g's particles being columns
+ * poff_dev[g] .. poff_dev[g+1], an S + 1 int64 offset array from 0 to P,
+ * checked before use: the call then synchronises `stream`), the median over
+ * the judged particles of their errors at their group's theta (mean of the
+ * two middle values).  result_dev (2 FP64) receives lambda and the
+ * statistic.  work_dev: caller-owned, 256-byte aligned,
+ * nb_theta_allocate_workspace_size(S, P) bytes (P = 0 without perr_dev).
+ * Queued on `stream`. */
+size_t nb_theta_allocate_workspace_size(int64_t S, int64_t P);
 int nb_theta_allocate(const double *pred_lnerr_dev, const double *pred_cost_dev,
                       const float *err_dev, const float *cost_dev, const float *size_dev,
                       const float *grid_dev, int T, int64_t S, double budget, double lam_lo,
-                      double lam_hi, int iters, float *labels_dev, double *result_dev,
-                      void *work_dev, size_t work_bytes, void *stream);
+                      double lam_hi, int iters, const float *perr_dev, const int64_t *poff_dev,
+                      int64_t P, float *labels_dev, double *result_dev, void *work_dev,
+                      size_t work_bytes, void *stream);
 /* Mean and spread (population standard deviation, FP64, two passes) of the
  * first ncols (<= 17) columns of S feature rows of `stride` floats: the
  * network's input standardisation.  Queued on `stream`. */

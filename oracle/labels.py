@@ -14,7 +14,9 @@ the features predict: ordinary least squares of ln(E + 1e-15) and of
 ln(C + 1) on the chosen feature columns plus an intercept (PE = the fit,
 PC = exp of the fit).  lambda is bisected in ln space so that the
 n_g-weighted median of the measured errors E at the chosen thetas meets the
-budget; the labels are those of the bracket's upper end.  Written as plain
+budget (or, as an option, the plain median over the judged particles of
+their own errors at their group's theta); the labels are those of the
+bracket's upper end.  Written as plain
 numpy: np.linalg.lstsq for the fit, np.argmin for the choice (first minimum
 on ties), a stable sort and a cumulative sum for the weighted median.
 """
@@ -52,8 +54,12 @@ def choose(lam, PE, PC, size):
     return np.argmin(PC / np.asarray(size, np.float64)[None, :] + lam * PE, axis=0)
 
 
-def allocate(E, C, size, grid, budget, lam_lo, lam_hi, iters, PE=None, PC=None):
-    """(labels (S,), lambda, weighted median error) of the rule above."""
+def allocate(E, C, size, grid, budget, lam_lo, lam_hi, iters, PE=None, PC=None,
+             perr=None, poff=None):
+    """(labels (S,), lambda, statistic) of the rule above.  The statistic
+    held at the budget is the n_g-weighted median of the groups' errors E,
+    or, with perr (T, P) and poff (S + 1): the median over the judged
+    particles of their own errors at their group's theta."""
     E = np.asarray(E, np.float64)
     C = np.asarray(C, np.float64)
     size = np.asarray(size, np.float64)
@@ -62,19 +68,25 @@ def allocate(E, C, size, grid, budget, lam_lo, lam_hi, iters, PE=None, PC=None):
     if PC is None:
         PC = C
     col = np.arange(E.shape[1])
+    if perr is not None:
+        perr = np.asarray(perr, np.float64)
+        group_of = np.repeat(col, np.diff(poff))
+        pcol = np.arange(perr.shape[1])
 
-    def wmed(lam):
+    def stat(lam):
         t = choose(lam, PE, PC, size)
-        return t, weighted_median(E[t, col], size)
+        if perr is None:
+            return t, weighted_median(E[t, col], size)
+        return t, float(np.median(perr[t[group_of], pcol]))
 
     lo, hi = float(lam_lo), float(lam_hi)
     for _ in range(iters):
         mid = float(np.sqrt(lo * hi))
-        if wmed(mid)[1] > budget:
+        if stat(mid)[1] > budget:
             lo = mid
         else:
             hi = mid
-    t, werr = wmed(hi)
+    t, werr = stat(hi)
     return np.asarray(grid, np.float32)[t], hi, werr
 
 

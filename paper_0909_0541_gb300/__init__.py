@@ -124,10 +124,10 @@ def _load():
     L.nb_theta_fit_workspace_size.restype = C.c_size_t
     L.nb_theta_fit_curves.argtypes = [vp, i64, i32, vp, i32, vp, vp, i32, vp, vp, vp,
                                       C.c_size_t, vp]
-    L.nb_theta_allocate_workspace_size.argtypes = [i64]
+    L.nb_theta_allocate_workspace_size.argtypes = [i64, i64]
     L.nb_theta_allocate_workspace_size.restype = C.c_size_t
     L.nb_theta_allocate.argtypes = [vp, vp, vp, vp, vp, vp, i32, i64, C.c_double, C.c_double,
-                                    C.c_double, i32, vp, vp, vp, C.c_size_t, vp]
+                                    C.c_double, i32, vp, vp, i64, vp, vp, vp, C.c_size_t, vp]
     L.nb_error_stats.argtypes = [vp, vp, vp, i64, C.c_double, vp, vp, vp]
     L.nb_column_stats.argtypes = [vp, i64, i32, i32, vp, vp, vp]
     L.nb_mlp_workspace_size.argtypes = [i64]
@@ -655,16 +655,20 @@ def theta_fit_curves(feat, err, cost, cols, stream=None):
 
 
 def theta_allocate(err, cost, size, grid, budget, lam_lo, lam_hi, iters, pred=None,
-                   stream=None):
-    """Labels (S,) float32 and (lambda, weighted median error) of the
-    allocation rule (nb_theta_allocate); pred = (pred ln error, pred cost)
-    from theta_fit_curves, or None for the measured curves."""
+                   perr=None, poff=None, stream=None):
+    """Labels (S,) float32 and (lambda, statistic) of the allocation rule
+    (nb_theta_allocate); pred = (pred ln error, pred cost) from
+    theta_fit_curves, or None for the measured curves; perr (T, P) float32
+    per-particle errors with poff (S + 1,) int64 offsets: hold the median
+    over particles at the budget instead of the weighted median of group
+    medians."""
     import torch
     T, S = int(err.shape[0]), int(err.shape[1])
+    P = 0 if perr is None else int(perr.shape[1])
     dev = err.device
     lab = torch.empty(S, dtype=torch.float32, device=dev)
     res = torch.empty(2, dtype=torch.float64, device=dev)
-    need = int(_lib.nb_theta_allocate_workspace_size(S))
+    need = int(_lib.nb_theta_allocate_workspace_size(S, P))
     work = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     pe, pc = pred if pred is not None else (None, None)
     _check(_lib.nb_theta_allocate(
@@ -673,25 +677,29 @@ def theta_allocate(err, cost, size, grid, budget, lam_lo, lam_hi, iters, pred=No
         _dptr(err.contiguous(), torch.float32, None, "err"),
         _dptr(cost.contiguous(), torch.float32, None, "cost"),
         _dptr(size, torch.float32, None, "size"), _dptr(grid, torch.float32, None, "grid"),
-        T, S, float(budget), float(lam_lo), float(lam_hi), int(iters), lab.data_ptr(),
-        res.data_ptr(), work.data_ptr(), int(work.numel()), _stream_handle(stream)),
-        "nb_theta_allocate")
+        T, S, float(budget), float(lam_lo), float(lam_hi), int(iters),
+        None if perr is None else _dptr(perr.contiguous(), torch.float32, None, "perr"),
+        None if poff is None else _dptr(poff, torch.int64, None, "poff"), P,
+        lab.data_ptr(), res.data_ptr(), work.data_ptr(), int(work.numel()),
+        _stream_handle(stream)), "nb_theta_allocate")
     r = res.cpu().numpy()
     return lab, float(r[0]), float(r[1])
 
 
-def error_stats(acc, ref, targets=None, q=0.99, stream=None):
+def error_stats(acc, ref, targets=None, q=0.99, err_out=None, stream=None):
     """(median, nearest-rank q-quantile) of |a - ref| / |ref| over the
-    targets (nb_error_stats): acc (n, 3) float32, ref (nt, 3) float64."""
+    targets (nb_error_stats): acc (n, 3) float32, ref (nt, 3) float64;
+    err_out (nt,) float32 receives the per-target errors when given."""
     import torch
     nt = int(ref.shape[0])
     out = torch.empty(2, dtype=torch.float64, device=ref.device)
-    err = torch.empty(max(nt, 1), dtype=torch.float32, device=ref.device)
+    err = err_out if err_out is not None else \
+        torch.empty(max(nt, 1), dtype=torch.float32, device=ref.device)
     _check(_lib.nb_error_stats(_dptr(acc, torch.float32, 3, "acc"),
                                _dptr(ref, torch.float64, 3, "ref"),
                                _dptr(targets, torch.int64, None, "targets"), nt, float(q),
-                               out.data_ptr(), err.data_ptr(), _stream_handle(stream)),
-           "nb_error_stats")
+                               out.data_ptr(), _dptr(err, torch.float32, None, "err_out"),
+                               _stream_handle(stream)), "nb_error_stats")
     o = out.cpu().numpy()
     return float(o[0]), float(o[1])
 

@@ -277,12 +277,32 @@ __device__ void allocate(double lam, const double *pe, const double *pc, const f
     __syncthreads();
 }
 
+// the statistic the bisection holds at the budget: the n_g-weighted median
+// of the groups' measured median errors, or (perr given) the median over the
+// judged particles of their own errors at their group's chosen theta
+__device__ double allocation_stat(const float *err, const float *nsz, int64_t S, double half,
+                                  const int32_t *tsel, const float *vals, const float *perr,
+                                  const int64_t *poff, int64_t P, float *pvals, double *red)
+{
+    if (!perr) return (double)select_weighted(vals, nsz, S, half, red);
+    for (int64_t g = threadIdx.x; g < S; g += blockDim.x) {
+        const int64_t t = tsel[g];
+        for (int64_t q = poff[g]; q < poff[g + 1]; q++) pvals[q] = perr[t * P + q];
+    }
+    __syncthreads();
+    const float a = select_weighted(pvals, nullptr, P, (double)((P - 1) / 2 + 1), red);
+    const float b = select_weighted(pvals, nullptr, P, (double)(P / 2 + 1), red);
+    return 0.5 * ((double)a + (double)b);
+}
+
 __global__ void __launch_bounds__(LB_T)
 k_theta_allocate(const double *__restrict__ pe, const double *__restrict__ pc,
                  const float *__restrict__ err, const float *__restrict__ cost,
                  const float *__restrict__ nsz, const float *__restrict__ grid, int T, int64_t S,
-                 double budget, double lam_lo, double lam_hi, int iters, int32_t *tsel,
-                 float *vals, float *__restrict__ labels, double *__restrict__ result)
+                 double budget, double lam_lo, double lam_hi, int iters,
+                 const float *__restrict__ perr, const int64_t *__restrict__ poff, int64_t P,
+                 int32_t *tsel, float *vals, float *pvals, float *__restrict__ labels,
+                 double *__restrict__ result)
 {
     __shared__ double red[LB_T / 32];
     double W = 0.0;
@@ -293,16 +313,16 @@ k_theta_allocate(const double *__restrict__ pe, const double *__restrict__ pc,
     for (int it = 0; it < iters; it++) {
         const double mid = sqrt(lo * hi);
         allocate(mid, pe, pc, err, cost, nsz, T, S, tsel, vals);
-        const float wm = select_weighted(vals, nsz, S, half, red);
-        if ((double)wm > budget) lo = mid;
+        const double st = allocation_stat(err, nsz, S, half, tsel, vals, perr, poff, P, pvals, red);
+        if (st > budget) lo = mid;
         else hi = mid;
     }
     allocate(hi, pe, pc, err, cost, nsz, T, S, tsel, vals);
-    const float wm = select_weighted(vals, nsz, S, half, red);
+    const double st = allocation_stat(err, nsz, S, half, tsel, vals, perr, poff, P, pvals, red);
     for (int64_t i = threadIdx.x; i < S; i += blockDim.x) labels[i] = grid[tsel[i]];
     if (threadIdx.x == 0) {
         result[0] = hi;
-        result[1] = (double)wm;
+        result[1] = st;
     }
 }
 
@@ -386,29 +406,61 @@ extern "C" int nb_theta_fit_curves(const float *feat_dev, int64_t S, int stride,
     return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
 }
 
-extern "C" size_t nb_theta_allocate_workspace_size(int64_t S)
+extern "C" size_t nb_theta_allocate_workspace_size(int64_t S, int64_t P)
 {
-    return S < 1 ? 0 : al256(sizeof(int32_t) * S) + al256(sizeof(float) * S);
+    return S < 1 || P < 0 ? 0
+                          : al256(sizeof(int32_t) * S) + al256(sizeof(float) * S) +
+                                al256(sizeof(float) * (P > 0 ? P : 1));
+}
+
+// per-particle statistic: poff (S + 1) must run from 0 to P without
+// decreasing, since it decides every index the allocation kernel writes;
+// one pass checks it before that kernel runs
+__global__ void k_check_poff(const int64_t *__restrict__ poff, int64_t S, int64_t P,
+                             int *__restrict__ bad)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < S;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = poff[g], b = poff[g + 1];
+        if (a < 0 || b < a || b > P || (g == 0 && a != 0) || (g == S - 1 && b != P)) *bad = 1;
+    }
 }
 
 extern "C" int nb_theta_allocate(const double *pred_lnerr_dev, const double *pred_cost_dev,
                                  const float *err_dev, const float *cost_dev,
                                  const float *size_dev, const float *grid_dev, int T, int64_t S,
                                  double budget, double lam_lo, double lam_hi, int iters,
+                                 const float *perr_dev, const int64_t *poff_dev, int64_t P,
                                  float *labels_dev, double *result_dev, void *work_dev,
                                  size_t work_bytes, void *stream)
 {
     if (T < 1 || S < 1 || !err_dev || !size_dev || !grid_dev || !labels_dev || !result_dev ||
         !work_dev || (!pred_cost_dev && !cost_dev) || !(lam_lo > 0.0) || !(lam_hi >= lam_lo) ||
-        !isfinite(lam_hi) || iters < 0 || iters > 200 || !(budget >= 0.0))
+        !isfinite(lam_hi) || iters < 0 || iters > 200 || !(budget >= 0.0) ||
+        (perr_dev && (!poff_dev || P < 1)))
         return NB_ERR_INVALID_ARG;
-    if (work_bytes < nb_theta_allocate_workspace_size(S) || ((uintptr_t)work_dev & 255u))
+    if (!perr_dev) P = 0;
+    if (work_bytes < nb_theta_allocate_workspace_size(S, P) || ((uintptr_t)work_dev & 255u))
         return NB_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
     int32_t *tsel = (int32_t *)work_dev;
     float *vals = (float *)((char *)work_dev + al256(sizeof(int32_t) * S));
-    k_theta_allocate<<<1, LB_T, 0, (cudaStream_t)stream>>>(
-        pred_lnerr_dev, pred_cost_dev, err_dev, cost_dev, size_dev, grid_dev, T, S, budget, lam_lo,
-        lam_hi, iters, tsel, vals, labels_dev, result_dev);
+    float *pvals = (float *)((char *)vals + al256(sizeof(float) * S));
+    if (perr_dev) {
+        // the offsets decide every index the kernel writes: checked first
+        int *bad = (int *)pvals;
+        int hbad = 0;
+        if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) return NB_ERR_CUDA;
+        k_check_poff<<<nb_grid(S, 256, 1024), 256, 0, s>>>(poff_dev, S, P, bad);
+        if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return NB_ERR_CUDA;
+        if (hbad) return NB_ERR_INVALID_ARG;
+    }
+    k_theta_allocate<<<1, LB_T, 0, s>>>(pred_lnerr_dev, pred_cost_dev, err_dev, cost_dev,
+                                        size_dev, grid_dev, T, S, budget, lam_lo, lam_hi, iters,
+                                        perr_dev, poff_dev, P, tsel, vals, pvals, labels_dev,
+                                        result_dev);
     return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
 }
 

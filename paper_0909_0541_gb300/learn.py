@@ -74,7 +74,7 @@ TREE_COLS = [0, 1, 2, 3, 4, 5, 11]   # the features of feature mode 1 (no walk)
 
 def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget=BUDGET,
                  ctx: NBody | None = None, feature_mode=0, label_rule="measured",
-                 walk_weight=0.0):
+                 walk_weight=0.0, label_stat="groups"):
     """(features (S,16), labels (S,), info) for S seeded random groups of the
     particle set (pos, mass: CUDA tensors); info holds the error and cost
     curves, the group sizes, the sampled groups and the exchange rate.
@@ -84,7 +84,9 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
     features of the feature mode).  A group's cost at a theta is its
     interactions, n_g (list length + n_g), plus walk_weight x list length: the
     walk's time per list entry in units of the force's time per interaction
-    (0: interactions only)."""
+    (0: interactions only).  label_stat: the error statistic the exchange rate
+    is bisected on, "groups" (n_g-weighted median of group medians) or
+    "particles" (median over the judged particles)."""
     import torch
     n = int(pos.shape[0])
     own = ctx is None
@@ -103,11 +105,15 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
     ref, _ = direct_sum(pos, mass, eps, t_dev)
     acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
     errs = torch.empty((len(grid), len(sel)), dtype=torch.float32, device=dev)
+    perr = torch.empty((len(grid), len(targets)), dtype=torch.float32, device=dev) \
+        if label_stat == "particles" else None
     cost = np.zeros((len(grid), len(sel)), np.float32)
     for t, th in enumerate(grid):
         ctx.walk_groups(float(th), n_crit)
         ctx.forces(eps, acc)
         errs[t] = group_errors(acc, ref, t_dev, o_dev)
+        if perr is not None:
+            error_stats(acc, ref, t_dev, err_out=perr[t])
         ln = ctx.copy_group_lengths()[sel]
         cost[t] = size * (ln + size) + walk_weight * ln
     grid_d = torch.from_numpy(np.asarray(grid, np.float32)).to(dev)
@@ -118,9 +124,10 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
         cols = TREE_COLS if feature_mode == 1 else list(range(NIN))
         pred = theta_fit_curves(X, errs, cost_d, cols)
         labels, hi, werr = theta_allocate(errs, cost_d, size_d, grid_d, budget, 1e-3, 1e9, 60,
-                                          pred=pred)
+                                          pred=pred, perr=perr, poff=o_dev)
     else:
-        labels, hi, werr = theta_allocate(errs, cost_d, size_d, grid_d, budget, 1.0, 1e6, 40)
+        labels, hi, werr = theta_allocate(errs, cost_d, size_d, grid_d, budget, 1.0, 1e6, 40,
+                                          perr=perr, poff=o_dev)
     E = errs.cpu().numpy()
     if own:
         ctx.close()

@@ -80,6 +80,31 @@ def test_allocation_matches_oracle(rule):
     assert clear.mean() > 0.99
 
 
+def test_allocation_particle_median_matches_oracle():
+    """The bisection held on the median over particles (per-particle errors
+    and group offsets) instead of the weighted median of group medians."""
+    import paper_0909_0541_gb300 as nb
+    X, E, C, size, grid = synthetic(S=3000)
+    rng = np.random.default_rng(9)
+    poff = np.r_[0, np.cumsum(size.astype(np.int64))].astype(np.int64)
+    P = int(poff[-1])
+    gid = np.repeat(np.arange(len(size)), size.astype(np.int64))
+    perr = (E[:, gid] * np.exp(0.4 * rng.normal(size=(E.shape[0], P)))).astype(np.float32)
+    lab, lam, st = nb.theta_allocate(_dev(E), _dev(C), _dev(size), _dev(grid), 1e-3, 1.0, 1e6,
+                                     40, perr=_dev(perr), poff=_dev(poff))
+    rlab, rlam, rst = olab.allocate(E, C, size, grid, 1e-3, 1.0, 1e6, 40, perr=perr, poff=poff)
+    assert abs(lam - rlam) <= 1e-9 * rlam and st == rst and st <= 1e-3
+    obj = C.astype(np.float64) / size[None, :] + rlam * np.log(np.maximum(E, 1e-9))
+    srt = np.sort(obj, axis=0)
+    clear = (srt[1] - srt[0]) > 1e-9 * np.abs(srt[0])
+    assert np.array_equal(lab.cpu().numpy()[clear], rlab[clear])
+    bad = poff.copy()
+    bad[5] = bad[6] + 1                                 # decreasing offsets: rejected
+    with pytest.raises(nb.NBError):
+        nb.theta_allocate(_dev(E), _dev(C), _dev(size), _dev(grid), 1e-3, 1.0, 1e6, 40,
+                          perr=_dev(perr), poff=_dev(bad))
+
+
 def test_allocation_edge_sizes():
     import paper_0909_0541_gb300 as nb
     X, E, C, size, grid = synthetic(S=1)
