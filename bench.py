@@ -67,6 +67,10 @@ def parse():
                          "median of group medians)")
     ap.add_argument("--no-learned", action="store_true",
                     help="leave the learned-vs-fixed-theta comparison out of the default line")
+    ap.add_argument("--quadstudy", action="store_true",
+                    help="monopole vs quadrupole cells at equal median error on --workload")
+    ap.add_argument("--quadrupole", action="store_true",
+                    help="the timed steps use quadrupole cells")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -371,6 +375,8 @@ def run_ours(args, ws, rank, local):
     if args.fused:
         ctx.set_fused(True)
     ctx.set_key_order(args.order)
+    if args.quadrupole:
+        ctx.set_quadrupole(True)
     dt = w["dt"]
     with torch.cuda.stream(stream):
         # first step synchronises: sizes the interaction-list storage
@@ -467,7 +473,7 @@ def run_ours(args, ws, rank, local):
         tg = torch.randperm(n, generator=g)[: args.judge_targets].to(dev)
         aj, _ = nb.direct_sum(pos0, mass, w["eps"], tg, stream=stream)
         acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
-        for mode in ("fp32", "fp32_comp", "fp64acc"):
+        for mode in (("fp32", "fp32_comp") if args.quadrupole else ("fp32", "fp32_comp", "fp64acc")):
             p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             p0.record(stream)
             ctx.forces(w["eps"], acc, None, mode)
@@ -531,6 +537,7 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args.workload, n, w, ws),
             "run": {"precision": args.precision, "key_order": args.order,
+                    "cells": "quadrupole" if args.quadrupole else "monopole",
                     "force_path": "fused walk+force" if args.fused else "lists",
                     "launch": ((f"eager (graph capture failed: {graph_failed})"
                                 if graph_failed else
@@ -704,6 +711,88 @@ def run_learned(args, ws, rank, local):
     line.update({k: r[k] for k in ("learned", "fixed_theta_matched", "fixed_theta_0.6",
                                    "interaction_gain_vs_matched", "time_gain_vs_matched",
                                    "training", "judge", "clocks")})
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- quadrupole cells
+def run_quadstudy(args, ws, rank, local):
+    """Monopole against quadrupole cells at equal median error (Sec. "Oct-tree
+    Method": "any high order moment"): on the given workload, theta is
+    bisected for each form to reach median |da|/|a| budgets of 2e-4 and 1e-3
+    against the FP64 direct sum (8192 targets), then the build and walk +
+    force at that theta are timed (CUDA events on the library's stream,
+    median of 5), with the SM clock sampled during the timed repetitions."""
+    import torch
+
+    import nbsynth
+    import paper_0909_0541_gb300 as nb
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ps, w = nbsynth.workload(args.workload)
+    n_crit, eps = w["n_crit"], w["eps"]
+    pos = torch.from_numpy(ps.pos).to(dev)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    g = torch.Generator().manual_seed(99)
+    tg = torch.randperm(ps.n, generator=g)[: args.judge_targets].to(dev)
+    ref, _ = nb.direct_sum(pos, mass, eps, tg)
+    acc = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    marks = []
+    out = {}
+    for form in ("monopole", "quadrupole"):
+        ctx = nb.NBody(ps.n, eps=eps, n_crit=n_crit)
+        ctx.set_quadrupole(form == "quadrupole")
+        ctx.build_tree(pos, mass)
+
+        def err_at(theta):
+            ctx.walk_groups(theta, n_crit)
+            ctx.forces(eps, acc)
+            return nb.error_stats(acc, ref, tg)[0]
+
+        rows = {}
+        for budget in (2e-4, 1e-3):
+            lo, hi = 0.05, 1.6
+            for _ in range(14):
+                mid = 0.5 * (lo + hi)
+                if err_at(mid) > budget:
+                    hi = mid
+                else:
+                    lo = mid
+            theta = lo
+            med = err_at(theta)
+            st = ctx.stats()
+            ctx.set_sync_checks(False)
+            wf, bd = [], []
+            t0 = sampler.mark()
+            for _ in range(5):
+                ctx.set_timing(True)
+                ctx.get_timing()
+                ctx.build_tree(pos, mass)
+                ctx.walk_groups(theta, n_crit)
+                ctx.forces(eps, acc)
+                tm = ctx.get_timing()
+                ctx.set_timing(False)
+                wf.append(tm["walk"][0] + tm["force"][0])
+                bd.append(tm["build"][0])
+            marks.append((t0, sampler.mark()))
+            ctx.sync_status()
+            ctx.set_sync_checks(True)
+            rows[f"{budget:g}"] = {"theta": theta, "median_rel_err": med,
+                                   "n_pp": st["n_pp"], "n_pc": st["n_pc"],
+                                   "walk_force_ms": statistics.median(wf),
+                                   "build_ms": statistics.median(bd)}
+        out[form] = rows
+        ctx.close()
+    clocks = sampler.stop(marks[0][0], marks[-1][1])
+    gain = {b: 1.0 - out["quadrupole"][b]["walk_force_ms"] / out["monopole"][b]["walk_force_ms"]
+            for b in out["monopole"]}
+    line = {"metric": "walk + force ms at equal median |da|/|a|: quadrupole vs monopole cells",
+            "value": gain["0.0002"], "unit": "fractional time saved at a 2e-4 budget",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": ps.n, "eps": eps, "n_crit": n_crit,
+                       "judge": f"nb_direct_sum (FP64), {args.judge_targets} targets"},
+            "forms": out, "time_gain_by_budget": gain, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -910,6 +999,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "crossover":
         run_crossover(args, ws, rank, local)
+    elif args.quadstudy:
+        run_quadstudy(args, ws, rank, local)
     elif args.workload == "learned4.19m":
         run_learned(args, ws, rank, local)
     else:

@@ -190,6 +190,28 @@ int nb_set_fused(nb_ctx *ctx, int on);
 #define NB_ORDER_HILBERT 1
 int nb_set_key_order(nb_ctx *ctx, int order);
 
+/* Quadrupole cells ("any high order moment" in the particle-cell term, Sec.
+ * "Oct-tree Method"; the paper itself uses the monopole).  With on != 0 the
+ * next tree builds also fold every cell's traceless quadrupole about its
+ * centre of mass, Q_ab = sum_k m_k (3 d_a d_b - |d|^2 delta_ab), d = x_k -
+ * COM, in FP64 bottom-up by the parallel-axis theorem; walks store each
+ * accepted cell's Q in FP32 beside its list record (in each 32-node chunk
+ * of the walk the accepted cells come before the particles); and nb_forces
+ * adds to every particle-cell term, softened like Eq. (gravity) with R^2 =
+ * |r|^2 + eps^2, r = x_i - COM:
+ *   a += Q r / R^5 - (5/2) (r.Q.r) r / R^7,   phi += -(1/2) r.Q.r / R^5.
+ * Switching on allocates 48 B per node slot of cfg.max_n (NOMEM on
+ * failure), and list storage then takes 32 B more per entry.  In this mode
+ * nb_forces takes NB_FP32 or NB_FP32_COMP (NB_FP64ACC: INVALID_ARG), a walk
+ * needs a tree built in this mode (else STATE), and nb_forces_fused and
+ * nb_set_fused's force passes are INVALID_ARG.  The opening test is
+ * unchanged, so the lists hold the same sets of nodes as without. */
+int nb_set_quadrupole(nb_ctx *ctx, int on);
+/* The quadrupoles of the current tree (built with nb_set_quadrupole on),
+ * n_nodes x 6 FP64 (xx, yy, zz, xy, xz, yz) in depth-first preorder, zero
+ * for particles; synchronising debug export. */
+int nb_copy_quadrupoles(nb_ctx *ctx, double *q_host);
+
 /* One kick-drift-kick leapfrog step of size dt in FP64 ("integrate orbits
  * ... and repeat", Sec. Introduction): v += a dt/2; x += v dt; rebuild the
  * tree, walk and force with cfg.eps, cfg.theta, cfg.n_crit, cfg.precision;

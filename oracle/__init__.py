@@ -67,7 +67,7 @@ def lib():
             L.or_tree_export_quad.restype = C.c_int
             L.or_tree_export_quad.argtypes = [vp, vp]
             L.or_tree_forces_quad.restype = C.c_int
-            L.or_tree_forces_quad.argtypes = [vp, i64, f64, f64, vp, vp, vp, vp]
+            L.or_tree_forces_quad.argtypes = [vp, i64, f64, f64, vp, vp, vp, vp, vp, C.c_int]
             L.or_neighbours.restype = i64
             L.or_neighbours.argtypes = [vp, f64, C.c_int, i64, vp, vp, i64]
             L.or_neighbours_brute.restype = i64
@@ -228,16 +228,20 @@ class Tree:
         assert lib().or_tree_export_quad(self._h, _ptr(Q)) == 0
         return Q
 
-    def forces_quad(self, n_crit, theta, eps):
+    def forces_quad(self, n_crit, theta, eps, with_amag=False, coords32=False):
         """forces() with the quadrupole term of every accepted cell:
-        (acc, pot, npp, npc)."""
+        (acc, pot, npp, npc), plus sum_j |a_ij| of the monopole terms when
+        with_amag; coords32 as in forces()."""
         acc = np.full((self.n, 3), np.nan)
         pot = np.full(self.n, np.nan)
+        am = np.full(self.n, np.nan) if with_amag else None
         npp, npc = C.c_int64(0), C.c_int64(0)
         rc = lib().or_tree_forces_quad(self._h, int(n_crit), float(theta), float(eps),
-                                       _ptr(acc), _ptr(pot), C.byref(npp), C.byref(npc))
+                                       _ptr(acc), _ptr(pot), _ptr(am), C.byref(npp),
+                                       C.byref(npc), 1 if coords32 else 0)
         assert rc == 0
-        return acc, pot, int(npp.value), int(npc.value)
+        out = (acc, pot, int(npp.value), int(npc.value))
+        return out + (am,) if with_amag else out
 
     def neighbours(self, h, group_form=False, n_crit=64):
         """Fixed-radius neighbours by the general treewalk: (offsets n+1,

@@ -1099,13 +1099,17 @@ int or_tree_forces(const or_tree *t, int64_t n_crit, double theta,
                        npc, coords32, 0);
 }
 
-/* the same with the quadrupole term of accepted cells (FP64 coordinates) */
+/* the same with the quadrupole term of accepted cells (FP64 coordinates, or
+ * with coords32 the group-relative FP32 coordinates and FP32 masses of
+ * or_tree_forces; the quadrupoles stay FP64); amag (nullable) as there */
 int or_tree_forces_quad(or_tree *t, int64_t n_crit, double theta, double eps,
-                        double *acc, double *pot, int64_t *npp, int64_t *npc)
+                        double *acc, double *pot, double *amag, int64_t *npp, int64_t *npc,
+                        int coords32)
 {
     if (or_tree_quadrupoles(t))
         return -1;
-    return tree_forces(t, n_crit, theta, NULL, eps, 0, NULL, acc, pot, NULL, npp, npc, 0, 1);
+    return tree_forces(t, n_crit, theta, NULL, eps, 0, NULL, acc, pot, amag, npp, npc,
+                       coords32, 1);
 }
 
 static int tree_forces(const or_tree *t, int64_t n_crit, double theta,

@@ -41,7 +41,8 @@ EXPORTED = [
     "nb_leapfrog_step_host", "nb_forces_fused", "nb_set_fused", "nb_set_feature_mode",
     "nb_direct_f32", "nb_direct_f32_workspace_size", "nb_set_key_order",
     "nb_theta_fit_workspace_size", "nb_theta_fit_curves", "nb_theta_allocate_workspace_size",
-    "nb_theta_allocate", "nb_error_stats", "nb_column_stats",
+    "nb_theta_allocate", "nb_error_stats", "nb_column_stats", "nb_set_quadrupole",
+    "nb_copy_quadrupoles",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -90,6 +91,8 @@ def _load():
     L.nb_forces_fused.argtypes = [vp, C.c_float, i32, C.c_float, vp, vp, i32]
     L.nb_set_fused.argtypes = [vp, i32]
     L.nb_set_key_order.argtypes = [vp, i32]
+    L.nb_set_quadrupole.argtypes = [vp, i32]
+    L.nb_copy_quadrupoles.argtypes = [vp, vp]
     L.nb_set_feature_mode.argtypes = [vp, i32]
     L.nb_leapfrog_step.argtypes = [vp, vp, vp, vp, i64, C.c_double]
     L.nb_leapfrog_reset.argtypes = [vp]
@@ -317,6 +320,16 @@ class NBody:
     def set_key_order(self, order: str):
         """Particle order of the next builds: "morton" (default) or "hilbert"."""
         _check(_lib.nb_set_key_order(self._h, KEY_ORDER[order]), "nb_set_key_order")
+
+    def set_quadrupole(self, on: bool):
+        """Quadrupole cells from the next build on (nb_set_quadrupole)."""
+        _check(_lib.nb_set_quadrupole(self._h, 1 if on else 0), "nb_set_quadrupole")
+
+    def copy_quadrupoles(self) -> np.ndarray:
+        """(n_nodes, 6) FP64 quadrupoles of the current tree, preorder."""
+        q = np.zeros((self.stats()["n_nodes"], 6))
+        _check(_lib.nb_copy_quadrupoles(self._h, _hptr(q)), "nb_copy_quadrupoles")
+        return q
 
     def set_fused(self, on: bool):
         """Leapfrog force passes without interaction lists (nb_set_fused)."""

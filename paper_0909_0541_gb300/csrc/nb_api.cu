@@ -53,10 +53,12 @@ static void free_all(nb_ctx *c)
 {
     // three device allocations: the context arena, the list storage, the
     // walk queues
-    void *ptrs[] = {c->arena, c->list_mem, c->wq, c->hstage};
+    void *ptrs[] = {c->arena, c->list_mem, c->wq, c->hstage, c->b_q};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->arena = c->list_mem = c->hstage = nullptr;
+    c->b_q = nullptr;
+    c->list_q = nullptr;
     c->wq = nullptr;
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->ev_drift) cudaEventDestroy(c->ev_drift);
@@ -304,23 +306,29 @@ static void phase_end(nb_ctx *c, int k, int phase)
 
 // List storage: list_xm (16 B) and list_id (4 B) per entry in one
 // allocation with 1/8 headroom, replaced only when a walk needs more.
+// In the quadrupole mode the same allocation also holds list_q (32 B per
+// entry) after list_id.
 static int ensure_lists(nb_ctx *c, int64_t groups, int64_t cap)
 {
     const int64_t need = groups * cap;
-    if (need <= c->list_alloc && cap == c->list_cap) return NB_OK;
-    if (need > c->list_alloc) {
+    const bool want_q = c->quad && !c->list_q;
+    if (need <= c->list_alloc && cap == c->list_cap && !want_q) return NB_OK;
+    if (need > c->list_alloc || want_q) {
         CK(cudaStreamSynchronize(c->stream));
         if (c->list_mem) cudaFree(c->list_mem);
         c->list_mem = nullptr;
         c->list_id = nullptr;
         c->list_xm = nullptr;
+        c->list_q = nullptr;
         c->list_alloc = 0;
         const int64_t want = need + need / 8;
         const size_t xm_bytes = (sizeof(float4) * (size_t)want + 255) & ~(size_t)255;
-        if (!dmalloc(&c->list_mem, xm_bytes + sizeof(int32_t) * (size_t)want))
-            return NB_ERR_NOMEM;
+        const size_t id_bytes = (sizeof(int32_t) * (size_t)want + 255) & ~(size_t)255;
+        const size_t q_bytes = c->quad ? 2 * sizeof(float4) * (size_t)want : 0;
+        if (!dmalloc(&c->list_mem, xm_bytes + id_bytes + q_bytes)) return NB_ERR_NOMEM;
         c->list_xm = (float4 *)c->list_mem;
         c->list_id = (int32_t *)((char *)c->list_mem + xm_bytes);
+        if (c->quad) c->list_q = (float4 *)((char *)c->list_mem + xm_bytes + id_bytes);
         c->list_alloc = want;
     }
     c->list_cap = cap;
@@ -434,6 +442,7 @@ int nb_build_tree(nb_ctx *c, const double *pos, const float *mass, int64_t n)
     c->has_lists = 0;
     c->n = n;
     c->nsys = 1;
+    c->tree_quad = c->quad && c->b_q;
     if (n == 0) {
         CK(cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_PP_CUM, c->stream));
         c->has_tree = 1;
@@ -458,6 +467,7 @@ int nb_build_tree_batched(nb_ctx *c, const double *pos, const float *mass,
     c->n = n;
     c->nsys = nsys;
     c->sys_off = offsets;
+    c->tree_quad = c->quad && c->b_q;
     const int tk = phase_begin(c);
     if (nsys == 1) nb_launch_build(c, pos, mass, n);
     else nb_launch_build_batched(c, pos, mass, n, offsets, nsys);
@@ -471,13 +481,14 @@ int nb_build_tree_batched(nb_ctx *c, const double *pos, const float *mass,
 static int walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g, bool formed)
 {
     if (!c) return NB_ERR_INVALID_ARG;
-    if (!c->has_tree) return NB_ERR_STATE;
+    if (!c->has_tree || (c->quad && !c->tree_quad)) return NB_ERR_STATE;
     if (!(theta >= 0.f) || n_crit < 1) return NB_ERR_INVALID_ARG;
     c->has_lists = 0;
     c->n_crit_cur = n_crit;
     if (c->n == 0) {
         c->groups_host = 0;
         c->has_lists = 1;
+        c->lists_quad = c->quad;
         return NB_OK;
     }
     const int tk = phase_begin(c);
@@ -527,13 +538,15 @@ static int walk_groups(nb_ctx *c, float theta, int n_crit, const float *theta_g,
         phase_end(c, tk, NB_PHASE_WALK);
         if (rc) return rc;
     } else {
-        if (c->list_cap < 1 || !c->list_id || !c->wq) return NB_ERR_CAPACITY;
+        if (c->list_cap < 1 || !c->list_id || !c->wq || (c->quad && !c->list_q))
+            return NB_ERR_CAPACITY;
         nb_launch_walk(c);
         phase_end(c, tk, NB_PHASE_WALK);
         int rc = finish(c);
         if (rc) return rc;
     }
     c->has_lists = 1;
+    c->lists_quad = c->quad;
     return NB_OK;
 }
 
@@ -617,8 +630,9 @@ int nb_walk_groups_learned(nb_ctx *c, int n_crit, const float *params, float fal
 int nb_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision)
 {
     if (!c) return NB_ERR_INVALID_ARG;
-    if (!c->has_lists) return NB_ERR_STATE;
-    if (!(eps >= 0.f) || precision < 0 || precision > 2 || (c->n > 0 && !acc))
+    if (!c->has_lists || (c->quad && !c->lists_quad)) return NB_ERR_STATE;
+    if (!(eps >= 0.f) || precision < 0 || precision > 2 || (c->n > 0 && !acc) ||
+        (c->quad && precision == NB_FP64ACC))
         return NB_ERR_INVALID_ARG;
     if (c->n == 0) return NB_OK;
     const int tk = phase_begin(c);
@@ -632,7 +646,7 @@ int nb_forces_fused(nb_ctx *c, float theta, int n_crit, float eps, float *acc, f
 {
     if (!c) return NB_ERR_INVALID_ARG;
     if (!(theta >= 0.f) || n_crit < 1 || !(eps >= 0.f) || precision < 0 || precision > 2 ||
-        (c->n > 0 && !acc))
+        (c->n > 0 && !acc) || c->quad)
         return NB_ERR_INVALID_ARG;
     if (!c->has_tree) return NB_ERR_STATE;
     c->has_lists = 0;   // the fused pass leaves no lists behind
@@ -710,6 +724,48 @@ int nb_set_key_order(nb_ctx *c, int order)
     if (order != c->key_order) c->acc_valid = 0;   // the kept a(x) was summed in the old order
     c->key_order = order;
     return NB_OK;
+}
+
+int nb_set_quadrupole(nb_ctx *c, int on)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (on && !c->b_q) {
+        CK(cudaStreamSynchronize(c->stream));
+        if (!dmalloc((void **)&c->b_q, sizeof(double) * 6 * (size_t)c->max_nodes))
+            return NB_ERR_NOMEM;
+    }
+    if ((on ? 1 : 0) != c->quad) c->acc_valid = 0;
+    c->quad = on ? 1 : 0;
+    return NB_OK;
+}
+
+int nb_copy_quadrupoles(nb_ctx *c, double *q_host)
+{
+    if (!c || !q_host) return NB_ERR_INVALID_ARG;
+    if (!c->has_tree || !c->tree_quad) return NB_ERR_STATE;
+    int rc = read_counters(c);
+    if (rc) return rc;
+    const int64_t nn = c->n > 0 ? c->cnt_host[CNT_NODES] : 0;
+    double *qb = (double *)malloc(sizeof(double) * 6 * (size_t)(nn > 0 ? nn : 1));
+    int32_t *map = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1));
+    if (!qb || !map) rc = NB_ERR_NOMEM;
+    if (!rc && nn > 0 &&
+        (cudaMemcpy(qb, c->b_q, sizeof(double) * 6 * (size_t)nn, cudaMemcpyDeviceToHost) !=
+             cudaSuccess ||
+         cudaMemcpy(map, c->pid2bfs, sizeof(int32_t) * (size_t)nn, cudaMemcpyDeviceToHost) !=
+             cudaSuccess))
+        rc = NB_ERR_CUDA;
+    for (int64_t u = 0; !rc && u < nn; u++) {
+        const int32_t b = map[u];
+        if (b < 0 || b >= nn) {
+            rc = NB_ERR_INTERNAL;
+            break;
+        }
+        for (int k = 0; k < 6; k++) q_host[6 * u + k] = qb[6 * (int64_t)b + k];
+    }
+    free(qb);
+    free(map);
+    return rc;
 }
 
 int nb_set_fused(nb_ctx *c, int on)

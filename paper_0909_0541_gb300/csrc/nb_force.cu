@@ -37,15 +37,17 @@
 
 // R targets per lane (R = 2 only with S = 1); S source streams: lane l is
 // target row l % W of stream l / W, W = 32 / S
-template <int MODE, bool GUARD, int R, int S, int TILE>
+// QUAD: list records carry the cells' quadrupoles (list_q) and the list
+// phase adds the quadrupole term (TILE = 32, FP32 modes)
+template <int MODE, bool GUARD, int R, int S, int TILE, bool QUAD>
 __device__ __forceinline__ void force_item(
     int32_t g, int32_t i0, float4 *tile, const int32_t *__restrict__ gfirst,
     const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
     const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
     const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
-    const float4 *__restrict__ list_xm, int64_t cap, int64_t alloc, int64_t n, float eps2,
-    float *__restrict__ acc, float *__restrict__ pot, long long *__restrict__ cnt,
-    unsigned *__restrict__ err)
+    const float4 *__restrict__ list_xm, const float4 *__restrict__ list_q, int64_t cap,
+    int64_t alloc, int64_t n, float eps2, float *__restrict__ acc, float *__restrict__ pot,
+    long long *__restrict__ cnt, unsigned *__restrict__ err)
 {
     constexpr int W = NB_WARP / S;
     const int lane = threadIdx.x & 31;
@@ -82,16 +84,35 @@ __device__ __forceinline__ void force_item(
     // (1) the list: sources outside the group, TILE records per tile
     constexpr int TK = TILE / NB_WARP;   // records each lane stages per tile
     const float4 *__restrict__ src = list_xm + (int64_t)g * cap;
-    for (int32_t j0 = 0; j0 < len; j0 += TILE) {
-#pragma unroll
-        for (int k = 0; k < TK; k++) {
-            const int32_t jj = j0 + k * NB_WARP + lane;
-            put_rec(tile, k * NB_WARP + lane, jj < len ? src[jj] : pad);
+    if constexpr (QUAD) {
+        static_assert(TILE == NB_WARP, "quadrupole tiles hold 32 records");
+        const float4 *__restrict__ srq = list_q + 2 * (int64_t)g * cap;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int32_t j0 = 0; j0 < len; j0 += TILE) {
+            const int32_t jj = j0 + lane;
+            const bool in = jj < len;
+            const float4 qa = in ? srq[2 * (int64_t)jj] : z4;
+            const float4 qb = in ? srq[2 * (int64_t)jj + 1] : z4;
+            put_rec_q(tile, lane, in ? src[jj] : pad, qa, qb);
+            const unsigned qm = __ballot_sync(0xffffffffu, qa.x != 0.f || qa.y != 0.f ||
+                                                               qa.z != 0.f || qa.w != 0.f ||
+                                                               qb.x != 0.f || qb.y != 0.f);
+            __syncwarp();
+            tile_pass_quad<MODE, GUARD, R, W>(tile, stream * W, t, eps2, qm, A, P);
+            __syncwarp();
         }
-        __syncwarp();
-        tile_pass<MODE, GUARD, false, R, W * TK>(tile, stream * W * TK, j0 + stream * W * TK, t,
-                                                 kk, eps2, A, P);
-        __syncwarp();
+    } else {
+        for (int32_t j0 = 0; j0 < len; j0 += TILE) {
+#pragma unroll
+            for (int k = 0; k < TK; k++) {
+                const int32_t jj = j0 + k * NB_WARP + lane;
+                put_rec(tile, k * NB_WARP + lane, jj < len ? src[jj] : pad);
+            }
+            __syncwarp();
+            tile_pass<MODE, GUARD, false, R, W * TK>(tile, stream * W * TK, j0 + stream * W * TK,
+                                                     t, kk, eps2, A, P);
+            __syncwarp();
+        }
     }
     // (2) the group's own members, j != i
     for (int32_t j0 = 0; j0 < ng; j0 += NB_WARP) {
@@ -212,18 +233,19 @@ k_item_order(const int32_t *__restrict__ items, const int32_t *__restrict__ gcou
 
 // TILE: list records staged per tile (the j-tile depth); BT: threads per
 // block.  Both are chosen by the autotuner for the FP32 mode.
-template <int MODE, bool GUARD, int TILE, int BT>
-__global__ void __launch_bounds__(BT, (MODE == MODE_F64 ? 5 : 4) * F_T / BT)
+template <int MODE, bool GUARD, int TILE, int BT, bool QUAD = false>
+__global__ void __launch_bounds__(BT, (QUAD ? 2 : MODE == MODE_F64 ? 5 : 4) * F_T / BT)
 k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
         const int32_t *__restrict__ gfirst,
         const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
         const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
         const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
-        const float4 *__restrict__ list_xm, int64_t cap, int64_t alloc, int64_t n,
-        long long *__restrict__ cnt, float eps2, float *__restrict__ acc, float *__restrict__ pot,
-        unsigned *__restrict__ err, int64_t max_items)
+        const float4 *__restrict__ list_xm, const float4 *__restrict__ list_q, int64_t cap,
+        int64_t alloc, int64_t n, long long *__restrict__ cnt, float eps2,
+        float *__restrict__ acc, float *__restrict__ pot, unsigned *__restrict__ err,
+        int64_t max_items)
 {
-    __shared__ float4 tiles[BT / NB_WARP][TILE];
+    __shared__ float4 tiles[BT / NB_WARP][QUAD ? TILE * 5 / 2 : TILE];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t nitems = (int32_t)cnt[CNT_ITEMS];
@@ -249,8 +271,9 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
             continue;
         }
 #define NB_FORCE_ITEM(R, S)                                                                   \
-    force_item<MODE, GUARD, R, S, TILE>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi, p_lo, \
-                                        perm, list_xm, cap, alloc, n, eps2, acc, pot, cnt, err)
+    force_item<MODE, GUARD, R, S, TILE, QUAD>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi,  \
+                                              p_lo, perm, list_xm, list_q, cap, alloc, n, eps2,   \
+                                              acc, pot, cnt, err)
         if (word & ITEM_R2) {
             NB_FORCE_ITEM(2, 1);
         } else {
@@ -267,20 +290,20 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
     }
 }
 
-template <int MODE, bool GUARD, int TILE, int BT>
+template <int MODE, bool GUARD, int TILE, int BT, bool QUAD = false>
 static void launch_force_t(nb_ctx *c, float eps2, float *acc, float *pot)
 {
     static int blocks = 0;
     if (blocks == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_force<MODE, GUARD, TILE, BT>, BT,
-                                                      0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks,
+                                                      k_force<MODE, GUARD, TILE, BT, QUAD>, BT, 0);
         if (blocks < 1) blocks = 1;
     }
-    k_force<MODE, GUARD, TILE, BT><<<c->num_sms * blocks, BT, 0, c->stream>>>(
+    k_force<MODE, GUARD, TILE, BT, QUAD><<<c->num_sms * blocks, BT, 0, c->stream>>>(
         c->items, c->item_order, c->gfirst, c->gcount, c->glen, c->gbox, c->p_hi, c->p_lo, c->perm,
-        c->list_xm, c->list_cap, c->list_alloc, c->n, c->cnt, eps2, acc, pot, c->err,
+        c->list_xm, c->list_q, c->list_cap, c->list_alloc, c->n, c->cnt, eps2, acc, pot, c->err,
         c->max_items);
-    nb_launched(c, "k_force");
+    nb_launched(c, QUAD ? "k_force (quadrupole)" : "k_force");
 }
 
 // FP32: the context's j-tile depth (32 or 64) and block size (256 or 128);
@@ -313,6 +336,15 @@ void nb_launch_forces(nb_ctx *c, float eps, float *acc, float *pot, int precisio
     nb_launched(c, "k_item_order");
     const float eps2 = eps * eps;
     const bool guard = !(eps2 >= FLT_MIN);
+    if (c->quad && c->lists_quad) {   // FP32 and compensated modes (checked by the caller)
+        switch (precision * 2 + (guard ? 1 : 0)) {
+        case 0: launch_force_t<MODE_FP32, false, F_TILE, F_T, true>(c, eps2, acc, pot); break;
+        case 1: launch_force_t<MODE_FP32, true, F_TILE, F_T, true>(c, eps2, acc, pot); break;
+        case 2: launch_force_t<MODE_COMP, false, F_TILE, F_T, true>(c, eps2, acc, pot); break;
+        default: launch_force_t<MODE_COMP, true, F_TILE, F_T, true>(c, eps2, acc, pot); break;
+        }
+        return;
+    }
     switch (precision * 2 + (guard ? 1 : 0)) {
     case 0: launch_force<MODE_FP32, false>(c, eps2, acc, pot); break;
     case 1: launch_force<MODE_FP32, true>(c, eps2, acc, pot); break;

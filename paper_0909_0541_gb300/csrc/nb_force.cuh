@@ -257,3 +257,166 @@ __device__ __forceinline__ void stream_sum(Acc<MODE> &A, int o)
     }
 }
 
+
+// ---------------------------------------------------------------- quadrupole
+// Cells carry their traceless quadrupole Q about the centre of mass; the
+// particle-cell term gains (softened like Eq. (gravity), R^2 = |r|^2 +
+// eps^2, r = x_i - COM = -d with d = COM - x_i):
+//   a += Q r / R^5 - (5/2) (r.Q.r) r / R^7 = -(Q d) R^-5 + (5/2)(d.Q.d) d R^-7
+//   phi += -(1/2) (d.Q.d) R^-5
+// The tile stores -Q, so with q' = (-Q) d and h = -(5/2) (d.(-Q).d) R^-7:
+//   a += q' R^-5 + h d,   and the potential sum (+m/R, negated at the end)
+//   gains (-1/2)(d.(-Q).d) R^-5.
+// Paired layout of a quadrupole tile: records 2p, 2p+1 share five slots,
+//   5p: {x, x', y, y'}  5p+1: {z, z', m, m'}  5p+2: {-Qxx, .., -Qyy, ..}
+//   5p+3: {-Qzz, .., -Qxy, ..}  5p+4: {-Qxz, .., -Qyz, ..}
+__device__ __forceinline__ void put_rec_q(float4 *tile, int j, float4 v, float4 qa, float4 qb)
+{
+    float *t = reinterpret_cast<float *>(tile) + 20 * (j >> 1) + (j & 1);
+    t[0] = v.x;
+    t[2] = v.y;
+    t[4] = v.z;
+    t[6] = v.w;
+    t[8] = -qa.x;
+    t[10] = -qa.y;
+    t[12] = -qa.z;
+    t[14] = -qa.w;
+    t[16] = -qb.x;
+    t[18] = -qb.y;
+}
+
+// two records against one target with packed FP32: the monopole steps of
+// interact2, then the quadrupole term
+template <bool GUARD>
+__device__ __forceinline__ void interact2_quad(const float4 *sl, const Tgt &t, float2 e2, Sum2 &P)
+{
+    const float4 a = sl[0], b = sl[1], c = sl[2], d = sl[3], e = sl[4];
+    const float2 dx = __fadd2_rn(make_float2(a.x, a.y), t.x);
+    const float2 dy = __fadd2_rn(make_float2(a.z, a.w), t.y);
+    const float2 dz = __fadd2_rn(make_float2(b.x, b.y), t.z);
+    float2 r2 = __ffma2_rn(dx, dx, e2);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const float2 m = make_float2(b.z, b.w);
+    float2 ri = make_float2(mufu_rsqrt(r2.x), mufu_rsqrt(r2.y));
+    if (GUARD) {
+        ri.x = r2.x >= FLT_MIN ? ri.x : 0.0f;
+        ri.y = r2.y >= FLT_MIN ? ri.y : 0.0f;
+    }
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    const float2 mr = __fmul2_rn(m, ri);
+    const float2 mr3 = __fmul2_rn(mr, ri2);
+    P.x = __ffma2_rn(mr3, dx, P.x);
+    P.y = __ffma2_rn(mr3, dy, P.y);
+    P.z = __ffma2_rn(mr3, dz, P.z);
+    P.p = __fadd2_rn(P.p, mr);
+    const float2 qxx = make_float2(c.x, c.y), qyy = make_float2(c.z, c.w);
+    const float2 qzz = make_float2(d.x, d.y), qxy = make_float2(d.z, d.w);
+    const float2 qxz = make_float2(e.x, e.y), qyz = make_float2(e.z, e.w);
+    float2 qx = __fmul2_rn(qxx, dx);
+    qx = __ffma2_rn(qxy, dy, qx);
+    qx = __ffma2_rn(qxz, dz, qx);
+    float2 qy = __fmul2_rn(qxy, dx);
+    qy = __ffma2_rn(qyy, dy, qy);
+    qy = __ffma2_rn(qyz, dz, qy);
+    float2 qz = __fmul2_rn(qxz, dx);
+    qz = __ffma2_rn(qyz, dy, qz);
+    qz = __ffma2_rn(qzz, dz, qz);
+    float2 dqd = __fmul2_rn(dx, qx);
+    dqd = __ffma2_rn(dy, qy, dqd);
+    dqd = __ffma2_rn(dz, qz, dqd);
+    const float2 ri5 = __fmul2_rn(__fmul2_rn(ri2, ri2), ri);
+    const float2 hp = __fmul2_rn(dqd, make_float2(-0.5f, -0.5f));
+    const float2 h = __fmul2_rn(__fmul2_rn(hp, make_float2(5.0f, 5.0f)), __fmul2_rn(ri5, ri2));
+    P.x = __ffma2_rn(ri5, qx, P.x);
+    P.y = __ffma2_rn(ri5, qy, P.y);
+    P.z = __ffma2_rn(ri5, qz, P.z);
+    P.x = __ffma2_rn(h, dx, P.x);
+    P.y = __ffma2_rn(h, dy, P.y);
+    P.z = __ffma2_rn(h, dz, P.z);
+    P.p = __ffma2_rn(hp, ri5, P.p);
+}
+
+// one record of a quadrupole tile, scalar (an odd-length stream), into the
+// .x halves
+template <bool GUARD>
+__device__ __forceinline__ void interact1_quad(const float4 *tile, int j, const Tgt &t, float eps2,
+                                               bool quad, Sum2 &P)
+{
+    const float *f = reinterpret_cast<const float *>(tile) + 20 * (j >> 1) + (j & 1);
+    const float dx = f[0] + t.x.x, dy = f[2] + t.y.x, dz = f[4] + t.z.x;
+    float r2 = fmaf(dx, dx, eps2);
+    r2 = fmaf(dy, dy, r2);
+    r2 = fmaf(dz, dz, r2);
+    float ri = mufu_rsqrt(r2);
+    if (GUARD) ri = r2 >= FLT_MIN ? ri : 0.0f;
+    const float ri2 = __fmul_rn(ri, ri);
+    const float mr = __fmul_rn(f[6], ri);
+    const float mr3 = __fmul_rn(mr, ri2);
+    P.x.x = fmaf(mr3, dx, P.x.x);
+    P.y.x = fmaf(mr3, dy, P.y.x);
+    P.z.x = fmaf(mr3, dz, P.z.x);
+    P.p.x = __fadd_rn(P.p.x, mr);
+    if (!quad) return;
+    const float qxx = f[8], qyy = f[10], qzz = f[12], qxy = f[14], qxz = f[16], qyz = f[18];
+    const float qx = fmaf(qxz, dz, fmaf(qxy, dy, qxx * dx));
+    const float qy = fmaf(qyz, dz, fmaf(qyy, dy, qxy * dx));
+    const float qz = fmaf(qzz, dz, fmaf(qyz, dy, qxz * dx));
+    const float dqd = fmaf(dz, qz, fmaf(dy, qy, dx * qx));
+    const float ri5 = ri2 * ri2 * ri;
+    const float hp = -0.5f * dqd;
+    const float h = (hp * 5.0f) * (ri5 * ri2);
+    P.x.x = fmaf(h, dx, fmaf(ri5, qx, P.x.x));
+    P.y.x = fmaf(h, dy, fmaf(ri5, qy, P.y.x));
+    P.z.x = fmaf(h, dz, fmaf(ri5, qz, P.z.x));
+    P.p.x = fmaf(hp, ri5, P.p.x);
+}
+
+// NJ records rb .. rb+NJ-1 of a quadrupole tile against the lane's R
+// targets.  qmask bit j: record j carries a quadrupole (a cell); pairs of
+// two particles take the monopole steps.  All lanes of one source stream read
+// the same records, so the choice is uniform within the stream.
+template <int MODE, bool GUARD, int R, int NJ>
+__device__ __forceinline__ void tile_pass_quad(const float4 *tile, int rb, const Tgt *t,
+                                               float eps2, unsigned qmask, Acc<MODE> *A, Sum2 *P)
+{
+    static_assert(MODE != MODE_F64, "the quadrupole pass sums in FP32");
+    if constexpr (NJ % 2 == 0) {
+        const float2 e2 = make_float2(eps2, eps2);
+#pragma unroll 4
+        for (int q = 0; q < NJ / 2; q++) {
+            const int j = rb + 2 * q;
+            const float4 *sl = tile + 5 * (j >> 1);
+            if ((qmask >> j) & 3u) {
+#pragma unroll
+                for (int r = 0; r < R; r++) interact2_quad<GUARD>(sl, t[r], e2, P[r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    interact2<GUARD, false>(sl[0], sl[1], t[r], e2, false, false, P[r]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < NJ; jj++) {
+            const int j = rb + jj;
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                interact1_quad<GUARD>(tile, j, t[r], eps2, (qmask >> j) & 1u, P[r]);
+        }
+    }
+    if constexpr (MODE == MODE_COMP) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            kahan(A[r].x, A[r].cx, P[r].x.x);
+            kahan(A[r].x, A[r].cx, P[r].x.y);
+            kahan(A[r].y, A[r].cy, P[r].y.x);
+            kahan(A[r].y, A[r].cy, P[r].y.y);
+            kahan(A[r].z, A[r].cz, P[r].z.x);
+            kahan(A[r].z, A[r].cz, P[r].z.y);
+            kahan(A[r].p, A[r].cp, -P[r].p.x);
+            kahan(A[r].p, A[r].cp, -P[r].p.y);
+            P[r].init();
+        }
+    }
+}

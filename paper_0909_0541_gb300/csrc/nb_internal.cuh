@@ -231,6 +231,14 @@ struct nb_ctx {
     int fused;               // leapfrog force passes use the fused walk and force
     int feature_mode;        // learned theta: 0 probe-walk features, 1 tree-only features
     int key_order;           // NB_ORDER_MORTON or NB_ORDER_HILBERT (next build)
+    // quadrupole cells: traceless Q (xx, yy, zz, xy, xz, yz) about the centre
+    // of mass per node in level order (FP64, allocated when first switched
+    // on), and two float4 per list entry (Qxx, Qyy, Qzz, Qxy | Qxz, Qyz, 0, 0)
+    int quad;
+    int tree_quad;    // the current tree's moments include Q
+    int lists_quad;   // the current lists carry Q (cells first in every chunk)
+    double *b_q;
+    float4 *list_q;
     int ev_used;
     int ev_graph;            // event pairs [0, ev_graph) are nodes of the captured graph
     int capturing;           // a graph capture is in progress on the stream

@@ -530,7 +530,8 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
               nb_wrec *__restrict__ wrec, double *__restrict__ b_mass, double *__restrict__ b_mx,
               double *__restrict__ b_com, int32_t *__restrict__ b_up,
               int32_t *__restrict__ lcount, int16_t *__restrict__ cbkt,
-              int32_t *__restrict__ cbkt_cnt, int64_t n, int hilbert, unsigned *__restrict__ err)
+              int32_t *__restrict__ cbkt_cnt, int64_t n, int hilbert, double *__restrict__ b_q,
+              unsigned *__restrict__ err)
 {
     __shared__ int32_t hb[NB_CBKT];   // cells per moments bucket in this block
     for (int k = threadIdx.x; k < NB_CBKT; k += blockDim.x) hb[k] = 0;
@@ -561,6 +562,9 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
             if (pb >= 0) atomicAdd(&lcount[pb], 1);   // a leaf child of pb (result unused)
             const double m = (double)h.w;
             b_mass[b] = m;
+            if (b_q)   // a particle has no quadrupole moment
+#pragma unroll
+                for (int k = 0; k < 6; k++) b_q[6 * (int64_t)b + k] = 0.0;
 #pragma unroll
             for (int d = 0; d < 3; d++) {
                 const double x = x64[3 * (int64_t)slot + d];
@@ -734,11 +738,77 @@ void nb_launch_wait_probe(nb_ctx *c, unsigned limit)
     nb_launched(c, "k_wait_probe");
 }
 
+// COM = sum(m x) / M, correctly rounded: one correctly rounded reciprocal
+// y = RN(1/M) shared by the three quotients, then Markstein's correction
+// q = RN(q0 + RN(a - M q0) y), q0 = RN(a y), which gives RN(a / M)
+// (Markstein 1990, IBM J. Res. Dev. 34(1)); s = |COM - geometric centre|
+// and the FP32 split of the record.  d2 starts as the first square: 0 + x = x
+// exactly for x >= 0.
+__device__ __forceinline__ void cell_com(int32_t b, int4 wb, double M, const double mx[3],
+                                         double *__restrict__ b_com, nb_wrec *__restrict__ wrec,
+                                         double com[3])
+{
+    const double y = M > 0.0 ? __drcp_rn(M) : 0.0;
+    double d2 = 0.0;
+    float hi[3], lo[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double g = b_com[3 * (int64_t)b + d];   // geometric centre
+        double cm = g;
+        if (M > 0.0) {
+            const double q0 = __dmul_rn(mx[d], y);
+            const double r = __fma_rn(-q0, M, mx[d]);
+            cm = __fma_rn(r, y, q0);
+        }
+        const double dd = __dsub_rn(cm, g);
+        d2 = d == 0 ? __dmul_rn(dd, dd) : __dadd_rn(d2, __dmul_rn(dd, dd));
+        hi[d] = __double2float_rn(cm);
+        lo[d] = __double2float_rn(__dsub_rn(cm, (double)hi[d]));
+        b_com[3 * (int64_t)b + d] = cm;
+        com[d] = cm;
+    }
+    const float lcf = wrec[b].c.x;
+    nb_wrec_put_lo(&wrec[b], make_float4(hi[0], hi[1], hi[2], __double2float_rn(M)),
+                   make_float4(lo[0], lo[1], lo[2], 0.0f));
+    nb_wrec_put_hi(&wrec[b], wb, lcf, __double2float_rn(__dsqrt_rn(d2)));
+}
+
+// Quadrupole of a cell about its centre of mass from its children's, by the
+// parallel-axis theorem: Q = sum_c [Q_c + m_c (3 d d^T - |d|^2 I)], d =
+// COM_c - COM, folded in octant order in FP64 (a particle child has Q_c = 0
+// and COM_c = its position).  The same moment as the sum over the cell's
+// members of m (3 d d^T - |d|^2 I) about the COM, reached by another route.
+__device__ __forceinline__ void cell_quad(int32_t b, int4 wb, const double com[3],
+                                          const double *b_mass, const double *b_com, double *b_q)
+{
+    double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int32_t k = 0; k < wb.w; k++) {
+        const int64_t c = (int64_t)wb.z + k;
+        const double m = __ldcg(&b_mass[c]);
+        double d[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) d[a] = __ldcg(&b_com[3 * c + a]) - com[a];
+        const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        q[0] += __ldcg(&b_q[6 * c + 0]) + m * (3.0 * d[0] * d[0] - d2);
+        q[1] += __ldcg(&b_q[6 * c + 1]) + m * (3.0 * d[1] * d[1] - d2);
+        q[2] += __ldcg(&b_q[6 * c + 2]) + m * (3.0 * d[2] * d[2] - d2);
+        q[3] += __ldcg(&b_q[6 * c + 3]) + m * 3.0 * d[0] * d[1];
+        q[4] += __ldcg(&b_q[6 * c + 4]) + m * 3.0 * d[0] * d[2];
+        q[5] += __ldcg(&b_q[6 * c + 5]) + m * 3.0 * d[1] * d[2];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) b_q[6 * (int64_t)b + k] = q[k];
+}
+
+// QUAD: the cell's centre of mass and quadrupole are finished before it
+// arrives at its parent (the parent's quadrupole needs both); otherwise the
+// arrival comes first and the centre of mass after it.
+template <bool QUAD>
 __global__ void __launch_bounds__(256)
 k_moments(const int32_t *__restrict__ clist, int64_t clist_len, nb_wrec *__restrict__ wrec,
           const int32_t *__restrict__ b_up, const int32_t *__restrict__ lcount, double *b_mass,
-          double *b_mx, double *__restrict__ b_com, int32_t *arrive, long long *__restrict__ cnt,
-          unsigned *err)
+          double *b_mx, double *b_com, double *b_q, int32_t *arrive,
+          long long *__restrict__ cnt, unsigned *err)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -793,39 +863,17 @@ k_moments(const int32_t *__restrict__ clist, int64_t clist_len, nb_wrec *__restr
 #pragma unroll
             for (int d = 0; d < 3; d++) b_mx[3 * (int64_t)b + d] = mx[d];
         }
-        __threadfence();   // the sums before the arrivals
+        double com[3];
+        if (QUAD && b >= 0) {
+            cell_com(b, wb, M, mx, b_com, wrec, com);
+            cell_quad(b, wb, com, b_mass, b_com, b_q);
+        }
+        __threadfence();   // the sums (and in QUAD the COM and Q) before the arrivals
         if (b >= 0) {
             const int32_t q = b_up[b];
             if (q >= 0 && nb_in(q < b, cnt, err, SITE_MOMENTS, b)) atomicAdd(&arrive[q], 1);
         }
-        if (b < 0) continue;
-        // COM = sum(m x) / M, correctly rounded: one correctly rounded
-        // reciprocal y = RN(1/M) shared by the three quotients, then
-        // Markstein's correction q = RN(q0 + RN(a - M q0) y), q0 = RN(a y),
-        // which gives RN(a / M) (Markstein 1990, IBM J. Res. Dev. 34(1)).
-        // d2 starts as the first square: 0 + x = x exactly for x >= 0.
-        const double y = M > 0.0 ? __drcp_rn(M) : 0.0;
-        double d2 = 0.0;
-        float hi[3], lo[3];
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const double g = b_com[3 * (int64_t)b + d];   // geometric centre
-            double com = g;
-            if (M > 0.0) {
-                const double q0 = __dmul_rn(mx[d], y);
-                const double r = __fma_rn(-q0, M, mx[d]);
-                com = __fma_rn(r, y, q0);
-            }
-            const double dd = __dsub_rn(com, g);
-            d2 = d == 0 ? __dmul_rn(dd, dd) : __dadd_rn(d2, __dmul_rn(dd, dd));
-            hi[d] = __double2float_rn(com);
-            lo[d] = __double2float_rn(__dsub_rn(com, (double)hi[d]));
-            b_com[3 * (int64_t)b + d] = com;
-        }
-        const float lcf = wrec[b].c.x;
-        nb_wrec_put_lo(&wrec[b], make_float4(hi[0], hi[1], hi[2], __double2float_rn(M)),
-                       make_float4(lo[0], lo[1], lo[2], 0.0f));
-        nb_wrec_put_hi(&wrec[b], wb, lcf, __double2float_rn(__dsqrt_rn(d2)));
+        if (!QUAD && b >= 0) cell_com(b, wb, M, mx, b_com, wrec, com);
     }
 }
 
@@ -1025,20 +1073,28 @@ static void build_tail(nb_ctx *c, const double *pos, const float *mass, int64_t 
     k_bfs_records<<<nb_grid(c->max_nodes, 256, gcap), 256, 0, s>>>(
         c->bfs2pid, c->pid2bfs, c->node_c, c->n_first, c->n_nchild, c->n_parent, c->n_depth,
         c->keys, c->root, sys_sorted, c->p_hi, c->p_lo, c->p_x64, c->cnt, c->wrec, c->b_mass,
-        c->b_mx, c->b_com, c->b_up, c->lcount, c->cbkt, c->cbkt_cnt, n, c->key_order, c->err);
+        c->b_mx, c->b_com, c->b_up, c->lcount, c->cbkt, c->cbkt_cnt, n, c->key_order,
+        c->quad ? c->b_q : nullptr, c->err);
     nb_launched(c, "k_bfs_records");
     const int cl_blocks = (int)((c->max_nodes + CL_TILE - 1) / CL_TILE);
     k_cell_list<<<cl_blocks > 0 ? cl_blocks : 1, 256, 0, s>>>(c->cbkt, c->cbkt_cnt, c->cnt,
                                                                c->clist, c->clist_len, c->err);
     nb_launched(c, "k_cell_list");
-    static int mblocks = 0;
+    static int mblocks = 0, qblocks = 0;
     if (mblocks == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mblocks, k_moments, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mblocks, k_moments<false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qblocks, k_moments<true>, 256, 0);
         if (mblocks < 1) mblocks = 1;
+        if (qblocks < 1) qblocks = 1;
     }
-    k_moments<<<c->num_sms * mblocks, 256, 0, s>>>(c->clist, c->clist_len, c->wrec, c->b_up,
-                                                   c->lcount, c->b_mass, c->b_mx, c->b_com,
-                                                   c->arrive, c->cnt, c->err);
+    if (c->quad && c->b_q)
+        k_moments<true><<<c->num_sms * qblocks, 256, 0, s>>>(
+            c->clist, c->clist_len, c->wrec, c->b_up, c->lcount, c->b_mass, c->b_mx, c->b_com,
+            c->b_q, c->arrive, c->cnt, c->err);
+    else
+        k_moments<false><<<c->num_sms * mblocks, 256, 0, s>>>(
+            c->clist, c->clist_len, c->wrec, c->b_up, c->lcount, c->b_mass, c->b_mx, c->b_com,
+            nullptr, c->arrive, c->cnt, c->err);
     nb_launched(c, "k_moments");
 }
 
@@ -1224,3 +1280,4 @@ void nb_launch_keys_raw(const double *pos, int64_t n, double *part, int nblk, do
     k_root<<<1, 256, 0, s>>>(part, nblk, root);
     k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, root, nullptr, keys, idx, 0);
 }
+

@@ -36,12 +36,13 @@
 // the opening test of one chunk of 32 frontier nodes (one per lane): emit
 // particles and accepted cells to the list (ballot + popc), queue the
 // children of opened cells (warp prefix sum)
-template <bool PROBE>
+template <bool PROBE, bool QUAD>
 __device__ __forceinline__ void visit_node(
     const NodeRec r, int32_t gb, int32_t gpid, const float4 &blo, const float4 &bhi,
     const float4 &bc, float invth, int32_t total, long long *cnt, unsigned *err, int lane,
     unsigned lt, int64_t room, int64_t base, int32_t *__restrict__ list_id,
-    float4 *__restrict__ list_xm, int32_t *qout_s, int32_t *qout, int64_t wq_cap,
+    float4 *__restrict__ list_xm, const double *__restrict__ b_q, float4 *__restrict__ list_q,
+    int32_t *qout_s, int32_t *qout, int64_t wq_cap,
     int32_t &len, int32_t &ncell,
     int32_t &nb, float &dmin, float &dmax, float &dsum)
 {
@@ -74,12 +75,28 @@ __device__ __forceinline__ void visit_node(
         dmax = fmaxf(dmax, d);
         dsum += d;
     }
+    // in the quadrupole mode a chunk's accepted cells come before its
+    // particles, so that the force kernel's tiles hold runs of cells (which
+    // take the quadrupole term) and runs of particles (which do not)
+    const unsigned cm = QUAD ? __ballot_sync(FULL, cell_emit) : 0u;
     if (!PROBE && emit) {
-        const int32_t pos = len + __popc(em & lt);
+        const int32_t pos = !QUAD ? len + __popc(em & lt)
+                            : cell_emit ? len + __popc(cm & lt)
+                                        : len + __popc(cm) + __popc(em & ~cm & lt);
         if (pos < room) {
             list_id[base + pos] = r.wb.x;
             list_xm[base + pos] = make_float4(nb_rel(r.a.x, r.d.x, bc.x), nb_rel(r.a.y, r.d.y, bc.y),
                                               nb_rel(r.a.z, r.d.z, bc.z), r.a.w);
+            if constexpr (QUAD) {   // the cell's Q in FP32 (zero for a particle)
+                float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (cell_emit) {
+                    const double *qb = b_q + 6 * (int64_t)r.b;
+#pragma unroll
+                    for (int k = 0; k < 6; k++) q[k] = __double2float_rn(qb[k]);
+                }
+                list_q[2 * (base + pos)] = make_float4(q[0], q[1], q[2], q[3]);
+                list_q[2 * (base + pos) + 1] = make_float4(q[4], q[5], 0.0f, 0.0f);
+            }
         }
     }
     len += __popc(em);
@@ -107,13 +124,14 @@ __device__ __forceinline__ void visit_node(
     nb += __shfl_sync(FULL, incl, 31);
 }
 
-template <bool PROBE>
+template <bool PROBE, bool QUAD = false>
 __global__ void __launch_bounds__(WALK_T, 4)
 k_walk(const nb_wrec *__restrict__ wrec,
        const int32_t *__restrict__ pid2bfs, const int32_t *__restrict__ gnode,
        const int32_t *__restrict__ gcount, const float4 *__restrict__ gbox,
        long long *__restrict__ cnt, int32_t *__restrict__ glen, int32_t *__restrict__ gcells,
-       int32_t *__restrict__ list_id, float4 *__restrict__ list_xm, int64_t cap, int64_t alloc,
+       int32_t *__restrict__ list_id, float4 *__restrict__ list_xm,
+       const double *__restrict__ b_q, float4 *__restrict__ list_q, int64_t cap, int64_t alloc,
        int32_t *__restrict__ wq, int64_t wq_cap, unsigned *__restrict__ err,
        float *__restrict__ feat, const double *__restrict__ roots, const int8_t *__restrict__ n_depth,
        const int32_t *__restrict__ gfirst, const int32_t *__restrict__ sys_sorted,
@@ -163,9 +181,9 @@ k_walk(const nb_wrec *__restrict__ wrec,
             for (int32_t i0 = 0; i0 < na; i0 += NB_WARP) {
                 const NodeRec r = load_node<PROBE>(i0 + lane, na, qin_s, qin, wrec,
                                                    total, cnt, err);
-                visit_node<PROBE>(r, gb, gpid, blo, bhi, bc, invth, total, cnt, err, lane, lt, room,
-                                  base, list_id, list_xm, qout_s, qout, wq_cap, len, ncell, nb, dmin,
-                                  dmax, dsum);
+                visit_node<PROBE, QUAD>(r, gb, gpid, blo, bhi, bc, invth, total, cnt, err, lane, lt, room,
+                                  base, list_id, list_xm, b_q, list_q, qout_s, qout, wq_cap, len,
+                                  ncell, nb, dmin, dmax, dsum);
             }
             if (nb > qmax) qmax = nb;
             if (nb > wq_cap) { bad |= NB_EF_QUEUE; break; }
@@ -291,8 +309,12 @@ int nb_walk_warps(nb_ctx *c)
                          cudaSharedmemCarveoutMaxShared);
     cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_walk<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_walk<false>, WALK_T, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, k_walk<true>, WALK_T, 0);
+    if (bp < blocks) blocks = bp;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, k_walk<false, true>, WALK_T, 0);
     if (bp < blocks) blocks = bp;
     if (blocks < 1) blocks = 1;
     return c->num_sms * blocks * WALK_WARPS;
@@ -304,11 +326,18 @@ void nb_launch_walk(nb_ctx *c)
     static_assert(CNT_LIST_TOT + 4 == CNT_WALK_Q, "counter layout");
     cudaMemsetAsync(&c->cnt[CNT_QMAX], 0, sizeof(long long), c->stream);
     const int blocks = c->walk_warps / WALK_WARPS;
-    k_walk<false><<<blocks, WALK_T, 0, c->stream>>>(
-        c->wrec, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
-        c->glen, c->gcells, c->list_id, c->list_xm, c->list_cap, c->list_alloc, c->wq,
-        c->wq_cap, c->err, nullptr, c->root, c->n_depth, c->gfirst,
-        c->nsys > 1 ? c->sys_sorted : nullptr, c->nsys > 1 ? c->sys_root : nullptr);
+    if (c->quad && c->b_q && c->list_q)
+        k_walk<false, true><<<blocks, WALK_T, 0, c->stream>>>(
+            c->wrec, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt, c->glen, c->gcells,
+            c->list_id, c->list_xm, c->b_q, c->list_q, c->list_cap, c->list_alloc, c->wq,
+            c->wq_cap, c->err, nullptr, c->root, c->n_depth, c->gfirst,
+            c->nsys > 1 ? c->sys_sorted : nullptr, c->nsys > 1 ? c->sys_root : nullptr);
+    else
+        k_walk<false><<<blocks, WALK_T, 0, c->stream>>>(
+            c->wrec, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt, c->glen, c->gcells,
+            c->list_id, c->list_xm, nullptr, nullptr, c->list_cap, c->list_alloc, c->wq,
+            c->wq_cap, c->err, nullptr, c->root, c->n_depth, c->gfirst,
+            c->nsys > 1 ? c->sys_sorted : nullptr, c->nsys > 1 ? c->sys_root : nullptr);
     nb_launched(c, "k_walk");
 }
 
@@ -320,7 +349,8 @@ void nb_launch_probe(nb_ctx *c, float *feat)
     const int blocks = c->walk_warps / WALK_WARPS;
     k_walk<true><<<blocks, WALK_T, 0, c->stream>>>(
         c->wrec, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt,
-        c->glen, c->gcells, nullptr, nullptr, 0, 0, c->wq, c->wq_cap, c->err, feat, c->root,
+        c->glen, c->gcells, nullptr, nullptr, nullptr, nullptr, 0, 0, c->wq, c->wq_cap, c->err,
+        feat, c->root,
         c->n_depth, c->gfirst, c->nsys > 1 ? c->sys_sorted : nullptr,
         c->nsys > 1 ? c->sys_root : nullptr);
     nb_launched(c, "k_walk");
