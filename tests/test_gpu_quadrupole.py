@@ -81,7 +81,7 @@ def test_quadrupole_forces_and_lists(oracle_lib, name, precision, tol):
     assert np.all(np.abs(g["pot"] - p) <= tol * np.abs(p))
     # the quadrupole term is really there: the monopole sum differs by far more
     a0, _, _, _ = T.forces(n_crit, theta, eps, coords32=True)
-    assert np.median(np.linalg.norm(a0 - a, axis=1) / am) > 100 * tol
+    assert np.median(np.linalg.norm(a0 - a, axis=1) / am) > 10 * tol
 
 
 def test_quadrupole_closed_form_far_pair(oracle_lib):
