@@ -234,7 +234,7 @@ k_item_order(const int32_t *__restrict__ items, const int32_t *__restrict__ gcou
 // TILE: list records staged per tile (the j-tile depth); BT: threads per
 // block.  Both are chosen by the autotuner for the FP32 mode.
 template <int MODE, bool GUARD, int TILE, int BT, bool QUAD = false>
-__global__ void __launch_bounds__(BT, (QUAD ? 2 : MODE == MODE_F64 ? 5 : 4) * F_T / BT)
+__global__ void __launch_bounds__(BT, (MODE == MODE_F64 ? 5 : 4) * F_T / BT)
 k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
         const int32_t *__restrict__ gfirst,
         const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
@@ -270,12 +270,18 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
             if (lane == 0) nb_bad(cnt, err, SITE_FORCE, g);
             continue;
         }
-#define NB_FORCE_ITEM(R, S)                                                                   \
-    force_item<MODE, GUARD, R, S, TILE, QUAD>(g, i0, tiles[w], gfirst, gcount, glen, gbox, p_hi,  \
+#define NB_FORCE_ITEM_AT(R, S, I0)                                                            \
+    force_item<MODE, GUARD, R, S, TILE, QUAD>(g, I0, tiles[w], gfirst, gcount, glen, gbox, p_hi,  \
                                               p_lo, perm, list_xm, list_q, cap, alloc, n, eps2,   \
                                               acc, pot, cnt, err)
+#define NB_FORCE_ITEM(R, S) NB_FORCE_ITEM_AT(R, S, i0)
         if (word & ITEM_R2) {
-            NB_FORCE_ITEM(2, 1);
+            if constexpr (QUAD) {   // one target per lane: two passes over the list
+                NB_FORCE_ITEM_AT(1, 1, i0);
+                NB_FORCE_ITEM_AT(1, 1, i0 + NB_WARP);
+            } else {
+                NB_FORCE_ITEM(2, 1);
+            }
         } else {
             switch ((word >> ITEM_LS_SHIFT) & 7) {
             case 0: NB_FORCE_ITEM(1, 1); break;
@@ -287,6 +293,7 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
             }
         }
 #undef NB_FORCE_ITEM
+#undef NB_FORCE_ITEM_AT
     }
 }
 
