@@ -212,6 +212,22 @@ int nb_set_quadrupole(nb_ctx *ctx, int on);
  * for particles; synchronising debug export. */
 int nb_copy_quadrupoles(nb_ctx *ctx, double *q_host);
 
+/* Fixed-radius neighbour search by the general treewalk (Sec. "General
+ * Treewalk", Fig. "general_treewalk": the force walk's descent with another
+ * distance test, for short-range interactions).  On the current tree, groups
+ * of n_crit are walked once each; the neighbours of particle i are the j != i
+ * with |x_j - x_i|^2 <= h^2, the squared distance summed (x, y) then z in FP64
+ * from the FP64 positions, every operation rounded on its own.  off_dev: n + 1
+ * int64 (device) receives the CSR offsets in caller order; *total_host the
+ * number of pairs.  idx_dev (int32 caller indices, device, nullable): when it
+ * holds cap >= total entries it receives each particle's neighbours in
+ * ascending caller index, else only the offsets and total are produced (call
+ * again with room).  Synchronises cfg.stream; forms groups, leaves no lists
+ * (nb_forces returns STATE until the next walk).  Errors: STATE (no tree),
+ * INVALID_ARG, CAPACITY (total >= 2^31 pairs), WALK_LIMIT, CUDA, NOMEM. */
+int nb_neighbours(nb_ctx *ctx, double h, int n_crit, int64_t *off_dev, int32_t *idx_dev,
+                  int64_t cap, int64_t *total_host);
+
 /* One kick-drift-kick leapfrog step of size dt in FP64 ("integrate orbits
  * ... and repeat", Sec. Introduction): v += a dt/2; x += v dt; rebuild the
  * tree, walk and force with cfg.eps, cfg.theta, cfg.n_crit, cfg.precision;

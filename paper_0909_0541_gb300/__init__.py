@@ -42,7 +42,7 @@ EXPORTED = [
     "nb_direct_f32", "nb_direct_f32_workspace_size", "nb_set_key_order",
     "nb_theta_fit_workspace_size", "nb_theta_fit_curves", "nb_theta_allocate_workspace_size",
     "nb_theta_allocate", "nb_error_stats", "nb_column_stats", "nb_set_quadrupole",
-    "nb_copy_quadrupoles",
+    "nb_copy_quadrupoles", "nb_neighbours",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -92,6 +92,7 @@ def _load():
     L.nb_set_fused.argtypes = [vp, i32]
     L.nb_set_key_order.argtypes = [vp, i32]
     L.nb_set_quadrupole.argtypes = [vp, i32]
+    L.nb_neighbours.argtypes = [vp, C.c_double, i32, vp, vp, i64, vp]
     L.nb_copy_quadrupoles.argtypes = [vp, vp]
     L.nb_set_feature_mode.argtypes = [vp, i32]
     L.nb_leapfrog_step.argtypes = [vp, vp, vp, vp, i64, C.c_double]
@@ -330,6 +331,20 @@ class NBody:
         q = np.zeros((self.stats()["n_nodes"], 6))
         _check(_lib.nb_copy_quadrupoles(self._h, _hptr(q)), "nb_copy_quadrupoles")
         return q
+
+    def neighbours(self, h, n_crit=64):
+        """(offsets (n+1,) int64, caller indices int32) CUDA tensors of every
+        particle's neighbours within h, ascending (nb_neighbours)."""
+        import torch
+        n = self.n
+        off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        tot = C.c_int64(0)
+        _check(_lib.nb_neighbours(self._h, float(h), int(n_crit), off.data_ptr(), None, 0,
+                                  C.byref(tot)), "nb_neighbours")
+        idx = torch.empty(max(tot.value, 1), dtype=torch.int32, device="cuda")
+        _check(_lib.nb_neighbours(self._h, float(h), int(n_crit), off.data_ptr(), idx.data_ptr(),
+                                  int(idx.numel()), C.byref(tot)), "nb_neighbours")
+        return off, idx[:tot.value]
 
     def set_fused(self, on: bool):
         """Leapfrog force passes without interaction lists (nb_set_fused)."""

@@ -273,6 +273,35 @@ static int read_counters(nb_ctx *c)
     return NB_OK;
 }
 
+int nb_read_err(nb_ctx *c, unsigned *bits) { return sync_read_bits(c, bits); }
+int nb_err_code(unsigned bits) { return err_code(bits); }
+
+// double the walk queues past the widest frontier seen (synchronising)
+int nb_grow_queues(nb_ctx *c)
+{
+    int rc = read_counters(c);
+    if (rc) return rc;
+    const int64_t want = 2 * (c->cnt_host[CNT_QMAX] > c->wq_cap ? c->cnt_host[CNT_QMAX] : c->wq_cap);
+    CK(cudaStreamSynchronize(c->stream));
+    return alloc_queues(c, want) ? NB_OK : NB_ERR_NOMEM;
+}
+
+// the largest root-cube side over the current tree's systems (synchronising)
+double nb_root_side(nb_ctx *c)
+{
+    double L = 0.0;
+    for (int64_t sy = 0; sy < c->nsys; sy++) {
+        double v = 0.0;
+        if (cudaMemcpy(&v, c->root + 8 * sy + 3, sizeof(double), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0.0;
+        }
+        if (v > L) L = v;
+    }
+    return L;
+}
+
 static int finish(nb_ctx *c)
 {
     if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
@@ -765,6 +794,27 @@ int nb_copy_quadrupoles(nb_ctx *c, double *q_host)
     }
     free(qb);
     free(map);
+    return rc;
+}
+
+int nb_neighbours(nb_ctx *c, double h, int n_crit, int64_t *off_dev, int32_t *idx_dev,
+                  int64_t cap, int64_t *total_host)
+{
+    if (!c || !(h >= 0.0) || !isfinite(h) || n_crit < 1 || !off_dev || !total_host || cap < 0)
+        return NB_ERR_INVALID_ARG;
+    if (!c->has_tree) return NB_ERR_STATE;
+    c->has_lists = 0;   // the search forms its own groups and leaves no lists
+    c->has_groups = 0;
+    *total_host = 0;
+    if (c->n == 0) {
+        CK(cudaMemsetAsync(off_dev, 0, sizeof(int64_t), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return NB_OK;
+    }
+    int rc = sync_read(c);   // start from a clear error word
+    if (rc) return rc;
+    rc = nb_neigh_run(c, h, n_crit, off_dev, idx_dev, cap, total_host);
+    if (rc == NB_OK) c->has_groups = 1;
     return rc;
 }
 

@@ -294,6 +294,22 @@ int nb_launch_direct(const double *pos, const float *mass, int64_t n, double eps
                      const int64_t *targets, int64_t nt, double *acc, double *pot,
                      cudaStream_t s);
 
+// nb_neigh.cu
+int nb_neigh_run(nb_ctx *c, double h, int n_crit, int64_t *off, int32_t *idx, int64_t cap,
+                 int64_t *total);
+// nb_api.cu helpers for synchronising calls in other units
+int nb_read_err(nb_ctx *c, unsigned *bits);
+int nb_err_code(unsigned bits);
+int nb_grow_queues(nb_ctx *c);
+double nb_root_side(nb_ctx *c);
+#define CK_RET(call)                                                        \
+    do {                                                                    \
+        if ((call) != cudaSuccess) {                                        \
+            cudaGetLastError();                                             \
+            return NB_ERR_CUDA;                                             \
+        }                                                                   \
+    } while (0)
+
 // nb_step.cu
 void nb_launch_kick(nb_ctx *c, double *vel, const float *acc, int64_t n, double h);
 void nb_launch_wait_probe(nb_ctx *c, unsigned limit);
