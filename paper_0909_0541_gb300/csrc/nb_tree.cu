@@ -575,9 +575,13 @@ k_bfs_records(const int32_t *__restrict__ bfs2pid, const int32_t *__restrict__ p
             const int4 wb = make_int4(u, c.x, pid2bfs[u + 1], n_nchild[u]);
             const int depth = n_depth[u];
             if (!nb_in(depth >= 0 && depth <= NB_LEVELS, cnt, err, SITE_RECORDS, u)) continue;
-            if (!nb_in(wb.w >= 1 && wb.w <= 8, cnt, err, SITE_RECORDS, u)) continue;
+            // a cell has 1..8 children, except a level-21 cell of coincident
+            // particles, which keeps all of them
+            if (!nb_in(wb.w >= 1 && (wb.w <= 8 || depth == NB_LEVELS), cnt, err, SITE_RECORDS, u))
+                continue;
             // moments bucket: deepest level first, then by number of children
-            const int k = (NB_DEPTHS - 1 - depth) * 8 + wb.w - 1;
+            // (more than 8 share the bucket of 8)
+            const int k = (NB_DEPTHS - 1 - depth) * 8 + (wb.w < 8 ? wb.w : 8) - 1;
             cbkt[b] = (int16_t)k;
             atomicAdd(&hb[k], 1);
             const double *root = roots + (sys ? 8 * (int64_t)sys[slot] : 0);
@@ -826,7 +830,7 @@ k_moments(const int32_t *__restrict__ clist, int64_t clist_len, nb_wrec *__restr
         if (b >= 0) {
             if (nb_in(b < total, cnt, err, SITE_MOMENTS, b)) {
                 wb = wrec[b].b;
-                if (nb_in(wb.z > b && wb.w >= 1 && wb.w <= 8 && (int64_t)wb.z + wb.w <= total, cnt,
+                if (nb_in(wb.z > b && wb.w >= 1 && (int64_t)wb.z + wb.w <= total, cnt,
                           err, SITE_MOMENTS, b))
                     need = wb.w - lcount[b];   // cell children still to arrive
                 else

@@ -109,9 +109,9 @@ __device__ __forceinline__ void visit_node(
     }
     const int32_t start = nb + incl - nch;
     if (open) {
-        if (start + nch <= WQ_SMEM) {   // the common case: all in shared memory
+        if (nch <= 8 && start + nch <= WQ_SMEM) {   // the common case: all in shared memory
 #pragma unroll
-            for (int k = 0; k < 8; k++)   // a cell has at most 8 children
+            for (int k = 0; k < 8; k++)   // a cell below level 21 has at most 8 children
                 if (k < nch) qout_s[start + k] = fc + k;
         } else {
             for (int32_t k = 0; k < nch; k++) {

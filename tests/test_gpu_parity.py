@@ -170,6 +170,29 @@ def test_coincident_particles_and_zero_softening(oracle_lib):
         assert np.all(np.abs(g["pot"] - p) <= 1e-5 * np.abs(p))
 
 
+@pytest.mark.parametrize("order", ["morton", "hilbert"])
+def test_level21_bucket_of_more_than_eight_coincident_particles(oracle_lib, order):
+    """A level-21 cell keeps all its coincident particles as children (here
+    40 at one point and 9 at another): topology, moments, lists and forces
+    against the oracle, with the bucket as a group (n_crit 64) and split into
+    one-particle groups (n_crit 16)."""
+    ps = nbsynth.uniform_cube(5000, 23)
+    pos = ps.pos.copy()
+    pos[1000:1040] = pos[3]
+    pos[2000:2009] = pos[4000]
+    for n_crit in (16, 64):
+        for eps in (0.0, 1e-3):
+            g = gpu_run(pos, ps.mass, theta=0.6, n_crit=n_crit, eps=eps, key_order=order)
+            T = oracle_lib.Tree(pos, ps.mass, order=order)
+            assert_tree_equal(g, T)
+            assert_lists_equal(g, T, 0.6, n_crit)
+            assert int(g["tree"]["nchild"].max()) == 41
+            a, p, _, _, am = T.forces(n_crit, 0.6, eps, with_amag=True, coords32=True)
+            d = np.linalg.norm(g["acc"].astype(np.float64) - a, axis=1)
+            assert np.all(np.isfinite(g["acc"])) and np.all(d <= 1e-5 * am)
+            g["ctx"].close()
+
+
 def test_theta_zero_is_direct_sum(oracle_lib):
     ps = nbsynth.plummer(3000, 4)
     eps = 1 / 64
