@@ -132,9 +132,7 @@ __device__ __forceinline__ void force_item(
     for (int r = 0; r < R; r++) pair_fold<MODE>(A[r], P[r]);
     if constexpr (S > 1) {
 #pragma unroll
-        for (int r = 0; r < R; r++)
-#pragma unroll
-            for (int o = W; o < NB_WARP; o <<= 1) stream_sum<MODE>(A[r], o);
+        for (int o = W; o < NB_WARP; o <<= 1) stream_sum<MODE>(A[0], o);
         if (stream != 0) return;
     }
 #pragma unroll
@@ -167,7 +165,7 @@ __device__ __forceinline__ int item_bucket(const int32_t *__restrict__ items,
     const int32_t g = items[2 * (int64_t)it], word = items[2 * (int64_t)it + 1];
     if (g < 0 || g >= ngroups) return NB_IBKT - 1;   // k_force reports the bad item
     const uint32_t len = (uint32_t)max(glen[g], 0) + (uint32_t)max(gcount[g], 0);
-    const int ls = min((word >> ITEM_LS_SHIFT) & 7, 5);
+    const int ls = (word & ITEM_R2) ? 0 : min((word >> ITEM_LS_SHIFT) & 7, 5);
     uint32_t w = ((word & ITEM_R2) ? 2u * len : len) >> ls;
     if (w < 1) w = 1;
     const int e = 31 - __clz(w);
@@ -278,24 +276,11 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
                                               acc, pot, cnt, err)
 #define NB_FORCE_ITEM(R, S) NB_FORCE_ITEM_AT(R, S, i0)
         if (word & ITEM_R2) {
-            if constexpr (QUAD) {   // one target per lane: two passes over the W rows
-                switch ((word >> ITEM_LS_SHIFT) & 7) {
-                case 0: NB_FORCE_ITEM_AT(1, 1, i0); NB_FORCE_ITEM_AT(1, 1, i0 + 32); break;
-                case 1: NB_FORCE_ITEM_AT(1, 2, i0); NB_FORCE_ITEM_AT(1, 2, i0 + 16); break;
-                case 2: NB_FORCE_ITEM_AT(1, 4, i0); NB_FORCE_ITEM_AT(1, 4, i0 + 8); break;
-                case 3: NB_FORCE_ITEM_AT(1, 8, i0); NB_FORCE_ITEM_AT(1, 8, i0 + 4); break;
-                case 4: NB_FORCE_ITEM_AT(1, 16, i0); NB_FORCE_ITEM_AT(1, 16, i0 + 2); break;
-                default: NB_FORCE_ITEM_AT(1, 32, i0); NB_FORCE_ITEM_AT(1, 32, i0 + 1); break;
-                }
+            if constexpr (QUAD) {   // one target per lane: two passes over the list
+                NB_FORCE_ITEM_AT(1, 1, i0);
+                NB_FORCE_ITEM_AT(1, 1, i0 + NB_WARP);
             } else {
-                switch ((word >> ITEM_LS_SHIFT) & 7) {
-                case 0: NB_FORCE_ITEM(2, 1); break;
-                case 1: NB_FORCE_ITEM(2, 2); break;
-                case 2: NB_FORCE_ITEM(2, 4); break;
-                case 3: NB_FORCE_ITEM(2, 8); break;
-                case 4: NB_FORCE_ITEM(2, 16); break;
-                default: NB_FORCE_ITEM(2, 32); break;
-                }
+                NB_FORCE_ITEM(2, 1);
             }
         } else {
             switch ((word >> ITEM_LS_SHIFT) & 7) {

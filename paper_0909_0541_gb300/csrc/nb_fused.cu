@@ -186,9 +186,7 @@ __device__ __forceinline__ void fused_item(
     }
     if constexpr (S > 1) {
 #pragma unroll
-        for (int r = 0; r < R; r++)
-#pragma unroll
-            for (int o = W; o < NB_WARP; o <<= 1) stream_sum<MODE>(A[r], o);
+        for (int o = W; o < NB_WARP; o <<= 1) stream_sum<MODE>(A[0], o);
         if (stream != 0) return;
     }
 #pragma unroll
@@ -255,14 +253,7 @@ k_walk_force(const int32_t *__restrict__ items, const nb_wrec *__restrict__ wrec
                                   pid2bfs, gnode, gfirst, gcount, gbox, p_hi, p_lo, perm, total,  \
                                   n, eps2, sys_sorted, sys_root, acc, pot, cnt, err, bad, fc)
         if (word & ITEM_R2) {
-            switch ((word >> ITEM_LS_SHIFT) & 7) {
-            case 0: NB_FUSED_ITEM(2, 1); break;
-            case 1: NB_FUSED_ITEM(2, 2); break;
-            case 2: NB_FUSED_ITEM(2, 4); break;
-            case 3: NB_FUSED_ITEM(2, 8); break;
-            case 4: NB_FUSED_ITEM(2, 16); break;
-            default: NB_FUSED_ITEM(2, 32); break;
-            }
+            NB_FUSED_ITEM(2, 1);
         } else {
             switch ((word >> ITEM_LS_SHIFT) & 7) {
             case 0: NB_FUSED_ITEM(1, 1); break;

@@ -1138,12 +1138,9 @@ k_group_scatter(const int32_t *__restrict__ gid, const int32_t *__restrict__ n_f
 
 // Force work items of a group of m members (iblock = 64: two targets per
 // lane, or 32): full items of iblock, then (iblock 64) one 32-target item
-// if more than 32 remain, then a tail of <= 32 targets rounded up to a power
-// of two m'.  With iblock 64 every item but a one-target tail holds two
-// targets per lane (the 32-target item as 16 rows x 2 streams, a tail as m'/2
-// rows x 64/m' streams); with iblock 32 one per lane (a tail as m' rows x
-// 32/m' streams).  Word: first member | log2(streams) << 27 | (1 << 30 for
-// two targets per lane).
+// if more than 32 remain, then a tail of <= 32 targets, run as 32/m' source
+// streams with m' the tail rounded up to a power of two.  Word: first member
+// | log2(streams) << 27 | (1 << 30 for a 64-target item).
 __device__ __forceinline__ int32_t item_count(int32_t m, int iblock)
 {
     int32_t c = m / iblock, rem = m - c * iblock;
@@ -1221,22 +1218,17 @@ k_items(const int32_t *__restrict__ item_off, const int32_t *__restrict__ gcount
             items[2 * (int64_t)(o + k) + 1] = i0 | (iblock == 64 ? (1 << 30) : 0);
         }
         int32_t rem = m - i0;
-        // with 64-target items every smaller item also holds two targets per
-        // lane: W = m'/2 rows and 64/m' source streams (a lone target: one per
-        // lane, 32 streams)
-        const int32_t r2 = iblock == 64 ? (1 << 30) : 0;
         if (iblock == 64 && rem > 32) {
             items[2 * (int64_t)(o + k)] = g;
-            items[2 * (int64_t)(o + k) + 1] = i0 | r2 | (1 << 27);
+            items[2 * (int64_t)(o + k) + 1] = i0;
             i0 += 32;
             rem -= 32;
             k++;
         }
         if (rem > 0) {
             const int lg = rem > 1 ? 32 - __clz(rem - 1) : 0;   // log2 of rem rounded up
-            const bool two = r2 && lg >= 1;
             items[2 * (int64_t)(o + k)] = g;
-            items[2 * (int64_t)(o + k) + 1] = i0 | (two ? r2 | ((6 - lg) << 27) : (5 - lg) << 27);
+            items[2 * (int64_t)(o + k) + 1] = i0 | ((5 - lg) << 27);
         }
     }
 }
