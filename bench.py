@@ -74,6 +74,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sizes", default="",
+                    help="crossover: comma-separated particle counts (default: 1000 ... 256000)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch512: fixed shape (n_crit 256, 64-target items, 32-record tiles, "
+                         "256-thread blocks) instead of the autotuner")
     ap.add_argument("--graph-steps", type=int, default=100,
                     help="KDK steps per captured graph (batch512 workload)")
     return ap.parse_args()
@@ -811,7 +816,8 @@ def run_crossover(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     theta, eps, reps = 0.6, 1.0 / 64, 7
-    sizes = [1000, 2000, 4000, 8000, 16000, 32000, 64000, 128000, 256000]
+    sizes = ([int(x) for x in args.sizes.split(",")] if args.sizes else
+             [1000, 2000, 4000, 8000, 16000, 32000, 64000, 128000, 256000])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     rows = []
@@ -939,8 +945,15 @@ def run_batch(args, ws, rank, local):
     ctx = nb.NBody(n, eps=eps, theta=theta, n_crit=64, max_systems=len(systems),
                    sync_checks=True, stream=stream)
     with torch.cuda.stream(stream):
-        pick, table = ctx.autotune(P, M, eps, theta, n_crits=(32, 64, 128, 256, 512),
-                                   reps=2, offsets=O)
+        if args.no_autotune:
+            pick, table = {"n_crit": 256, "rows": 2, "tile": 32, "block": 256}, {}
+            ctx.cfg.n_crit = 256
+            ctx.close()
+            ctx = nb.NBody(n, eps=eps, theta=theta, n_crit=256, max_systems=len(systems),
+                           sync_checks=True, stream=stream)
+        else:
+            pick, table = ctx.autotune(P, M, eps, theta, n_crits=(32, 64, 128, 256, 512),
+                                       reps=2, offsets=O)
         ctx.leapfrog_step_batched(P, V, M, O, dt)      # sizes the lists, caches a(x)
         ctx.set_sync_checks(False)
         ctx.graph_capture_leapfrog(P, V, M, dt, nsteps, offsets=O)
