@@ -127,17 +127,29 @@ k_direct32_reduce(const float4 *__restrict__ partial, int64_t n, int parts,
     if (pot) pot[i] = s[3];
 }
 
-// parts of the source range for n particles on a device with `sms` SMs:
-// enough blocks for four per SM, each part at least D_MIN_PART_TILES tiles
+// parts of the source range for n particles on a device with `sms` SMs: of
+// the part counts that keep every part at least D_MIN_PART_TILES tiles long,
+// the one whose blocks fill the 4 x sms resident slots best (the last wave as
+// full as possible), the smallest on a tie
 static int direct_parts(int64_t n, int sms)
 {
     const int64_t tb = (n + D_TGT - 1) / D_TGT;
-    int64_t parts = ((int64_t)sms * 4 + tb - 1) / (tb > 0 ? tb : 1);
-    const int64_t by_len = n / ((int64_t)D_TJ * D_MIN_PART_TILES);
-    if (parts > by_len) parts = by_len;
-    if (parts > D_MAX_PARTS) parts = D_MAX_PARTS;
-    if (parts < 1) parts = 1;
-    return (int)parts;
+    const int64_t tiles = (n + D_TJ - 1) / D_TJ;
+    const double slots = 4.0 * (sms > 0 ? sms : 1);
+    int best = 1;
+    double best_eff = -1.0;
+    for (int P = 1; P <= D_MAX_PARTS; P++) {
+        const int64_t part_len = (tiles + P - 1) / P * D_TJ;
+        if (P > 1 && part_len < (int64_t)D_TJ * D_MIN_PART_TILES) break;
+        const int64_t rp = (n + part_len - 1) / part_len;
+        const double waves = (double)(tb * rp) / slots;
+        const double eff = waves / __builtin_ceil(waves);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = P;
+        }
+    }
+    return best;
 }
 
 static int current_sms(int *sms)
@@ -155,11 +167,9 @@ extern "C" size_t nb_direct_f32_workspace_size(int64_t n)
 {
     if (n <= 0) return 0;
     int sms = 0;
-    if (current_sms(&sms)) {
-        cudaGetLastError();
-        sms = 256;   // no device: the size for the largest SM count
-    }
-    const int parts = direct_parts(n, sms);
+    int parts = D_MAX_PARTS;   // no device: room for the largest part count
+    if (current_sms(&sms)) cudaGetLastError();
+    else parts = direct_parts(n, sms);
     return align256(sizeof(float4) * (size_t)n) +
            (parts > 1 ? sizeof(float4) * (size_t)n * (size_t)parts : 0);
 }
