@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel of the timed steps from the host instead of "
                          "replaying them from one CUDA graph")
+    ap.add_argument("--overlap", action="store_true",
+                    help="force passes overlap the walk with the force sum in one launch")
     ap.add_argument("--fused", action="store_true",
                     help="force passes walk and sum in one kernel, no interaction lists")
     ap.add_argument("--judge-targets", type=int, default=8192)
@@ -379,6 +381,8 @@ def run_ours(args, ws, rank, local):
     stream.wait_stream(torch.cuda.current_stream(dev))
     if args.fused:
         ctx.set_fused(True)
+    if args.overlap:
+        ctx.set_overlap(True)
     ctx.set_key_order(args.order)
     if args.quadrupole:
         ctx.set_quadrupole(True)
@@ -543,7 +547,9 @@ def run_ours(args, ws, rank, local):
             "config": workload_config(args.workload, n, w, ws),
             "run": {"precision": args.precision, "key_order": args.order,
                     "cells": "quadrupole" if args.quadrupole else "monopole",
-                    "force_path": "fused walk+force" if args.fused else "lists",
+                    "force_path": ("fused walk+force" if args.fused else
+                                   "lists, walk overlapped with the force sum" if args.overlap
+                                   else "lists"),
                     "launch": ((f"eager (graph capture failed: {graph_failed})"
                                 if graph_failed else
                                 "eager: every kernel launched from the host") if args.eager

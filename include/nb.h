@@ -228,6 +228,26 @@ int nb_copy_quadrupoles(nb_ctx *ctx, double *q_host);
 int nb_neighbours(nb_ctx *ctx, double h, int n_crit, int64_t *off_dev, int32_t *idx_dev,
                   int64_t cap, int64_t *total_host);
 
+/* nb_walk_groups + nb_forces in one persistent launch that overlaps them:
+ * every warp takes a force work item whose group's walk has finished, else
+ * the next group to walk, so the walk (bound by the latency of its record
+ * fetches) and the force sum (bound by the FMA pipe) share the SMs.  The lists
+ * and every item's sums are computed exactly as by the two calls, so the
+ * results are the same bits.  precision: NB_FP32 or NB_FP32_COMP (others
+ * INVALID_ARG); not in the quadrupole mode (INVALID_ARG).  It needs list
+ * storage sized by an earlier synchronising walk: without it, the call runs
+ * nb_walk_groups + nb_forces when sync_checks is on and returns CAPACITY
+ * when it is off.  With sync_checks on, a list that outgrows its slot makes
+ * the call redo the walk and the force sum separately (growing the storage).
+ * Timing: the group formation counts as NB_PHASE_WALK, the overlapped launch
+ * as NB_PHASE_FORCE.  Errors: as nb_walk_groups and nb_forces. */
+int nb_walk_forces(nb_ctx *ctx, float theta, int n_crit, float eps, float *acc_dev,
+                   float *pot_dev, int precision);
+/* on != 0: the force passes of nb_leapfrog_step (and its batched, host and
+ * graph forms) use nb_walk_forces (FP32 and compensated modes, monopole
+ * cells; otherwise the separate calls). */
+int nb_set_overlap(nb_ctx *ctx, int on);
+
 /* One kick-drift-kick leapfrog step of size dt in FP64 ("integrate orbits
  * ... and repeat", Sec. Introduction): v += a dt/2; x += v dt; rebuild the
  * tree, walk and force with cfg.eps, cfg.theta, cfg.n_crit, cfg.precision;

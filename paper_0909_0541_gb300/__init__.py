@@ -42,7 +42,7 @@ EXPORTED = [
     "nb_direct_f32", "nb_direct_f32_workspace_size", "nb_set_key_order",
     "nb_theta_fit_workspace_size", "nb_theta_fit_curves", "nb_theta_allocate_workspace_size",
     "nb_theta_allocate", "nb_error_stats", "nb_column_stats", "nb_set_quadrupole",
-    "nb_copy_quadrupoles", "nb_neighbours",
+    "nb_copy_quadrupoles", "nb_neighbours", "nb_walk_forces", "nb_set_overlap",
 ]
 MLP_NPARAM = 9960
 NFEAT_STRIDE = 16
@@ -92,6 +92,8 @@ def _load():
     L.nb_set_fused.argtypes = [vp, i32]
     L.nb_set_key_order.argtypes = [vp, i32]
     L.nb_set_quadrupole.argtypes = [vp, i32]
+    L.nb_walk_forces.argtypes = [vp, C.c_float, i32, C.c_float, vp, vp, i32]
+    L.nb_set_overlap.argtypes = [vp, i32]
     L.nb_neighbours.argtypes = [vp, C.c_double, i32, vp, vp, i64, vp]
     L.nb_copy_quadrupoles.argtypes = [vp, vp]
     L.nb_set_feature_mode.argtypes = [vp, i32]
@@ -345,6 +347,20 @@ class NBody:
         _check(_lib.nb_neighbours(self._h, float(h), int(n_crit), off.data_ptr(), idx.data_ptr(),
                                   int(idx.numel()), C.byref(tot)), "nb_neighbours")
         return off, idx[:tot.value]
+
+    def walk_forces(self, theta, n_crit, eps, acc, pot=None, precision="fp32"):
+        """Groups, walk and force sum with the walk overlapping the force sum
+        in one launch (nb_walk_forces): the same results as walk_groups +
+        forces."""
+        import torch
+        _check(_lib.nb_walk_forces(self._h, float(theta), int(n_crit), float(eps),
+                                   _dptr(acc, torch.float32, 3, "acc"),
+                                   _dptr(pot, torch.float32, None, "pot"),
+                                   PRECISION.get(precision, precision)), "nb_walk_forces")
+
+    def set_overlap(self, on: bool):
+        """Leapfrog force passes through walk_forces (nb_set_overlap)."""
+        _check(_lib.nb_set_overlap(self._h, 1 if on else 0), "nb_set_overlap")
 
     def set_fused(self, on: bool):
         """Leapfrog force passes without interaction lists (nb_set_fused)."""

@@ -157,6 +157,7 @@ static void carve_context(nb_ctx *c, Arena &a)
     a.carve(&c->gbox, 3 * N);
     a.carve(&c->gfeat, 16 * N);
     a.carve(&c->gtheta, N);
+    a.carve(&c->gready, N);
     a.carve(&c->items, 2 * c->max_items);
     a.carve(&c->item_cnt, N + 1);
     a.carve(&c->item_order, c->max_items);
@@ -194,7 +195,7 @@ static const char *const SITE_NAME[SITE_N_] = {
     "k_moments: cell, parent or child run", "groups: group or member range",
     "k_items: item index", "k_walk: queued node", "k_walk: child run", "k_force: item",
     "k_rs_scatter: destination", "k_moments: wait for children ran out",
-    "k_rs_scatter: look-back wait ran out"};
+    "k_rs_scatter: look-back wait ran out", "k_walk_force: wait for a group's walk ran out"};
 
 static int err_code(unsigned bits)
 {
@@ -735,6 +736,9 @@ static int force_pass(nb_ctx *c, const double *pos, const float *mass, int64_t n
     if (c->fused)
         return nb_forces_fused(c, c->cfg.theta, c->cfg.n_crit, c->cfg.eps, c->acc_cache,
                                c->pot_cache, c->cfg.precision);
+    if (c->overlap && !c->quad && c->cfg.precision != NB_FP64ACC)
+        return nb_walk_forces(c, c->cfg.theta, c->cfg.n_crit, c->cfg.eps, c->acc_cache,
+                              c->pot_cache, c->cfg.precision);
     rc = nb_walk_groups(c, c->cfg.theta, c->cfg.n_crit, nullptr);
     if (rc) return rc;
     return nb_forces(c, c->cfg.eps, c->acc_cache, c->pot_cache, c->cfg.precision);
@@ -816,6 +820,61 @@ int nb_neighbours(nb_ctx *c, double h, int n_crit, int64_t *off_dev, int32_t *id
     rc = nb_neigh_run(c, h, n_crit, off_dev, idx_dev, cap, total_host);
     if (rc == NB_OK) c->has_groups = 1;
     return rc;
+}
+
+int nb_walk_forces(nb_ctx *c, float theta, int n_crit, float eps, float *acc, float *pot,
+                   int precision)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    if (!(theta >= 0.f) || n_crit < 1 || !(eps >= 0.f) ||
+        (precision != NB_FP32 && precision != NB_FP32_COMP) || (c->n > 0 && !acc) || c->quad)
+        return NB_ERR_INVALID_ARG;
+    if (!c->has_tree) return NB_ERR_STATE;
+    // no list storage yet (or it is too small, found by a synchronising
+    // call): the separate walk sizes it, then the separate force sum
+    if (c->list_cap < 1 || !c->list_id || !c->wq) {
+        if (!c->sync_checks) return NB_ERR_CAPACITY;
+        int rc = nb_walk_groups(c, theta, n_crit, nullptr);
+        if (rc) return rc;
+        return nb_forces(c, eps, acc, pot, precision);
+    }
+    c->has_lists = 0;
+    c->n_crit_cur = n_crit;
+    if (c->n == 0) {
+        c->groups_host = 0;
+        c->has_lists = 1;
+        c->lists_quad = 0;
+        return NB_OK;
+    }
+    int tk = phase_begin(c);
+    nb_launch_groups(c, theta, n_crit, nullptr);
+    phase_end(c, tk, NB_PHASE_WALK);
+    c->has_groups = 1;
+    tk = phase_begin(c);
+    nb_launch_walk_force(c, eps, acc, pot, precision);
+    phase_end(c, tk, NB_PHASE_FORCE);
+    if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
+    c->has_lists = 1;
+    c->lists_quad = 0;
+    if (!c->sync_checks) return NB_OK;
+    unsigned bits = 0;
+    int rc = sync_read_bits(c, &bits);
+    if (rc) return rc;
+    if (bits & (NB_EF_CAPACITY | NB_EF_QUEUE)) {
+        // a list outgrew its slot or a frontier the queues: the separate,
+        // synchronising walk grows the storage, then the force sum again
+        rc = nb_walk_groups(c, theta, n_crit, nullptr);
+        if (rc) return rc;
+        return nb_forces(c, eps, acc, pot, precision);
+    }
+    return err_code(bits);
+}
+
+int nb_set_overlap(nb_ctx *c, int on)
+{
+    if (!c) return NB_ERR_INVALID_ARG;
+    c->overlap = on ? 1 : 0;
+    return NB_OK;
 }
 
 int nb_set_fused(nb_ctx *c, int on)

@@ -32,6 +32,7 @@
 // item's result does not depend on when it runs, so the order changes
 // timing only.
 #include "nb_force.cuh"
+#include "nb_walk.cuh"
 
 #define F_T 256
 
@@ -39,7 +40,9 @@
 // target row l % W of stream l / W, W = 32 / S
 // QUAD: list records carry the cells' quadrupoles (list_q) and the list
 // phase adds the quadrupole term (TILE = 32, FP32 modes)
-template <int MODE, bool GUARD, int R, int S, int TILE, bool QUAD>
+// CG: the list and its length are read through L2 only (the overlapped
+// kernel reads lists that other warps of the same launch wrote)
+template <int MODE, bool GUARD, int R, int S, int TILE, bool QUAD, bool CG = false>
 __device__ __forceinline__ void force_item(
     int32_t g, int32_t i0, float4 *tile, const int32_t *__restrict__ gfirst,
     const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
@@ -62,7 +65,8 @@ __device__ __forceinline__ void force_item(
     const int64_t room = alloc - (int64_t)g * cap;
     int64_t lim = cap < room ? cap : room;
     if (lim < 0) lim = 0;
-    const int32_t len = glen[g] < lim ? glen[g] : (int32_t)lim;
+    const int32_t gl = CG ? __ldcg(&glen[g]) : glen[g];
+    const int32_t len = gl < lim ? gl : (int32_t)lim;
     const float4 bc = gbox[3 * (int64_t)g + 2];
     const float4 pad = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
     Tgt t[R];
@@ -106,7 +110,8 @@ __device__ __forceinline__ void force_item(
 #pragma unroll
             for (int k = 0; k < TK; k++) {
                 const int32_t jj = j0 + k * NB_WARP + lane;
-                put_rec(tile, k * NB_WARP + lane, jj < len ? src[jj] : pad);
+                put_rec(tile, k * NB_WARP + lane,
+                        jj < len ? (CG ? __ldcg(&src[jj]) : src[jj]) : pad);
             }
             __syncwarp();
             tile_pass<MODE, GUARD, false, R, W * TK>(tile, stream * W * TK, j0 + stream * W * TK,
@@ -359,6 +364,202 @@ void nb_launch_forces(nb_ctx *c, float eps, float *acc, float *pot, int precisio
     case 3: launch_force<MODE_COMP, true>(c, eps2, acc, pot); break;
     case 4: launch_force<MODE_F64, false>(c, eps2, acc, pot); break;
     default: launch_force<MODE_F64, true>(c, eps2, acc, pot); break;
+    }
+}
+
+// ---------------------------------------------------------------- overlap
+// The walk and the force sum in one persistent launch.  The walk is bound by
+// the latency of its record fetches and the force sum by the FMA pipe; run as
+// two launches, each leaves the other's unit idle.  Here every warp takes,
+// in turn, whatever is ready: a force item whose group's walk has finished,
+// else the next group to walk, else it waits (bounded) for the group of the
+// next force item.  Walks are taken in group order and force items in item
+// order (a group's items are contiguous), so a warp that waits waits for a
+// walk that a running warp has already claimed.  A finished walk publishes
+// its list with a release store to the group's flag; a force warp acquires
+// the flag and reads the list through L2.  Every item and every list is
+// computed as in the two separate launches, so the results are the same bits.
+__device__ __forceinline__ int32_t ov_ld_acquire(const int32_t *p)
+{
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void ov_st_release(int32_t *p, int32_t v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+#define OV_T 256
+#define OV_WARPS (OV_T / NB_WARP)
+#define OV_SPIN_LIMIT (1u << 22)
+
+template <int MODE, bool GUARD>
+__global__ void __launch_bounds__(OV_T, 4)
+k_walk_force(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ pid2bfs,
+             const int32_t *__restrict__ gnode, const int32_t *__restrict__ gcount,
+             const float4 *__restrict__ gbox, long long *__restrict__ cnt,
+             int32_t *__restrict__ glen, int32_t *__restrict__ gcells,
+             int32_t *__restrict__ list_id, float4 *__restrict__ list_xm, int64_t cap,
+             int64_t alloc, int32_t *__restrict__ wq, int64_t wq_cap, unsigned *__restrict__ err,
+             const double *__restrict__ roots, const int8_t *__restrict__ n_depth,
+             const int32_t *__restrict__ gfirst, const int32_t *__restrict__ sys_sorted,
+             const int32_t *__restrict__ sys_root, const int32_t *__restrict__ items,
+             const float4 *__restrict__ p_hi, const float4 *__restrict__ p_lo,
+             const int32_t *__restrict__ perm, int64_t n, float eps2, float *__restrict__ acc,
+             float *__restrict__ pot, int64_t max_items, int32_t *__restrict__ gready)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t gw = (int64_t)blockIdx.x * OV_WARPS + w;
+    int32_t *const qa = wq + gw * 2 * wq_cap;
+    int32_t *const qb = qa + wq_cap;
+    // per warp: the walk's frontier queues, or (while it sums) the force tile
+    __shared__ __align__(16) int32_t sq[OV_WARPS][2 * WQ_SMEM];
+    int32_t *const qa_s = sq[w];
+    int32_t *const qb_s = qa_s + WQ_SMEM;
+    float4 *const tile = reinterpret_cast<float4 *>(sq[w]);
+    const int32_t G = (int32_t)cnt[CNT_GROUPS];
+    const int32_t total = (int32_t)cnt[CNT_NODES];
+    int32_t nitems = (int32_t)cnt[CNT_ITEMS];
+    if (nitems > max_items) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) nb_bad(cnt, err, SITE_FORCE, nitems);
+        nitems = (int32_t)max_items;
+    }
+    long long pp = 0, pc = 0, tot = 0;
+    int32_t mx = 0, qmax = 0;
+    unsigned bad = 0;
+    bool walks_left = true;
+    for (;;) {
+        // lane 0 picks the next task: 1 a ready force item, 2 a walk, 3 skip a
+        // bad item, 0 done
+        int act = 0;
+        long long task = 0;
+        if (lane == 0) {
+            for (unsigned spins = 0;;) {
+                const long long it = *(volatile long long *)&cnt[CNT_FORCE_Q];
+                if (it < nitems) {
+                    const int32_t g = items[2 * it];
+                    const bool okg = g >= 0 && g < G;
+                    if (!okg || ov_ld_acquire(&gready[g]) != 0) {
+                        if ((long long)atomicCAS((unsigned long long *)&cnt[CNT_FORCE_Q],
+                                                 (unsigned long long)it,
+                                                 (unsigned long long)(it + 1)) == it) {
+                            act = okg ? 1 : 3;
+                            task = it;
+                            break;
+                        }
+                        continue;   // another warp took it: look again
+                    }
+                }
+                if (walks_left) {
+                    const long long gnext = nb_atomic_add(&cnt[CNT_WALK_Q], 1LL);
+                    if (gnext < G) {
+                        act = 2;
+                        task = gnext;
+                        break;
+                    }
+                    walks_left = false;
+                }
+                if (it >= nitems) break;
+                if (++spins > OV_SPIN_LIMIT) {
+                    nb_bad(cnt, err, SITE_OVERLAP_WAIT, it);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        act = __shfl_sync(FULL, act, 0);
+        task = __shfl_sync(FULL, task, 0);
+        if (act == 0) break;
+        if (act == 3) {
+            if (lane == 0) nb_bad(cnt, err, SITE_FORCE, task);
+            continue;
+        }
+        if (act == 2) {
+            const int g = (int)task;
+            walk_one<false, false>(g, wrec, pid2bfs, gnode, gcount, gbox, cnt, glen, gcells,
+                                   list_id, list_xm, nullptr, nullptr, cap, alloc, qa, qb, qa_s,
+                                   qb_s, wq_cap, err, nullptr, roots, n_depth, gfirst,
+                                   sys_sorted, sys_root, total, lane, lt, pp, pc, tot, mx, qmax,
+                                   bad);
+            __threadfence();   // every lane's list writes before the flag
+            __syncwarp();
+            if (lane == 0) ov_st_release(&gready[g], 1);
+            continue;
+        }
+        const int32_t g = items[2 * task], word = items[2 * task + 1];
+        const int32_t i0 = word & ITEM_MEMBER_MASK;
+#define NB_OV_ITEM(R, S)                                                                      \
+    force_item<MODE, GUARD, R, S, F_TILE, false, true>(g, i0, tile, gfirst, gcount, glen, gbox,   \
+                                                       p_hi, p_lo, perm, list_xm, nullptr, cap,  \
+                                                       alloc, n, eps2, acc, pot, cnt, err)
+        if (word & ITEM_R2) {
+            NB_OV_ITEM(2, 1);
+        } else {
+            switch ((word >> ITEM_LS_SHIFT) & 7) {
+            case 0: NB_OV_ITEM(1, 1); break;
+            case 1: NB_OV_ITEM(1, 2); break;
+            case 2: NB_OV_ITEM(1, 4); break;
+            case 3: NB_OV_ITEM(1, 8); break;
+            case 4: NB_OV_ITEM(1, 16); break;
+            default: NB_OV_ITEM(1, 32); break;
+            }
+        }
+#undef NB_OV_ITEM
+        __syncwarp();
+    }
+    if (lane == 0) {
+        nb_atomic_add(&cnt[CNT_PP], pp);
+        nb_atomic_add(&cnt[CNT_PC], pc);
+        nb_atomic_add(&cnt[CNT_PP_CUM], pp);
+        nb_atomic_add(&cnt[CNT_PC_CUM], pc);
+        nb_atomic_add(&cnt[CNT_LIST_TOT], tot);
+        atomicMax(&cnt[CNT_LIST_MAX], (long long)mx);
+        atomicMax(&cnt[CNT_QMAX], (long long)qmax);
+        if (bad) atomicOr(err, bad);
+    }
+}
+
+template <int MODE, bool GUARD>
+static void launch_walk_force_t(nb_ctx *c, float eps2, float *acc, float *pot)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_walk_force<MODE, GUARD>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr = true;
+    }
+    // one pair of frontier queues per warp: no more warps than the queues hold
+    const int blocks = c->walk_warps / OV_WARPS;
+    k_walk_force<MODE, GUARD><<<blocks > 0 ? blocks : 1, OV_T, 0, c->stream>>>(
+        c->wrec, c->pid2bfs, c->gnode, c->gcount, c->gbox, c->cnt, c->glen, c->gcells,
+        c->list_id, c->list_xm, c->list_cap, c->list_alloc, c->wq, c->wq_cap, c->err, c->root,
+        c->n_depth, c->gfirst, c->nsys > 1 ? c->sys_sorted : nullptr,
+        c->nsys > 1 ? c->sys_root : nullptr, c->items, c->p_hi, c->p_lo, c->perm, c->n, eps2,
+        acc, pot, c->max_items, c->gready);
+    nb_launched(c, "k_walk_force");
+}
+
+// after the groups are formed: clears the counters and flags, then the
+// overlapped launch (FP32 and compensated modes)
+void nb_launch_walk_force(nb_ctx *c, float eps, float *acc, float *pot, int precision)
+{
+    cudaMemsetAsync(&c->cnt[CNT_LIST_TOT], 0, sizeof(long long) * 5, c->stream);
+    static_assert(CNT_LIST_TOT + 4 == CNT_WALK_Q, "counter layout");
+    cudaMemsetAsync(&c->cnt[CNT_QMAX], 0, sizeof(long long), c->stream);
+    cudaMemsetAsync(&c->cnt[CNT_FORCE_Q], 0, sizeof(long long), c->stream);
+    cudaMemsetAsync(c->gready, 0, sizeof(int32_t) * (size_t)c->max_n, c->stream);
+    const float eps2 = eps * eps;
+    const bool guard = !(eps2 >= FLT_MIN);
+    switch ((precision == NB_FP32_COMP ? 2 : 0) + (guard ? 1 : 0)) {
+    case 0: launch_walk_force_t<MODE_FP32, false>(c, eps2, acc, pot); break;
+    case 1: launch_walk_force_t<MODE_FP32, true>(c, eps2, acc, pot); break;
+    case 2: launch_walk_force_t<MODE_COMP, false>(c, eps2, acc, pot); break;
+    default: launch_walk_force_t<MODE_COMP, true>(c, eps2, acc, pot); break;
     }
 }
 

@@ -85,6 +85,7 @@ enum {
     SITE_SORT,        // radix-sort destination out of range
     SITE_MOMENTS_WAIT,  // a wait for a cell's children ran out (moments)
     SITE_SORT_WAIT,     // a radix-sort look-back wait ran out
+    SITE_OVERLAP_WAIT,  // a force item's wait for its group's walk ran out
     SITE_N_
 };
 
@@ -196,6 +197,7 @@ struct nb_ctx {
 
     // learned opening angle: group features (16 floats) and theta per group
     float *gfeat, *gtheta;
+    int32_t *gready;  // overlapped walk and force: a group's list is complete
 
     // device memory: one arena for every fixed-size array, one allocation
     // for the list storage (list_xm then list_id), one for the walk queues
@@ -229,6 +231,7 @@ struct nb_ctx {
     // timing and launch accounting
     int timing;
     int fused;               // leapfrog force passes use the fused walk and force
+    int overlap;             // leapfrog force passes overlap the walk with the force sum
     int feature_mode;        // learned theta: 0 probe-walk features, 1 tree-only features
     int key_order;           // NB_ORDER_MORTON or NB_ORDER_HILBERT (next build)
     // quadrupole cells: traceless Q (xx, yy, zz, xy, xz, yz) about the centre
@@ -290,9 +293,14 @@ void nb_launch_mlp_infer(nb_ctx *c, const float *params, const float *feat, floa
 
 // nb_force.cu
 void nb_launch_forces(nb_ctx *c, float eps, float *acc, float *pot, int precision);
+void nb_launch_walk_force(nb_ctx *c, float eps, float *acc, float *pot, int precision);
 int nb_launch_direct(const double *pos, const float *mass, int64_t n, double eps,
                      const int64_t *targets, int64_t nt, double *acc, double *pot,
                      cudaStream_t s);
+
+// the overlapped walk and force (nb_api.cu)
+extern "C" int nb_walk_forces(nb_ctx *c, float theta, int n_crit, float eps, float *acc,
+                              float *pot, int precision);
 
 // nb_neigh.cu
 int nb_neigh_run(nb_ctx *c, double h, int n_crit, int64_t *off, int32_t *idx, int64_t cap,
