@@ -473,6 +473,7 @@ k_walk_force(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ pid2b
         }
         act = __shfl_sync(FULL, act, 0);
         task = __shfl_sync(FULL, task, 0);
+        __syncwarp();   // lane 0's acquire orders the whole warp's reads of the list
         if (act == 0) break;
         if (act == 3) {
             if (lane == 0) nb_bad(cnt, err, SITE_FORCE, task);
