@@ -370,12 +370,13 @@ void nb_launch_forces(nb_ctx *c, float eps, float *acc, float *pot, int precisio
 // ---------------------------------------------------------------- overlap
 // The walk and the force sum in one persistent launch.  The walk is bound by
 // the latency of its record fetches and the force sum by the FMA pipe; run as
-// two launches, each leaves the other's unit idle.  Here every warp takes,
-// in turn, whatever is ready: a force item whose group's walk has finished,
-// else the next group to walk, else it waits (bounded) for the group of the
-// next force item.  Walks are taken in group order and force items in item
-// order (a group's items are contiguous), so a warp that waits waits for a
-// walk that a running warp has already claimed.  A finished walk publishes
+// two launches, each leaves the other's unit idle.  Here every warp claims
+// the next force item (item order, one atomic each) and, until that item's
+// group has been walked, walks the next group in line (group order); once
+// every walk is claimed it waits, bounded, for the claimed ones.  A group's
+// items are contiguous and walks go in group order, so a warp only ever
+// waits for walks that running warps have claimed, and the SMs hold walking
+// and summing warps at the same time.  A finished walk publishes
 // its list with a release store to the group's flag; a force warp acquires
 // the flag and reads the list through L2.  Every item and every list is
 // computed as in the two separate launches, so the results are the same bits.
@@ -431,67 +432,49 @@ k_walk_force(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ pid2b
     long long pp = 0, pc = 0, tot = 0;
     int32_t mx = 0, qmax = 0;
     unsigned bad = 0;
-    bool walks_left = true;
     for (;;) {
-        // lane 0 picks the next task: 1 a ready force item, 2 a walk, 3 skip a
-        // bad item, 0 done
-        int act = 0;
+        // the next force item, in item order (one atomic per item)
         long long task = 0;
-        if (lane == 0) {
-            for (unsigned spins = 0;;) {
-                const long long it = *(volatile long long *)&cnt[CNT_FORCE_Q];
-                if (it < nitems) {
-                    const int32_t g = items[2 * it];
-                    const bool okg = g >= 0 && g < G;
-                    if (!okg || ov_ld_acquire(&gready[g]) != 0) {
-                        if ((long long)atomicCAS((unsigned long long *)&cnt[CNT_FORCE_Q],
-                                                 (unsigned long long)it,
-                                                 (unsigned long long)(it + 1)) == it) {
-                            act = okg ? 1 : 3;
-                            task = it;
-                            break;
-                        }
-                        continue;   // another warp took it: look again
-                    }
-                }
-                if (walks_left) {
-                    const long long gnext = nb_atomic_add(&cnt[CNT_WALK_Q], 1LL);
-                    if (gnext < G) {
-                        act = 2;
-                        task = gnext;
-                        break;
-                    }
-                    walks_left = false;
-                }
-                if (it >= nitems) break;
-                if (++spins > OV_SPIN_LIMIT) {
-                    nb_bad(cnt, err, SITE_OVERLAP_WAIT, it);
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        act = __shfl_sync(FULL, act, 0);
+        if (lane == 0) task = nb_atomic_add(&cnt[CNT_FORCE_Q], 1LL);
         task = __shfl_sync(FULL, task, 0);
-        __syncwarp();   // lane 0's acquire orders the whole warp's reads of the list
-        if (act == 0) break;
-        if (act == 3) {
+        if (task >= nitems) break;
+        const int32_t gt = items[2 * task];
+        if (gt < 0 || gt >= G) {
             if (lane == 0) nb_bad(cnt, err, SITE_FORCE, task);
             continue;
         }
-        if (act == 2) {
-            const int g = (int)task;
-            walk_one<false, false>(g, wrec, pid2bfs, gnode, gcount, gbox, cnt, glen, gcells,
-                                   list_id, list_xm, nullptr, nullptr, cap, alloc, qa, qb, qa_s,
-                                   qb_s, wq_cap, err, nullptr, roots, n_depth, gfirst,
-                                   sys_sorted, sys_root, total, lane, lt, pp, pc, tot, mx, qmax,
-                                   bad);
-            __threadfence();   // every lane's list writes before the flag
-            __syncwarp();
-            if (lane == 0) ov_st_release(&gready[g], 1);
-            continue;
+        // until its group's list is complete, walk the next group in line;
+        // once every walk is claimed, wait (bounded) for the claimed ones
+        bool ready = false;
+        for (unsigned spins = 0;;) {
+            int32_t rd = 0;
+            if (lane == 0) rd = ov_ld_acquire(&gready[gt]);
+            ready = __shfl_sync(FULL, rd, 0) != 0;
+            if (ready) break;
+            long long gw = G;
+            if (lane == 0 && *(volatile long long *)&cnt[CNT_WALK_Q] < G)
+                gw = nb_atomic_add(&cnt[CNT_WALK_Q], 1LL);
+            gw = __shfl_sync(FULL, gw, 0);
+            if (gw < G) {
+                walk_one<false, false>((int)gw, wrec, pid2bfs, gnode, gcount, gbox, cnt, glen,
+                                       gcells, list_id, list_xm, nullptr, nullptr, cap, alloc, qa,
+                                       qb, qa_s, qb_s, wq_cap, err, nullptr, roots, n_depth,
+                                       gfirst, sys_sorted, sys_root, total, lane, lt, pp, pc, tot,
+                                       mx, qmax, bad);
+                __threadfence();   // every lane's list writes before the flag
+                __syncwarp();
+                if (lane == 0) ov_st_release(&gready[gw], 1);
+                continue;
+            }
+            if (++spins > OV_SPIN_LIMIT) {
+                if (lane == 0) nb_bad(cnt, err, SITE_OVERLAP_WAIT, gt);
+                break;
+            }
+            __nanosleep(100);
         }
-        const int32_t g = items[2 * task], word = items[2 * task + 1];
+        __syncwarp();   // lane 0's acquire orders the whole warp's reads of the list
+        if (!ready) break;
+        const int32_t g = gt, word = items[2 * task + 1];
         const int32_t i0 = word & ITEM_MEMBER_MASK;
 #define NB_OV_ITEM(R, S)                                                                      \
     force_item<MODE, GUARD, R, S, F_TILE, false, true>(g, i0, tile, gfirst, gcount, glen, gbox,   \
