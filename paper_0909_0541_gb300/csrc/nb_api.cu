@@ -177,9 +177,25 @@ static void carve_context(nb_ctx *c, Arena &a)
     }
 }
 
+// A captured graph holds the device addresses of the list storage and the
+// walk queues in its kernel nodes; once either is freed and allocated again,
+// replaying it would touch freed memory.  Every such reallocation drops the
+// graph (nb_graph_launch then returns NB_ERR_STATE until the next capture).
+static void drop_graph(nb_ctx *c)
+{
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+        c->graph_launches = 0;
+        c->ev_graph = 0;
+        c->graph_runs = 0;
+    }
+}
+
 // walk queues: two frontier queues of wq_cap entries per warp
 static bool alloc_queues(nb_ctx *c, int64_t wq_cap)
 {
+    drop_graph(c);
     if (c->wq) cudaFree(c->wq);
     c->wq = nullptr;
     c->wq_cap = 0;
@@ -345,6 +361,7 @@ static int ensure_lists(nb_ctx *c, int64_t groups, int64_t cap)
     if (need <= c->list_alloc && cap == c->list_cap && !want_q) return NB_OK;
     if (need > c->list_alloc || want_q) {
         CK(cudaStreamSynchronize(c->stream));
+        drop_graph(c);
         if (c->list_mem) cudaFree(c->list_mem);
         c->list_mem = nullptr;
         c->list_id = nullptr;

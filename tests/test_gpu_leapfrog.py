@@ -151,3 +151,35 @@ def test_graph_replay_times_its_phases_and_equals_eager_steps():
             ctx.sync_status()
         out.append((pos.cpu().numpy(), vel.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_graph_dropped_when_list_storage_is_reallocated():
+    """A captured graph holds the list storage's addresses: a later
+    synchronising walk that needs more room reallocates it and must drop the
+    graph (replaying it would touch freed memory), so the next launch is
+    refused with NB_ERR_STATE and a new capture works."""
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(6000, 93)
+    dev = torch.device("cuda")
+    pos = torch.from_numpy(ps.pos).to(dev)
+    vel = torch.from_numpy(ps.vel).to(dev)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(stream):
+        ctx = nb.NBody(ps.n, eps=1 / 64, theta=0.75, n_crit=64, stream=stream)
+        ctx.leapfrog_step(pos, vel, mass, 1 / 128)
+        ctx.graph_capture_leapfrog(pos, vel, mass, 1 / 128, 2)
+        ctx.graph_launch()
+        ctx.sync_status()
+        ctx.build_tree(pos, mass)
+        ctx.walk_groups(0.0, 64)          # every list holds every particle: more room
+        with pytest.raises(nb.NBError) as ei:
+            ctx.graph_launch()
+        assert ei.value.code == -6        # STATE: capture again
+        ctx.leapfrog_reset()
+        ctx.leapfrog_step(pos, vel, mass, 1 / 128)
+        ctx.graph_capture_leapfrog(pos, vel, mass, 1 / 128, 2)
+        ctx.graph_launch()
+        ctx.sync_status()
+        ctx.close()
