@@ -57,8 +57,12 @@ def parse():
     ap.add_argument("--fused", action="store_true",
                     help="force passes walk and sum in one kernel, no interaction lists")
     ap.add_argument("--judge-targets", type=int, default=8192)
-    ap.add_argument("--train-groups", type=int, default=6000,
-                    help="learned4.19m: groups labelled for training")
+    ap.add_argument("--train-groups", type=int, default=10527,
+                    help="learned theta: groups labelled for training (x 19 grid thetas: "
+                         "about 200k samples)")
+    ap.add_argument("--judge-per-group", type=int, default=24,
+                    help="learned theta: members of each training group judged against the "
+                         "FP64 direct sum")
     ap.add_argument("--learned-form", default="tree", choices=["tree", "probe"],
                     help="learned4.19m: tree-only features and labels from predicted "
                          "curves (tree), or probe-walk features and labels from the "
@@ -621,7 +625,8 @@ def learned_comparison(args, dev):
     X, y, info = learn.make_dataset(tpos, tmass, eps, n_crit, args.train_groups, seed=1,
                                     ctx=tctx, feature_mode=mode,
                                     label_rule="predicted" if mode == 1 else "measured",
-                                    walk_weight=walk_weight, label_stat=args.label_stat)
+                                    walk_weight=walk_weight, label_stat=args.label_stat,
+                                    judge_per_group=args.judge_per_group)
     params, hist = learn.train(X, y, epochs=150, batch=256, lr=2e-3)
     g = torch.Generator().manual_seed(98)
     ttg = torch.randperm(tr.n, generator=g)[: args.judge_targets].to(dev)
@@ -684,6 +689,7 @@ def learned_comparison(args, dev):
         "workload": "halomix4.19m", "n": ps.n, "eps": eps, "n_crit": n_crit,
         "train_set": "halo mix 4,194,304 (3000 halos, another seed)",
         "train_groups": int(X.shape[0]), "train_samples": int(X.shape[0]) * len(learn.THETA_GRID),
+        "judged_members_per_group": f"at most {args.judge_per_group}",
         "error_budget": learn.BUDGET,
         "learned_form": ("tree-only features, labels from predicted curves"
                          if mode == 1 else "probe-walk features, labels from measured curves"),

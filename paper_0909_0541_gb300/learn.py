@@ -58,15 +58,23 @@ def pack_params(w: dict, mu, sigma) -> np.ndarray:
     return p.astype(np.float32)
 
 
-def judge_targets(ctx: NBody, groups: np.ndarray):
-    """Caller indices of the members of `groups` (in group order) and the
-    offsets of each group's rows."""
+def judge_targets(ctx: NBody, groups: np.ndarray, per_group=0, seed=0):
+    """Caller indices of the judged members of `groups` (in group order), the
+    offsets of each group's rows, and the groups' sizes.  per_group > 0 judges
+    a seeded random subset of at most that many members per group."""
     gg = ctx.copy_groups()
     perm = ctx.copy_perm()
     first, count = gg["gfirst"][groups], gg["gcount"][groups]
-    targets = np.concatenate([perm[f:f + c] for f, c in zip(first, count)]).astype(np.int64)
-    off = np.r_[0, np.cumsum(count)].astype(np.int64)
-    return targets, off
+    rng = np.random.default_rng(seed)
+    rows = []
+    for f, c in zip(first, count):
+        m = perm[f:f + c]
+        if per_group and c > per_group:
+            m = m[np.sort(rng.choice(c, per_group, replace=False))]
+        rows.append(m)
+    targets = np.concatenate(rows).astype(np.int64)
+    off = np.r_[0, np.cumsum([len(r) for r in rows])].astype(np.int64)
+    return targets, off, count.astype(np.float32)
 
 
 TREE_COLS = [0, 1, 2, 3, 4, 5, 11]   # the features of feature mode 1 (no walk)
@@ -74,7 +82,7 @@ TREE_COLS = [0, 1, 2, 3, 4, 5, 11]   # the features of feature mode 1 (no walk)
 
 def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget=BUDGET,
                  ctx: NBody | None = None, feature_mode=0, label_rule="measured",
-                 walk_weight=0.0, label_stat="groups"):
+                 walk_weight=0.0, label_stat="groups", judge_per_group=0):
     """(features (S,16), labels (S,), info) for S seeded random groups of the
     particle set (pos, mass: CUDA tensors); info holds the error and cost
     curves, the group sizes, the sampled groups and the exchange rate.
@@ -86,7 +94,8 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
     walk's time per list entry in units of the force's time per interaction
     (0: interactions only).  label_stat: the error statistic the exchange rate
     is bisected on, "groups" (n_g-weighted median of group medians) or
-    "particles" (median over the judged particles)."""
+    "particles" (median over the judged particles).  judge_per_group > 0 judges
+    at most that many seeded members of each group against the direct sum."""
     import torch
     n = int(pos.shape[0])
     own = ctx is None
@@ -97,8 +106,7 @@ def make_dataset(pos, mass, eps, n_crit, n_sample, seed, grid=THETA_GRID, budget
     G = int(feat.shape[0])
     rng = np.random.default_rng(seed)
     sel = np.sort(rng.choice(G, min(n_sample, G), replace=False))
-    targets, off = judge_targets(ctx, sel)
-    size = np.diff(off).astype(np.float32)
+    targets, off, size = judge_targets(ctx, sel, judge_per_group, seed + 17)
     dev = pos.device
     t_dev = torch.from_numpy(targets).to(dev)
     o_dev = torch.from_numpy(off).to(dev)
