@@ -915,48 +915,63 @@ k_sys_of(const int64_t *__restrict__ off, int64_t nsys, int64_t n, int32_t *__re
     }
 }
 
-// bounding box and root cube of each system (one block per system), the
-// same arithmetic as k_bbox + k_root
-__global__ void __launch_bounds__(256)
+// bounding box and root cube of each system (one block of 1024 threads per
+// system), the same arithmetic as k_bbox + k_root: min / max on the
+// order-preserving integer image of the FP64 bits (integer compares instead
+// of FP64 ones), then the root cube in FP64 with explicit rounding
+#define RS_SYS_T 1024
+__global__ void __launch_bounds__(RS_SYS_T)
 k_roots_sys(const double *__restrict__ pos, const int64_t *__restrict__ off, int64_t nsys,
             int64_t n, double *__restrict__ roots, unsigned *__restrict__ err)
 {
-    __shared__ double s[8][6];
+    const long long FLIP = 0x7fffffffffffffffll;
+    __shared__ long long s[RS_SYS_T / 32][6];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long *__restrict__ pb = reinterpret_cast<const long long *>(pos);
     for (int64_t sy = blockIdx.x; sy < nsys; sy += gridDim.x) {
         int64_t a = off[sy], b = off[sy + 1];
         a = a < 0 ? 0 : (a > n ? n : a);
         b = b < a ? a : (b > n ? n : b);
-        double lo[3], hi[3];
-        for (int k = 0; k < 3; k++) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+        long long lo[3], hi[3];
+        for (int k = 0; k < 3; k++) { lo[k] = LLONG_MAX; hi[k] = LLONG_MIN; }
         bool bad = false;
         for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x)
+#pragma unroll
             for (int k = 0; k < 3; k++) {
-                const double x = pos[3 * i + k];
-                bad |= !isfinite(x);
-                lo[k] = fmin(lo[k], x);
-                hi[k] = fmax(hi[k], x);
+                const long long bits = pb[3 * i + k];
+                bad |= (bits & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;   // inf or NaN
+                const long long key = bits ^ ((bits >> 63) & FLIP);
+                lo[k] = min(lo[k], key);
+                hi[k] = max(hi[k], key);
             }
         if (bad) atomicOr(err, NB_EF_NONFINITE);
+#pragma unroll
         for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
             for (int k = 0; k < 3; k++) {
-                lo[k] = fmin(lo[k], __shfl_down_sync(0xffffffffu, lo[k], o));
-                hi[k] = fmax(hi[k], __shfl_down_sync(0xffffffffu, hi[k], o));
+                lo[k] = min(lo[k], __shfl_down_sync(0xffffffffu, lo[k], o));
+                hi[k] = max(hi[k], __shfl_down_sync(0xffffffffu, hi[k], o));
             }
         if (lane == 0)
             for (int k = 0; k < 3; k++) { s[w][k] = lo[k]; s[w][3 + k] = hi[k]; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int ww = 1; ww < (int)(blockDim.x >> 5); ww++)
+            for (int ww = 1; ww < RS_SYS_T / 32; ww++)
                 for (int k = 0; k < 3; k++) {
-                    s[0][k] = fmin(s[0][k], s[ww][k]);
-                    s[0][3 + k] = fmax(s[0][3 + k], s[ww][3 + k]);
+                    s[0][k] = min(s[0][k], s[ww][k]);
+                    s[0][3 + k] = max(s[0][3 + k], s[ww][3 + k]);
                 }
+            double lx[3], hx[3];
+            for (int k = 0; k < 6; k++) {   // back to FP64 (the map is its own inverse)
+                const long long v = s[0][k];
+                const double x = __longlong_as_double(v ^ ((v >> 63) & FLIP));
+                if (k < 3) lx[k] = x; else hx[k - 3] = x;
+            }
             double *root = roots + 8 * sy;
             double ext = 0.0;
             for (int k = 0; k < 3; k++) {
-                root[k] = __dmul_rn(0.5, __dadd_rn(s[0][k], s[0][3 + k]));
-                const double e = __dsub_rn(s[0][3 + k], s[0][k]);
+                root[k] = __dmul_rn(0.5, __dadd_rn(lx[k], hx[k]));
+                const double e = __dsub_rn(hx[k], lx[k]);
                 if (e > ext) ext = e;
             }
             double L = __dmul_rn(ext, 1.0 + 0x1p-20);
@@ -1014,7 +1029,7 @@ void nb_launch_build_batched(nb_ctx *c, const double *pos, const float *mass, in
     const int gs = (int)(nsys < 65535 ? nsys : 65535);
     k_sys_of<<<gs, 256, 0, s>>>(off, nsys, n, c->sys_of, c->err);
     nb_launched(c, "k_sys_of");
-    k_roots_sys<<<gs, 256, 0, s>>>(pos, off, nsys, n, c->root, c->err);
+    k_roots_sys<<<gs, RS_SYS_T, 0, s>>>(pos, off, nsys, n, c->root, c->err);
     nb_launched(c, "k_roots_sys");
     k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, c->sys_of, c->keys, c->idx,
                                            c->key_order);
