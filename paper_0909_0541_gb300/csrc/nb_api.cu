@@ -211,8 +211,7 @@ static const char *const SITE_NAME[SITE_N_] = {
     "k_moments: cell, parent or child run", "groups: group or member range",
     "k_items: item index", "k_walk: queued node", "k_walk: child run", "k_force: item",
     "k_rs_scatter: destination", "k_moments: wait for children ran out",
-    "k_rs_scatter: look-back wait ran out", "k_walk_force: wait for a group's walk ran out",
-    "k_force: a list tile's copy did not arrive"};
+    "k_rs_scatter: look-back wait ran out", "k_walk_force: wait for a group's walk ran out"};
 
 static int err_code(unsigned bits)
 {
@@ -1341,19 +1340,6 @@ int nb_copy_group_lengths(nb_ctx *c, int32_t *len, int64_t cap)
     return NB_OK;
 }
 
-// records 0 .. L-1 of a list copied in the paired layout of a force tile
-// (records 2p, 2p+1 as {x, x', y, y'} {z, z', m, m'}) into rows (x, y, z, m)
-static void unpair(const float *paired, int64_t L, float *xm)
-{
-    for (int64_t j = 0; j < L; j++) {
-        const float *t = paired + 4 * (j & ~(int64_t)1) + (j & 1);
-        xm[4 * j] = t[0];
-        xm[4 * j + 1] = t[2];
-        xm[4 * j + 2] = t[4];
-        xm[4 * j + 3] = t[6];
-    }
-}
-
 int nb_copy_list(nb_ctx *c, int64_t g, int32_t *entries, float *xm, int64_t cap,
                  int64_t *len_out)
 {
@@ -1372,21 +1358,11 @@ int nb_copy_list(nb_ctx *c, int64_t g, int32_t *entries, float *xm, int64_t cap,
     if (entries && L > 0)
         CK(cudaMemcpyAsync(entries, c->list_id + g * c->list_cap, sizeof(int32_t) * L,
                            cudaMemcpyDeviceToHost, c->stream));
-    float *paired = nullptr;
-    const int64_t L2 = (L + 1) & ~(int64_t)1;   // whole pairs (the slot is even)
-    if (xm && L > 0) {
-        paired = (float *)malloc(sizeof(float4) * (size_t)L2);
-        if (!paired) return NB_ERR_NOMEM;
-        if (cudaMemcpyAsync(paired, c->list_xm + g * c->list_cap, sizeof(float4) * L2,
-                            cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
-            free(paired);
-            return NB_ERR_CUDA;
-        }
-    }
-    const bool okc = cudaStreamSynchronize(c->stream) == cudaSuccess;
-    if (okc && paired) unpair(paired, L, xm);
-    free(paired);
-    return okc ? NB_OK : NB_ERR_CUDA;
+    if (xm && L > 0)
+        CK(cudaMemcpyAsync(xm, c->list_xm + g * c->list_cap, sizeof(float4) * L,
+                           cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NB_OK;
 }
 
 int nb_copy_lists(nb_ctx *c, int64_t *offsets, int32_t *entries, float *xm)
@@ -1408,42 +1384,26 @@ int nb_copy_lists(nb_ctx *c, int64_t *offsets, int32_t *entries, float *xm)
         free(len);
         return NB_ERR_CUDA;
     }
-    // the records travel in their paired layout and are unpaired on the host
-    float *paired = nullptr;
-    if (xm) {
-        paired = (float *)malloc(sizeof(float4) * (size_t)(c->list_cap > 0 ? c->list_cap : 1));
-        if (!paired) {
-            free(len);
-            return NB_ERR_NOMEM;
-        }
-    }
     int64_t off = 0;
-    int rc2 = NB_OK;
-    for (int64_t g = 0; g < G && rc2 == NB_OK; g++) {
+    for (int64_t g = 0; g < G; g++) {
         if (offsets) offsets[g] = off;
         const int64_t L = len[g] < c->list_cap ? len[g] : c->list_cap;
         if (entries && L > 0 &&
             cudaMemcpyAsync(entries + off, c->list_id + g * c->list_cap, sizeof(int32_t) * L,
-                            cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-            rc2 = NB_ERR_CUDA;
-        if (rc2 == NB_OK && xm && L > 0) {
-            const int64_t L2 = (L + 1) & ~(int64_t)1;
-            if (cudaMemcpyAsync(paired, c->list_xm + g * c->list_cap, sizeof(float4) * L2,
-                                cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-                cudaStreamSynchronize(c->stream) != cudaSuccess)
-                rc2 = NB_ERR_CUDA;
-            else
-                unpair(paired, L, xm + 4 * off);
+                            cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+            free(len);
+            return NB_ERR_CUDA;
+        }
+        if (xm && L > 0 &&
+            cudaMemcpyAsync(xm + 4 * off, c->list_xm + g * c->list_cap, sizeof(float4) * L,
+                            cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+            free(len);
+            return NB_ERR_CUDA;
         }
         off += len[g];
     }
-    if (offsets && rc2 == NB_OK) offsets[G] = off;
+    if (offsets) offsets[G] = off;
     free(len);
-    free(paired);
-    if (rc2) {
-        cudaGetLastError();
-        return rc2;
-    }
     CK(cudaStreamSynchronize(c->stream));
     return NB_OK;
 }

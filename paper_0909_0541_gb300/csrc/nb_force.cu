@@ -42,12 +42,9 @@
 // phase adds the quadrupole term (TILE = 32, FP32 modes)
 // CG: the list and its length are read through L2 only (the overlapped
 // kernel reads lists that other warps of the same launch wrote)
-// Non-QUAD tiles arrive by bulk copy: `tile` holds two buffers of TILE records,
-// mbar two mbarriers, ph the warp's expected parity of each.
 template <int MODE, bool GUARD, int R, int S, int TILE, bool QUAD, bool CG = false>
 __device__ __forceinline__ void force_item(
-    int32_t g, int32_t i0, float4 *tile, uint64_t *mbar, uint32_t &ph,
-    const int32_t *__restrict__ gfirst,
+    int32_t g, int32_t i0, float4 *tile, const int32_t *__restrict__ gfirst,
     const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
     const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
     const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
@@ -100,7 +97,7 @@ __device__ __forceinline__ void force_item(
             const bool in = jj < len;
             const float4 qa = in ? srq[2 * (int64_t)jj] : z4;
             const float4 qb = in ? srq[2 * (int64_t)jj + 1] : z4;
-            put_rec_q(tile, lane, in ? paired_rec(src, jj) : pad, qa, qb);
+            put_rec_q(tile, lane, in ? src[jj] : pad, qa, qb);
             const unsigned qm = __ballot_sync(0xffffffffu, qa.x != 0.f || qa.y != 0.f ||
                                                                qa.z != 0.f || qa.w != 0.f ||
                                                                qb.x != 0.f || qb.y != 0.f);
@@ -109,39 +106,15 @@ __device__ __forceinline__ void force_item(
             __syncwarp();
         }
     } else {
-        // tile k lands in buffer k & 1 while the warp sums tile k - 1
-        const int32_t ntile = (len + TILE - 1) / TILE;
-        const int32_t len2 = (len + 1) & ~1;   // whole pairs of the paired layout
-        if (ntile > 0 && lane == 0)
-            bulk_tile(tile, src, 16u * (uint32_t)(len2 < TILE ? len2 : TILE), &mbar[0]);
-        for (int32_t k = 0; k < ntile; k++) {
-            const int b = k & 1;
-            float4 *buf = tile + b * TILE;
-            if (k + 1 < ntile && lane == 0) {
-                const int32_t j1 = (k + 1) * TILE;
-                const int32_t nr = len2 - j1 < TILE ? len2 - j1 : TILE;
-                bulk_tile(tile + (b ^ 1) * TILE, src + j1, 16u * (uint32_t)nr, &mbar[b ^ 1]);
-            }
-            const bool landed = mbar_wait(&mbar[b], (ph >> b) & 1u);
-            ph ^= 1u << b;
-            if (!__all_sync(0xffffffffu, landed)) {
-                // a tile that never arrived: report it, wait (bounded) for the
-                // copy still in flight, and leave the item's sums invalid
-                if (lane == 0) nb_bad(cnt, err, SITE_TILE_WAIT, g);
-                if (k + 1 < ntile) {
-                    mbar_wait(&mbar[b ^ 1], (ph >> (b ^ 1)) & 1u);
-                    ph ^= 1u << (b ^ 1);
-                }
-                break;
-            }
-            const int32_t j0 = k * TILE;
-            if (j0 + TILE > len) {   // the last tile: padding past the list
+        for (int32_t j0 = 0; j0 < len; j0 += TILE) {
 #pragma unroll
-                for (int q = 0; q < TK; q++)
-                    if (j0 + q * NB_WARP + lane >= len) put_rec(buf, q * NB_WARP + lane, pad);
-                __syncwarp();
+            for (int k = 0; k < TK; k++) {
+                const int32_t jj = j0 + k * NB_WARP + lane;
+                put_rec(tile, k * NB_WARP + lane,
+                        jj < len ? (CG ? __ldcg(&src[jj]) : src[jj]) : pad);
             }
-            tile_pass<MODE, GUARD, false, R, W * TK>(buf, stream * W * TK, j0 + stream * W * TK,
+            __syncwarp();
+            tile_pass<MODE, GUARD, false, R, W * TK>(tile, stream * W * TK, j0 + stream * W * TK,
                                                      t, kk, eps2, A, P);
             __syncwarp();
         }
@@ -277,16 +250,9 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
         float *__restrict__ acc, float *__restrict__ pot, unsigned *__restrict__ err,
         int64_t max_items)
 {
-    __shared__ __align__(128) float4 tiles[BT / NB_WARP][QUAD ? TILE * 5 / 2 : 2 * TILE];
-    __shared__ __align__(8) uint64_t mbars[BT / NB_WARP][2];
+    __shared__ float4 tiles[BT / NB_WARP][QUAD ? TILE * 5 / 2 : TILE];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-        mbar_init(&mbars[w][0]);
-        mbar_init(&mbars[w][1]);
-    }
-    __syncwarp();
-    uint32_t ph = 0;
     int32_t nitems = (int32_t)cnt[CNT_ITEMS];
     const int32_t ngroups = (int32_t)cnt[CNT_GROUPS];
     if (nitems > max_items) {
@@ -310,8 +276,7 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
             continue;
         }
 #define NB_FORCE_ITEM_AT(R, S, I0)                                                            \
-    force_item<MODE, GUARD, R, S, TILE, QUAD>(g, I0, tiles[w], mbars[w], ph, gfirst, gcount,     \
-                                              glen, gbox, p_hi,                                 \
+    force_item<MODE, GUARD, R, S, TILE, QUAD>(g, I0, tiles[w], gfirst, gcount, glen, gbox, p_hi,  \
                                               p_lo, perm, list_xm, list_q, cap, alloc, n, eps2,   \
                                               acc, pot, cnt, err)
 #define NB_FORCE_ITEM(R, S) NB_FORCE_ITEM_AT(R, S, i0)
@@ -453,17 +418,10 @@ k_walk_force(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ pid2b
     int32_t *const qa = wq + gw * 2 * wq_cap;
     int32_t *const qb = qa + wq_cap;
     // per warp: the walk's frontier queues, or (while it sums) the force tile
-    __shared__ __align__(128) int32_t sq[OV_WARPS][2 * WQ_SMEM];
-    __shared__ __align__(8) uint64_t mbars[OV_WARPS][2];
+    __shared__ __align__(16) int32_t sq[OV_WARPS][2 * WQ_SMEM];
     int32_t *const qa_s = sq[w];
     int32_t *const qb_s = qa_s + WQ_SMEM;
     float4 *const tile = reinterpret_cast<float4 *>(sq[w]);
-    if (lane == 0) {
-        mbar_init(&mbars[w][0]);
-        mbar_init(&mbars[w][1]);
-    }
-    __syncwarp();
-    uint32_t ph = 0;
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     const int32_t total = (int32_t)cnt[CNT_NODES];
     int32_t nitems = (int32_t)cnt[CNT_ITEMS];
@@ -519,8 +477,7 @@ k_walk_force(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ pid2b
         const int32_t g = gt, word = items[2 * task + 1];
         const int32_t i0 = word & ITEM_MEMBER_MASK;
 #define NB_OV_ITEM(R, S)                                                                      \
-    force_item<MODE, GUARD, R, S, F_TILE, false, true>(g, i0, tile, mbars[w], ph, gfirst,       \
-                                                       gcount, glen, gbox,                      \
+    force_item<MODE, GUARD, R, S, F_TILE, false, true>(g, i0, tile, gfirst, gcount, glen, gbox,   \
                                                        p_hi, p_lo, perm, list_xm, nullptr, cap,  \
                                                        alloc, n, eps2, acc, pot, cnt, err)
         if (word & ITEM_R2) {

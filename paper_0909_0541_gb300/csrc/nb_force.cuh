@@ -258,67 +258,6 @@ __device__ __forceinline__ void stream_sum(Acc<MODE> &A, int o)
 }
 
 
-// ---------------------------------------------------------------- list tiles
-// The walk stores every list in the paired layout of a tile (records 2p,
-// 2p+1 interleaved in two 16-byte slots), so a tile is a straight copy of
-// TILE x 16 bytes: one lane issues it as a bulk asynchronous copy
-// (cp.async.bulk) into shared memory, completing on an mbarrier, and the warp
-// computes on the previous tile meanwhile (two buffers).  The copy costs no
-// registers and no load or store instruction per lane.
-#define NB_MBAR_SPIN (1u << 22)   // polls before a wait for a tile gives up
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// one thread: an mbarrier expecting one arrival, made visible to the
-// asynchronous proxy
-__device__ __forceinline__ void mbar_init(uint64_t *mbar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// one thread: `bytes` (a multiple of 16) from global src to shared dst,
-// completing on mbar; earlier generic writes to dst are ordered before it
-__device__ __forceinline__ void bulk_tile(void *dst, const void *src, uint32_t bytes,
-                                          uint64_t *mbar)
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
-}
-
-// every lane: wait for the phase of the given parity to complete (bounded);
-// false when the wait gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity)
-{
-    const uint32_t m = smem_u32(mbar);
-    for (unsigned i = 0; i < NB_MBAR_SPIN; i++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(m), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// record j of a list stored in the paired layout (global memory)
-__device__ __forceinline__ float4 paired_rec(const float4 *list, int64_t j)
-{
-    const float *t = reinterpret_cast<const float *>(list) + 4 * (j & ~(int64_t)1) + (j & 1);
-    return make_float4(t[0], t[2], t[4], t[6]);
-}
-
 // ---------------------------------------------------------------- quadrupole
 // Cells carry their traceless quadrupole Q about the centre of mass; the
 // particle-cell term gains (softened like Eq. (gravity), R^2 = |r|^2 +

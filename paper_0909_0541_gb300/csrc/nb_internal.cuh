@@ -86,7 +86,6 @@ enum {
     SITE_MOMENTS_WAIT,  // a wait for a cell's children ran out (moments)
     SITE_SORT_WAIT,     // a radix-sort look-back wait ran out
     SITE_OVERLAP_WAIT,  // a force item's wait for its group's walk ran out
-    SITE_TILE_WAIT,     // a force tile's bulk copy did not arrive within the limit
     SITE_N_
 };
 

@@ -116,13 +116,8 @@ __device__ __forceinline__ void visit_node(
                                         : len + __popc(cm) + __popc(em & ~cm & lt);
         if (pos < room) {
             list_id[base + pos] = r.wb.x;
-            // the paired layout of a force tile: records 2p, 2p+1 interleaved
-            // as {x, x', y, y'} {z, z', m, m'} (base is even)
-            float *t = reinterpret_cast<float *>(list_xm + base) + 4 * (pos & ~1) + (pos & 1);
-            t[0] = nb_rel(r.a.x, r.d.x, bc.x);
-            t[2] = nb_rel(r.a.y, r.d.y, bc.y);
-            t[4] = nb_rel(r.a.z, r.d.z, bc.z);
-            t[6] = r.a.w;
+            list_xm[base + pos] = make_float4(nb_rel(r.a.x, r.d.x, bc.x), nb_rel(r.a.y, r.d.y, bc.y),
+                                              nb_rel(r.a.z, r.d.z, bc.z), r.a.w);
             if constexpr (QUAD) {   // the cell's Q in FP32 (zero for a particle)
                 float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (cell_emit) {
