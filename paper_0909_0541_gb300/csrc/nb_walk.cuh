@@ -132,13 +132,28 @@ __device__ __forceinline__ void visit_node(
     }
     len += __popc(em);
     ncell += __popc(__ballot_sync(FULL, cell_emit));
-    int32_t incl = nch;
+    // exclusive prefix sum of the children over the lanes: with at most 15
+    // children per lane (every cell but a level-21 bucket), from one ballot
+    // per bit of the count; otherwise by a shuffle scan
+    int32_t excl = 0, tot = 0;
+    if (__any_sync(FULL, nch > 15)) {
+        int32_t incl = nch;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        excl = incl - nch;
+        tot = __shfl_sync(FULL, incl, 31);
+    } else {
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const unsigned m = __ballot_sync(FULL, (nch >> b) & 1);
+            excl += __popc(m & lt) << b;
+            tot += __popc(m) << b;
+        }
     }
-    const int32_t start = nb + incl - nch;
+    const int32_t start = nb + excl;
     if (open) {
         if (nch <= 8 && start + nch <= WQ_SMEM) {   // the common case: all in shared memory
 #pragma unroll
@@ -152,7 +167,7 @@ __device__ __forceinline__ void visit_node(
             }
         }
     }
-    nb += __shfl_sync(FULL, incl, 31);
+    nb += tot;
 }
 
 
