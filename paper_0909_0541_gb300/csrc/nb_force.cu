@@ -3,10 +3,13 @@
 // Work items cut a group's members into 64-target items (two targets per
 // lane) while 64 or more remain, then one 32-target item if more than 32
 // remain, then a tail of at most 32 targets rounded up to a power of two m'.
-// A tail runs as S = 32 / m' source streams: the warp is S rows of m' lanes,
-// stream s takes entries s*W .. s*W+W-1 (W = 32/S) of every 32-record tile,
-// and the streams' sums are combined with shuffles at the end -- so small
-// groups keep every lane busy.  One warp takes one item from a global queue;
+// An item of m' <= 32 targets runs as S source streams: the warp is S rows
+// of W = 32/S lanes, stream s takes entries s*W .. s*W+W-1 of every
+// 32-record tile, and the streams' sums are combined with shuffles at the
+// end -- so small groups keep every lane busy.  Items of 4 to 32 targets
+// hold two targets per lane (S = 64/m'), like the 64-target items, so every
+// staged record pair feeds two interactions; items of two and one targets
+// hold one (S = 16, 32).  One warp takes one item from a global queue;
 // targets are FP32 coordinates relative to the group centre.  Sources are
 // staged TILE at a time: one coalesced 16-byte load per lane into a per-warp
 // shared-memory tile, then broadcast reads.  The tile holds record
@@ -36,8 +39,8 @@
 
 #define F_T 256
 
-// R targets per lane (R = 2 only with S = 1); S source streams: lane l is
-// target row l % W of stream l / W, W = 32 / S
+// R targets per lane; S source streams: lane l is target row l % W of
+// stream l / W, W = 32 / S, and holds targets i0 + row + r W (r < R)
 // QUAD: list records carry the cells' quadrupoles (list_q) and the list
 // phase adds the quadrupole term (TILE = 32, FP32 modes)
 // CG: the list and its length are read through L2 only (the overlapped
@@ -67,23 +70,21 @@ __device__ __forceinline__ void force_item(
     if (lim < 0) lim = 0;
     const int32_t gl = CG ? __ldcg(&glen[g]) : glen[g];
     const int32_t len = gl < lim ? gl : (int32_t)lim;
-    const float4 bc = gbox[3 * (int64_t)g + 2];
     const float4 pad = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
     Tgt t[R];
-    int32_t kk[R], slot[R];
-    bool ok[R];
     Acc<MODE> A[R];
     Sum2 P[R];
+    {
+        const float4 bc = gbox[3 * (int64_t)g + 2];
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int32_t k = i0 + r * W + row;
-        ok[r] = k < ng;
-        kk[r] = k;
-        slot[r] = f + (ok[r] ? k : ng - 1);
-        const float4 h = p_hi[slot[r]], lo = p_lo[slot[r]];
-        t[r].set(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y), nb_rel(h.z, lo.z, bc.z));
-        A[r].init();
-        P[r].init();
+        for (int r = 0; r < R; r++) {
+            const int32_t k = i0 + r * W + row;
+            const int32_t s = f + (k < ng ? k : ng - 1);
+            const float4 h = p_hi[s], lo = p_lo[s];
+            t[r].set(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y), nb_rel(h.z, lo.z, bc.z));
+            A[r].init();
+            P[r].init();
+        }
     }
     // (1) the list: sources outside the group, TILE records per tile
     constexpr int TK = TILE / NB_WARP;   // records each lane stages per tile
@@ -106,25 +107,40 @@ __device__ __forceinline__ void force_item(
             __syncwarp();
         }
     } else {
+        // the next tile's records are loaded into registers while the warp
+        // sums the current one, so the list fetch overlaps the arithmetic
+        float4 nxt[TK];
+#pragma unroll
+        for (int k = 0; k < TK; k++) {
+            const int32_t jj = k * NB_WARP + lane;
+            nxt[k] = jj < len ? (CG ? __ldcg(&src[jj]) : src[jj]) : pad;
+        }
         for (int32_t j0 = 0; j0 < len; j0 += TILE) {
 #pragma unroll
-            for (int k = 0; k < TK; k++) {
-                const int32_t jj = j0 + k * NB_WARP + lane;
-                put_rec(tile, k * NB_WARP + lane,
-                        jj < len ? (CG ? __ldcg(&src[jj]) : src[jj]) : pad);
-            }
+            for (int k = 0; k < TK; k++) put_rec(tile, k * NB_WARP + lane, nxt[k]);
             __syncwarp();
+#pragma unroll
+            for (int k = 0; k < TK; k++) {
+                const int32_t jj = j0 + TILE + k * NB_WARP + lane;
+                nxt[k] = jj < len ? (CG ? __ldcg(&src[jj]) : src[jj]) : pad;
+            }
             tile_pass<MODE, GUARD, false, R, W * TK>(tile, stream * W * TK, j0 + stream * W * TK,
-                                                     t, kk, eps2, A, P);
+                                                     t, nullptr, eps2, A, P);
             __syncwarp();
         }
     }
-    // (2) the group's own members, j != i
-    for (int32_t j0 = 0; j0 < ng; j0 += NB_WARP) {
+    // (2) the group's own members, j != i (the group's range and centre are
+    // taken up again here, so they need not stay live through the list phase)
+    const int32_t f2 = gfirst[g], ng2 = gcount[g];
+    const float4 bc = gbox[3 * (int64_t)g + 2];
+    int32_t kk[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) kk[r] = i0 + r * W + row;
+    for (int32_t j0 = 0; j0 < ng2; j0 += NB_WARP) {
         const int32_t jj = j0 + lane;
         float4 v = pad;
-        if (jj < ng) {
-            const float4 h = p_hi[f + jj], lo = p_lo[f + jj];
+        if (jj < ng2) {
+            const float4 h = p_hi[f2 + jj], lo = p_lo[f2 + jj];
             v = make_float4(nb_rel(h.x, lo.x, bc.x), nb_rel(h.y, lo.y, bc.y),
                             nb_rel(h.z, lo.z, bc.z), h.w);
         }
@@ -137,13 +153,15 @@ __device__ __forceinline__ void force_item(
     for (int r = 0; r < R; r++) pair_fold<MODE>(A[r], P[r]);
     if constexpr (S > 1) {
 #pragma unroll
-        for (int o = W; o < NB_WARP; o <<= 1) stream_sum<MODE>(A[0], o);
+        for (int o = W; o < NB_WARP; o <<= 1)
+#pragma unroll
+            for (int r = 0; r < R; r++) stream_sum<MODE>(A[r], o);
         if (stream != 0) return;
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        if (!ok[r]) continue;
-        const int64_t o = perm[slot[r]];
+        if (kk[r] >= ng2) continue;
+        const int64_t o = perm[f2 + kk[r]];
         float ax, ay, az, ph;
         if (MODE == MODE_F64) {
             ax = (float)A[r].dx; ay = (float)A[r].dy; az = (float)A[r].dz; ph = (float)A[r].dp;
@@ -158,6 +176,24 @@ __device__ __forceinline__ void force_item(
         acc[3 * o + 2] = az;
         if (pot) pot[o] = ph;
     }
+}
+
+// one item in a function of its own: each item shape gets its own register
+// allocation instead of sharing the largest one's (the call costs a few
+// instructions per item, against thousands per list)
+template <int MODE, bool GUARD, int R, int S, int TILE, bool QUAD>
+__device__ __noinline__ void force_item_call(
+    int32_t g, int32_t i0, float4 *tile, const int32_t *__restrict__ gfirst,
+    const int32_t *__restrict__ gcount, const int32_t *__restrict__ glen,
+    const float4 *__restrict__ gbox, const float4 *__restrict__ p_hi,
+    const float4 *__restrict__ p_lo, const int32_t *__restrict__ perm,
+    const float4 *__restrict__ list_xm, const float4 *__restrict__ list_q, int64_t cap,
+    int64_t alloc, int64_t n, float eps2, float *__restrict__ acc, float *__restrict__ pot,
+    long long *__restrict__ cnt, unsigned *__restrict__ err)
+{
+    force_item<MODE, GUARD, R, S, TILE, QUAD>(g, i0, tile, gfirst, gcount, glen, gbox, p_hi, p_lo,
+                                              perm, list_xm, list_q, cap, alloc, n, eps2, acc,
+                                              pot, cnt, err);
 }
 
 // cost bucket of an item, 0 = costliest: 4 x log2 of (list + members) x
@@ -276,26 +312,27 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
             continue;
         }
 #define NB_FORCE_ITEM_AT(R, S, I0)                                                            \
-    force_item<MODE, GUARD, R, S, TILE, QUAD>(g, I0, tiles[w], gfirst, gcount, glen, gbox, p_hi,  \
+    force_item_call<MODE, GUARD, R, S, TILE, QUAD>(g, I0, tiles[w], gfirst, gcount, glen, gbox,   \
+                                                   p_hi,                                          \
                                               p_lo, perm, list_xm, list_q, cap, alloc, n, eps2,   \
                                               acc, pot, cnt, err)
 #define NB_FORCE_ITEM(R, S) NB_FORCE_ITEM_AT(R, S, i0)
-        if (word & ITEM_R2) {
-            if constexpr (QUAD) {   // one target per lane: two passes over the list
+        if constexpr (QUAD) {   // one target per lane: a 64-target item in two passes
+            if (word & ITEM_R2) {
                 NB_FORCE_ITEM_AT(1, 1, i0);
                 NB_FORCE_ITEM_AT(1, 1, i0 + NB_WARP);
             } else {
-                NB_FORCE_ITEM(2, 1);
+                switch ((word >> ITEM_LS_SHIFT) & 7) {
+                case 0: NB_FORCE_ITEM(1, 1); break;
+                case 1: NB_FORCE_ITEM(1, 2); break;
+                case 2: NB_FORCE_ITEM(1, 4); break;
+                case 3: NB_FORCE_ITEM(1, 8); break;
+                case 4: NB_FORCE_ITEM(1, 16); break;
+                default: NB_FORCE_ITEM(1, 32); break;
+                }
             }
         } else {
-            switch ((word >> ITEM_LS_SHIFT) & 7) {
-            case 0: NB_FORCE_ITEM(1, 1); break;
-            case 1: NB_FORCE_ITEM(1, 2); break;
-            case 2: NB_FORCE_ITEM(1, 4); break;
-            case 3: NB_FORCE_ITEM(1, 8); break;
-            case 4: NB_FORCE_ITEM(1, 16); break;
-            default: NB_FORCE_ITEM(1, 32); break;
-            }
+            NB_ITEM_SHAPES(word, NB_FORCE_ITEM);
         }
 #undef NB_FORCE_ITEM
 #undef NB_FORCE_ITEM_AT
@@ -480,18 +517,7 @@ k_walk_force(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ pid2b
     force_item<MODE, GUARD, R, S, F_TILE, false, true>(g, i0, tile, gfirst, gcount, glen, gbox,   \
                                                        p_hi, p_lo, perm, list_xm, nullptr, cap,  \
                                                        alloc, n, eps2, acc, pot, cnt, err)
-        if (word & ITEM_R2) {
-            NB_OV_ITEM(2, 1);
-        } else {
-            switch ((word >> ITEM_LS_SHIFT) & 7) {
-            case 0: NB_OV_ITEM(1, 1); break;
-            case 1: NB_OV_ITEM(1, 2); break;
-            case 2: NB_OV_ITEM(1, 4); break;
-            case 3: NB_OV_ITEM(1, 8); break;
-            case 4: NB_OV_ITEM(1, 16); break;
-            default: NB_OV_ITEM(1, 32); break;
-            }
-        }
+        NB_ITEM_SHAPES(word, NB_OV_ITEM);
 #undef NB_OV_ITEM
         __syncwarp();
     }

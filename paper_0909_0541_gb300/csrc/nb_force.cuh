@@ -23,6 +23,30 @@ static constexpr int F_MASK_UNROLL = 8;   // unroll of the masked phase
 
 enum { MODE_FP32 = 0, MODE_COMP = 1, MODE_F64 = 2 };
 
+// The shape an item is summed in, CALL(R, S): R targets per lane, S source
+// streams (the warp as S rows of 32/S lanes, each row over 1/S of every
+// tile).  A 64-target item runs as (2, 1).  A tail item of 32/2^ls targets
+// (ls = 0..3: 32, 16, 8, 4 targets) runs as (2, 2^(ls+1)): two targets per
+// lane, so each staged record pair feeds two interactions per lane, as in a
+// full item.  Tails of two and one targets run as (1, 16) and (1, 32): with
+// two targets per lane their streams would hold a single record per tile and
+// lose the paired arithmetic.
+#define NB_ITEM_SHAPES(word, CALL)                                                           \
+    do {                                                                                      \
+        if ((word) & ITEM_R2) {                                                               \
+            CALL(2, 1);                                                                       \
+        } else {                                                                              \
+            switch (((word) >> ITEM_LS_SHIFT) & 7) {                                          \
+            case 0: CALL(2, 2); break;                                                        \
+            case 1: CALL(2, 4); break;                                                        \
+            case 2: CALL(2, 8); break;                                                        \
+            case 3: CALL(2, 16); break;                                                       \
+            case 4: CALL(1, 16); break;                                                       \
+            default: CALL(1, 32); break;                                                      \
+            }                                                                                 \
+        }                                                                                     \
+    } while (0)
+
 __device__ __forceinline__ float mufu_rsqrt(float x)
 {
     float r;

@@ -186,7 +186,9 @@ __device__ __forceinline__ void fused_item(
     }
     if constexpr (S > 1) {
 #pragma unroll
-        for (int o = W; o < NB_WARP; o <<= 1) stream_sum<MODE>(A[0], o);
+        for (int o = W; o < NB_WARP; o <<= 1)
+#pragma unroll
+            for (int r = 0; r < R; r++) stream_sum<MODE>(A[r], o);
         if (stream != 0) return;
     }
 #pragma unroll
@@ -252,18 +254,7 @@ k_walk_force(const int32_t *__restrict__ items, const nb_wrec *__restrict__ wrec
     fused_item<MODE, GUARD, R, S>(g, i0, bufs[w], sq[w], sq[w] + WQ_SMEM, qa, qb, wq_cap, wrec, \
                                   pid2bfs, gnode, gfirst, gcount, gbox, p_hi, p_lo, perm, total,  \
                                   n, eps2, sys_sorted, sys_root, acc, pot, cnt, err, bad, fc)
-        if (word & ITEM_R2) {
-            NB_FUSED_ITEM(2, 1);
-        } else {
-            switch ((word >> ITEM_LS_SHIFT) & 7) {
-            case 0: NB_FUSED_ITEM(1, 1); break;
-            case 1: NB_FUSED_ITEM(1, 2); break;
-            case 2: NB_FUSED_ITEM(1, 4); break;
-            case 3: NB_FUSED_ITEM(1, 8); break;
-            case 4: NB_FUSED_ITEM(1, 16); break;
-            default: NB_FUSED_ITEM(1, 32); break;
-            }
-        }
+        NB_ITEM_SHAPES(word, NB_FUSED_ITEM);
 #undef NB_FUSED_ITEM
         if (bad) break;
     }
