@@ -146,7 +146,14 @@ __device__ __forceinline__ void force_item(
         }
         put_rec(tile, lane, v);
         __syncwarp();
-        tile_pass<MODE, GUARD, true, R, W>(tile, stream * W, j0 + stream * W, t, kk, eps2, A, P);
+        // only a tile that holds one of this item's targets needs the j == i
+        // mask; elsewhere the mask changes nothing and the plain pass runs
+        if (j0 < i0 + R * W && j0 + NB_WARP > i0)
+            tile_pass<MODE, GUARD, true, R, W>(tile, stream * W, j0 + stream * W, t, kk, eps2, A,
+                                               P);
+        else
+            tile_pass<MODE, GUARD, false, R, W>(tile, stream * W, j0 + stream * W, t, kk, eps2,
+                                                A, P);
         __syncwarp();
     }
 #pragma unroll
