@@ -66,12 +66,13 @@ __device__ __forceinline__ NodeRec load_node(int32_t i, int32_t na, const int32_
 //   box centre to accepted cells' centres of mass / L + 1e-7);  11 depth / 22
 // the opening test of one chunk of 32 frontier nodes (one per lane): emit
 // particles and accepted cells to the list (ballot + popc), queue the
-// children of opened cells (warp prefix sum)
+// children of opened cells (warp prefix sum); list_id, list_xm and list_q
+// point at the group's own list slot
 template <bool PROBE, bool QUAD>
 __device__ __forceinline__ void visit_node(
     const NodeRec r, int32_t gb, int32_t gpid, const float4 &blo, const float4 &bhi,
     const float4 &bc, float invth, int32_t total, long long *cnt, unsigned *err, int lane,
-    unsigned lt, int64_t room, int64_t base, int32_t *__restrict__ list_id,
+    unsigned lt, int64_t room, int32_t *__restrict__ list_id,
     float4 *__restrict__ list_xm, const double *__restrict__ b_q, float4 *__restrict__ list_q,
     int32_t *qout_s, int32_t *qout, int64_t wq_cap,
     int32_t &len, int32_t &ncell,
@@ -115,8 +116,8 @@ __device__ __forceinline__ void visit_node(
                             : cell_emit ? len + __popc(cm & lt)
                                         : len + __popc(cm) + __popc(em & ~cm & lt);
         if (pos < room) {
-            list_id[base + pos] = r.wb.x;
-            list_xm[base + pos] = make_float4(nb_rel(r.a.x, r.d.x, bc.x), nb_rel(r.a.y, r.d.y, bc.y),
+            list_id[pos] = r.wb.x;
+            list_xm[pos] = make_float4(nb_rel(r.a.x, r.d.x, bc.x), nb_rel(r.a.y, r.d.y, bc.y),
                                               nb_rel(r.a.z, r.d.z, bc.z), r.a.w);
             if constexpr (QUAD) {   // the cell's Q in FP32 (zero for a particle)
                 float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -125,8 +126,8 @@ __device__ __forceinline__ void visit_node(
 #pragma unroll
                     for (int k = 0; k < 6; k++) q[k] = __double2float_rn(qb[k]);
                 }
-                list_q[2 * (base + pos)] = make_float4(q[0], q[1], q[2], q[3]);
-                list_q[2 * (base + pos) + 1] = make_float4(q[4], q[5], 0.0f, 0.0f);
+                list_q[2 * pos] = make_float4(q[0], q[1], q[2], q[3]);
+                list_q[2 * pos + 1] = make_float4(q[4], q[5], 0.0f, 0.0f);
             }
         }
     }
@@ -135,7 +136,8 @@ __device__ __forceinline__ void visit_node(
     // exclusive prefix sum of the children over the lanes: with at most 15
     // children per lane (every cell but a level-21 bucket), from one ballot
     // per bit of the count; otherwise by a shuffle scan
-    int32_t excl = 0, tot = 0;
+    int32_t excl = 0;
+    const int32_t tot = __reduce_add_sync(FULL, nch);
     if (__any_sync(FULL, nch > 15)) {
         int32_t incl = nch;
 #pragma unroll
@@ -144,14 +146,10 @@ __device__ __forceinline__ void visit_node(
             if (lane >= o) incl += y;
         }
         excl = incl - nch;
-        tot = __shfl_sync(FULL, incl, 31);
     } else {
 #pragma unroll
-        for (int b = 0; b < 4; b++) {
-            const unsigned m = __ballot_sync(FULL, (nch >> b) & 1);
-            excl += __popc(m & lt) << b;
-            tot += __popc(m) << b;
-        }
+        for (int b = 0; b < 4; b++)
+            excl += __popc(__ballot_sync(FULL, (nch >> b) & 1) & lt) << b;
     }
     const int32_t start = nb + excl;
     if (open) {
@@ -199,6 +197,10 @@ __device__ __forceinline__ void walk_one(
                            ? pid2bfs[gpid] : -1;
     const int64_t base = (int64_t)g * cap;
     const int64_t room = alloc - base < cap ? (alloc - base > 0 ? alloc - base : 0) : cap;
+    // the group's list slot (no lists in the probe walk)
+    int32_t *const lid = PROBE ? nullptr : list_id + base;
+    float4 *const lxm = PROBE ? nullptr : list_xm + base;
+    float4 *const lq = QUAD ? list_q + 2 * base : nullptr;
     int32_t len = 0, ncell = 0;
     float dmin = INFINITY, dmax = 0.0f, dsum = 0.0f;
     int32_t *qin = qa, *qout = qb, *qin_s = qa_s, *qout_s = qb_s;
@@ -216,7 +218,7 @@ __device__ __forceinline__ void walk_one(
             const NodeRec r = load_node<PROBE>(i0 + lane, na, qin_s, qin, wrec,
                                                total, cnt, err);
             visit_node<PROBE, QUAD>(r, gb, gpid, blo, bhi, bc, invth, total, cnt, err, lane, lt, room,
-                              base, list_id, list_xm, b_q, list_q, qout_s, qout, wq_cap, len,
+                              lid, lxm, b_q, lq, qout_s, qout, wq_cap, len,
                               ncell, nb, dmin, dmax, dsum);
         }
         if (nb > qmax) qmax = nb;
