@@ -1164,9 +1164,12 @@ __device__ __forceinline__ int32_t item_count(int32_t m, int iblock)
 }
 
 // group box over the members' FP32 positions, its FP32 centre, FP32
-// 1/theta, and the number of force work items of the group; one warp per
-// group, the members strided over the lanes and the box reduced by shuffles
-// (min and max are exact, so the order does not matter)
+// 1/theta, and the number of force work items of the group.  A warp takes 32
+// consecutive groups: for each in turn the members are strided over the lanes
+// and the box is reduced by shuffles (min and max are exact, so the order
+// does not matter), and lane k keeps group k's box.  The FP64 centre and
+// 1/theta then run once for all 32 groups, one per lane: an FP64 instruction
+// costs GB300's FP64 pipe as much for one active lane as for 32.
 __global__ void __launch_bounds__(256)
 k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gcount,
               const float4 *__restrict__ p_hi, long long *__restrict__ cnt,
@@ -1177,41 +1180,56 @@ k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gc
     const int lane = threadIdx.x & 31;
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     const int32_t nw = gridDim.x * (blockDim.x >> 5);
-    for (int32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < G; g += nw) {
-        const int32_t f = gfirst[g], m = gcount[g];
-        if (!(f >= 0 && m >= 1 && (int64_t)f + m <= n)) {
-            if (lane == 0) {
-                nb_bad(cnt, err, SITE_GROUPS, g);
-                item_cnt[g] = 0;
+    for (int32_t g0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * NB_WARP; g0 < G;
+         g0 += nw * NB_WARP) {
+        const int32_t gl = g0 + lane;   // this lane's group
+        int32_t fl = 0, ml = 0;
+        if (gl < G) {
+            fl = gfirst[gl];
+            ml = gcount[gl];
+        }
+        const bool okl = gl < G && fl >= 0 && ml >= 1 && (int64_t)fl + ml <= n;
+        const unsigned okm = __ballot_sync(FULL, okl);
+        float blx = 0.f, bly = 0.f, blz = 0.f, bhx = 0.f, bhy = 0.f, bhz = 0.f;
+        for (int k = 0; k < NB_WARP && g0 + k < G; k++) {
+            if (!((okm >> k) & 1u)) continue;
+            const int32_t f = __shfl_sync(FULL, fl, k), m = __shfl_sync(FULL, ml, k);
+            float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+            float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+            for (int32_t j = lane; j < m; j += NB_WARP) {
+                const float4 p = p_hi[f + j];
+                lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
+                hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lx = fminf(lx, __shfl_xor_sync(FULL, lx, o));
+                ly = fminf(ly, __shfl_xor_sync(FULL, ly, o));
+                lz = fminf(lz, __shfl_xor_sync(FULL, lz, o));
+                hx = fmaxf(hx, __shfl_xor_sync(FULL, hx, o));
+                hy = fmaxf(hy, __shfl_xor_sync(FULL, hy, o));
+                hz = fmaxf(hz, __shfl_xor_sync(FULL, hz, o));
+            }
+            if (lane == k) {
+                blx = lx; bly = ly; blz = lz;
+                bhx = hx; bhy = hy; bhz = hz;
+            }
+        }
+        if (gl >= G) continue;
+        if (!okl) {
+            nb_bad(cnt, err, SITE_GROUPS, gl);
+            item_cnt[gl] = 0;
             continue;
         }
-        float lx = INFINITY, ly = INFINITY, lz = INFINITY;
-        float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
-        for (int32_t k = lane; k < m; k += NB_WARP) {
-            const float4 p = p_hi[f + k];
-            lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
-            hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lx = fminf(lx, __shfl_xor_sync(FULL, lx, o));
-            ly = fminf(ly, __shfl_xor_sync(FULL, ly, o));
-            lz = fminf(lz, __shfl_xor_sync(FULL, lz, o));
-            hx = fmaxf(hx, __shfl_xor_sync(FULL, hx, o));
-            hy = fmaxf(hy, __shfl_xor_sync(FULL, hy, o));
-            hz = fmaxf(hz, __shfl_xor_sync(FULL, hz, o));
-        }
-        if (lane != 0) continue;
-        const float th = theta_g ? theta_g[g] : theta;
+        const float th = theta_g ? theta_g[gl] : theta;
         const float invth = __double2float_rn(__ddiv_rn(1.0, (double)th));
-        const float cx = __double2float_rn(__dmul_rn(0.5, __dadd_rn((double)lx, (double)hx)));
-        const float cy = __double2float_rn(__dmul_rn(0.5, __dadd_rn((double)ly, (double)hy)));
-        const float cz = __double2float_rn(__dmul_rn(0.5, __dadd_rn((double)lz, (double)hz)));
-        gbox[3 * (int64_t)g] = make_float4(lx, ly, lz, 0.0f);
-        gbox[3 * (int64_t)g + 1] = make_float4(hx, hy, hz, 0.0f);
-        gbox[3 * (int64_t)g + 2] = make_float4(cx, cy, cz, invth);
-        item_cnt[g] = item_count(m, iblock);
+        const float cx = __double2float_rn(__dmul_rn(0.5, __dadd_rn((double)blx, (double)bhx)));
+        const float cy = __double2float_rn(__dmul_rn(0.5, __dadd_rn((double)bly, (double)bhy)));
+        const float cz = __double2float_rn(__dmul_rn(0.5, __dadd_rn((double)blz, (double)bhz)));
+        gbox[3 * (int64_t)gl] = make_float4(blx, bly, blz, 0.0f);
+        gbox[3 * (int64_t)gl + 1] = make_float4(bhx, bhy, bhz, 0.0f);
+        gbox[3 * (int64_t)gl + 2] = make_float4(cx, cy, cz, invth);
+        item_cnt[gl] = item_count(ml, iblock);
     }
 }
 

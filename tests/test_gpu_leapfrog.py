@@ -183,3 +183,46 @@ def test_graph_dropped_when_list_storage_is_reallocated():
         ctx.graph_launch()
         ctx.sync_status()
         ctx.close()
+
+
+@pytest.mark.parametrize("dt,offset", [(1.0 / 128, 0), (0.01, 0), (1.0 / 128, 1)])
+def test_kick_and_drift_are_the_fp64_formulas(dt, offset):
+    """The kick v + fl64(a) (dt/2) and the drift x + v dt, each operation
+    rounded on its own, bit for bit: 16-byte aligned buffers (four components
+    per thread and round) and buffers one double off that alignment (one
+    component at a time); zero, negative-zero and subnormal velocities
+    included."""
+    import paper_0909_0541_gb300 as nb
+    ps = nbsynth.plummer(6000, 41)
+    eps, theta, n_crit = 1.0 / 64, 0.7, 64
+    v0 = ps.vel.copy()
+    v0[:7, 0] = 0.0
+    v0[7:14, 1] = -0.0
+    v0[14:21, 2] = 3e-310
+    v0[21:28, 0] = -2.5e-308
+    dev = torch.device("cuda")
+
+    def placed(a):   # a device copy whose data pointer is `offset` doubles past 16-byte alignment
+        flat = torch.empty(a.size + offset, dtype=torch.float64, device=dev)
+        view = flat[offset:].view(a.shape)
+        view.copy_(torch.from_numpy(a))
+        assert (view.data_ptr() % 16 == 0) == (offset == 0)
+        return view
+
+    pos, vel = placed(ps.pos), placed(v0)
+    mass = torch.from_numpy(ps.mass).to(dev)
+    ctx = nb.NBody(ps.n, eps=eps, theta=theta, n_crit=n_crit)
+    a0 = torch.empty((ps.n, 3), dtype=torch.float32, device=dev)
+    ctx.build_tree(pos, mass)
+    ctx.walk_groups(theta, n_crit)
+    ctx.forces(eps, a0)
+    ctx.leapfrog_step(pos, vel, mass, dt)
+    a1 = torch.empty_like(a0)
+    ctx.leapfrog_acc(a1)
+    h = 0.5 * dt
+    vh = v0 + a0.cpu().numpy().astype(np.float64) * h
+    x1 = ps.pos + vh * dt
+    v1 = vh + a1.cpu().numpy().astype(np.float64) * h
+    assert np.array_equal(pos.cpu().numpy(), x1)
+    assert np.array_equal(vel.cpu().numpy(), v1)
+    ctx.close()
