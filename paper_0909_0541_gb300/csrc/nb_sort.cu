@@ -73,60 +73,62 @@ k_scan_reduce(const int32_t *__restrict__ in, int64_t n_max,
 }
 
 // one block: exclusive scan of the tile sums; writes out[n] and the total
-__global__ void __launch_bounds__(1024)
-k_scan_bsum(int32_t *__restrict__ bsum, int nb, int32_t *__restrict__ out,
-            int64_t n_max, const long long *__restrict__ n_dev,
-            long long *__restrict__ total_dev)
-{
-    __shared__ int32_t part[1024];
-    const int t = threadIdx.x;
-    const int per = (nb + 1023) / 1024;
-    const int lo = t * per, hi = min(nb, lo + per);
-    int32_t s = 0;
-    for (int i = lo; i < hi; i++) s += bsum[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        int32_t y = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += y;
-        __syncthreads();
-    }
-    int32_t run = t > 0 ? part[t - 1] : 0;
-    for (int i = lo; i < hi; i++) {
-        const int32_t v = bsum[i];
-        bsum[i] = run;
-        run += v;
-    }
-    if (t == 1023) {
-        const int64_t n = eff_n(n_max, n_dev);
-        out[n] = part[1023];
-        if (total_dev) *total_dev = part[1023];
-    }
-}
-
+// Second pass: each block adds up the totals of the tiles before its own
+// (at most a few thousand, read from L2 by the whole block), then scans its
+// tile.  Each thread holds 8 consecutive elements, loaded and stored as two
+// 16-byte vectors when the arrays allow it (VEC).  The block of the last
+// non-empty tile (block 0 when n is 0) writes out[n] and the total.
+template <bool VEC>
 __global__ void __launch_bounds__(SCAN_T)
 k_scan_apply(const int32_t *__restrict__ in, int32_t *__restrict__ out,
              int64_t n_max, const long long *__restrict__ n_dev,
-             const int32_t *__restrict__ bsum)
+             const int32_t *__restrict__ bsum, long long *__restrict__ total_dev)
 {
+    static_assert(SCAN_I == 8, "two 16-byte vectors per thread");
     const int64_t n = eff_n(n_max, n_dev);
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    if (base >= n) return;
+    const int64_t last = n > 0 ? (n - 1) / SCAN_TILE : 0;
+    if ((int64_t)blockIdx.x > last) return;
+    int32_t before = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += SCAN_T) before += bsum[i];
+    {
+        int32_t all;
+        block_excl_scan(before, &all);
+        before = all;
+    }
+    const int64_t i0 = base + (int64_t)threadIdx.x * SCAN_I;
     int32_t v[SCAN_I];
+    if (VEC && i0 + SCAN_I <= n) {
+        const int4 a = reinterpret_cast<const int4 *>(in + i0)[0];
+        const int4 b = reinterpret_cast<const int4 *>(in + i0)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_I; k++) v[k] = i0 + k < n ? in[i0 + k] : 0;
+    }
     int32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_I; k++) {
-        const int64_t i = base + threadIdx.x * SCAN_I + k;
-        v[k] = i < n ? in[i] : 0;
-        s += v[k];
-    }
-    int32_t run = block_excl_scan(s, nullptr) + bsum[blockIdx.x];
+    for (int k = 0; k < SCAN_I; k++) s += v[k];
+    int32_t tile_total;
+    int32_t run = block_excl_scan(s, &tile_total) + before;
+    int32_t o[SCAN_I];
 #pragma unroll
     for (int k = 0; k < SCAN_I; k++) {
-        const int64_t i = base + threadIdx.x * SCAN_I + k;
-        if (i < n) out[i] = run;
+        o[k] = run;
         run += v[k];
+    }
+    if (VEC && i0 + SCAN_I <= n) {
+        reinterpret_cast<int4 *>(out + i0)[0] = make_int4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<int4 *>(out + i0)[1] = make_int4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_I; k++)
+            if (i0 + k < n) out[i0 + k] = o[k];
+    }
+    if ((int64_t)blockIdx.x == last && threadIdx.x == 0) {
+        out[n] = before + tile_total;
+        if (total_dev) *total_dev = before + tile_total;
     }
 }
 
@@ -140,10 +142,12 @@ void nb_exclusive_scan(nb_ctx *c, const int32_t *in, int32_t *out, int64_t n_max
     const int g = nb > 0 ? nb : 1;
     k_scan_reduce<<<g, SCAN_T, 0, c->stream>>>(in, n_max, n_dev, c->scan_bsum);
     nb_launched(c, "k_scan_reduce");
-    k_scan_bsum<<<1, 1024, 0, c->stream>>>(c->scan_bsum, g, out, n_max, n_dev,
-                                           total_dev);
-    nb_launched(c, "k_scan_bsum");
-    k_scan_apply<<<g, SCAN_T, 0, c->stream>>>(in, out, n_max, n_dev, c->scan_bsum);
+    if (((uintptr_t)in & 15u) == 0 && ((uintptr_t)out & 15u) == 0)
+        k_scan_apply<true><<<g, SCAN_T, 0, c->stream>>>(in, out, n_max, n_dev, c->scan_bsum,
+                                                        total_dev);
+    else
+        k_scan_apply<false><<<g, SCAN_T, 0, c->stream>>>(in, out, n_max, n_dev, c->scan_bsum,
+                                                         total_dev);
     nb_launched(c, "k_scan_apply");
 }
 
@@ -448,8 +452,10 @@ void nb_exclusive_scan_raw(const int32_t *in, int32_t *out, int64_t n_max, int32
     const int nb = (int)((n_max + SCAN_TILE - 1) / SCAN_TILE);
     const int g = nb > 0 ? nb : 1;
     k_scan_reduce<<<g, SCAN_T, 0, s>>>(in, n_max, nullptr, bsum);
-    k_scan_bsum<<<1, 1024, 0, s>>>(bsum, g, out, n_max, nullptr, nullptr);
-    k_scan_apply<<<g, SCAN_T, 0, s>>>(in, out, n_max, nullptr, bsum);
+    if (((uintptr_t)in & 15u) == 0 && ((uintptr_t)out & 15u) == 0)
+        k_scan_apply<true><<<g, SCAN_T, 0, s>>>(in, out, n_max, nullptr, bsum, nullptr);
+    else
+        k_scan_apply<false><<<g, SCAN_T, 0, s>>>(in, out, n_max, nullptr, bsum, nullptr);
 }
 
 // keys/idx hold the input and, after the 8 passes, the sorted output;
