@@ -293,7 +293,8 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
         float *__restrict__ acc, float *__restrict__ pot, unsigned *__restrict__ err,
         int64_t max_items)
 {
-    __shared__ float4 tiles[BT / NB_WARP][QUAD ? TILE * 5 / 2 : TILE];
+    __shared__ float4 tiles[BT / NB_WARP][QUAD ? TILE * 5 / 2
+                                               : (TILE > F_TILE_STREAMS ? TILE : F_TILE_STREAMS)];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t nitems = (int32_t)cnt[CNT_ITEMS];
@@ -319,7 +320,8 @@ k_force(const int32_t *__restrict__ items, const int32_t *__restrict__ order,
             continue;
         }
 #define NB_FORCE_ITEM_AT(R, S, I0)                                                            \
-    force_item_call<MODE, GUARD, R, S, TILE, QUAD>(g, I0, tiles[w], gfirst, gcount, glen, gbox,   \
+    force_item_call<MODE, GUARD, R, S, QUAD ? TILE : item_tile(S, TILE), QUAD>(                   \
+        g, I0, tiles[w], gfirst, gcount, glen, gbox,                                              \
                                                    p_hi,                                          \
                                               p_lo, perm, list_xm, list_q, cap, alloc, n, eps2,   \
                                               acc, pot, cnt, err)
@@ -521,7 +523,8 @@ k_walk_force(const nb_wrec *__restrict__ wrec, const int32_t *__restrict__ pid2b
         const int32_t g = gt, word = items[2 * task + 1];
         const int32_t i0 = word & ITEM_MEMBER_MASK;
 #define NB_OV_ITEM(R, S)                                                                      \
-    force_item<MODE, GUARD, R, S, F_TILE, false, true>(g, i0, tile, gfirst, gcount, glen, gbox,   \
+    force_item<MODE, GUARD, R, S, item_tile(S, F_TILE), false, true>(                             \
+        g, i0, tile, gfirst, gcount, glen, gbox,                                                  \
                                                        p_hi, p_lo, perm, list_xm, nullptr, cap,  \
                                                        alloc, n, eps2, acc, pot, cnt, err)
         NB_ITEM_SHAPES(word, NB_OV_ITEM);

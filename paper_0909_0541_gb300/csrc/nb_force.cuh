@@ -15,6 +15,15 @@
 #include "nb_internal.cuh"
 
 #define F_TILE 32   // list records staged per tile (a multiple of 32)
+// Items of more than one source stream stage at least F_TILE_STREAMS list
+// records per tile, so that each stream still sums several record pairs per
+// tile (the list force kernel, the overlapped kernel and the fused pass all
+// use this rule, so their sums run in the same order)
+#define F_TILE_STREAMS 64
+__host__ __device__ constexpr int item_tile(int S, int tile)
+{
+    return S > 1 && tile < F_TILE_STREAMS ? F_TILE_STREAMS : tile;
+}
 static constexpr int F_MASK_UNROLL = 8;   // unroll of the masked phase
 // item word: first member | log2(source streams) << 27 | two-targets-per-lane flag
 #define ITEM_R2 (1 << 30)

@@ -8,11 +8,12 @@
 // as k_walk does.  Instead of writing the accepted sources to the group's
 // list, the warp appends each one's FP32 record (position relative to the
 // group centre, mass) to a buffer of FW_BUF records in shared memory; every
-// time 32 records are buffered, they are summed against the item's targets
-// with the same tile pass as the list force kernel.  The remainder is padded
-// like the list's last tile, then the group's own members are summed.  The
-// records reach the tile pass in list order and in the same 32-record tiles,
-// so the accelerations equal the list path's bit for bit.
+// time a tile's worth is buffered (32 records, or 64 for an item of several
+// source streams), it is summed against the item's targets with the same
+// tile pass as the list force kernel.  The remainder is padded like the
+// list's last tile, then the group's own members are summed.  The records
+// reach the tile pass in list order and in the same tiles, so the
+// accelerations equal the list path's bit for bit.
 //
 // An item of a group with several items walks the group again: the walk is
 // repeated per item, and the interaction lists never touch HBM.
@@ -21,7 +22,9 @@
 
 #define FW_T 128
 #define FW_WARPS (FW_T / NB_WARP)
-#define FW_BUF 64   // buffered records per warp (32 are summed whenever 32 are ready)
+// buffered records per warp: a tile of item_tile(S, 32) records is summed
+// whenever one is ready, and a chunk of the walk adds at most 32
+#define FW_BUF (F_TILE_STREAMS + NB_WARP)
 // unroll of the tile pass inside the walk loop: the walk's live state leaves
 // fewer registers than the list force kernel has
 static constexpr int FW_UNROLL = 4;
@@ -45,6 +48,8 @@ __device__ __forceinline__ void fused_item(
 {
     const unsigned FULL = 0xffffffffu;
     constexpr int W = NB_WARP / S;
+    constexpr int FT = item_tile(S, NB_WARP);   // records per summed tile, as the list path
+    constexpr int FK = FT / NB_WARP;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int row = lane % W, stream = lane / W;
@@ -129,13 +134,13 @@ __device__ __forceinline__ void fused_item(
                 }
             nb += __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            if (nbuf >= NB_WARP) {   // one full tile: sum it, keep the rest
-                tile_pass<MODE, GUARD, false, R, W, FW_UNROLL>(buf, stream * W, 0, t, kk, eps2, A,
-                                                               P);
+            if (nbuf >= FT) {   // one full tile: sum it, keep the rest
+                tile_pass<MODE, GUARD, false, R, W * FK, FW_UNROLL>(buf, stream * W * FK, 0, t, kk,
+                                                                    eps2, A, P);
                 __syncwarp();
-                // move the rest down by whole record pairs (NB_WARP is even)
-                if (lane < ((nbuf - NB_WARP + 1) & ~1)) buf[lane] = buf[NB_WARP + lane];
-                nbuf -= NB_WARP;
+                // move the rest (< 32 records) down by whole record pairs (FT is even)
+                if (lane < ((nbuf - FT + 1) & ~1)) buf[lane] = buf[FT + lane];
+                nbuf -= FT;
                 __syncwarp();
             }
         }
@@ -154,9 +159,12 @@ __device__ __forceinline__ void fused_item(
         }
     }
     if (nbuf > 0) {   // the last, padded tile of the list
-        if (lane >= nbuf) put_rec(buf, lane, pad);
+#pragma unroll
+        for (int k = 0; k < FK; k++)
+            if (k * NB_WARP + lane >= nbuf) put_rec(buf, k * NB_WARP + lane, pad);
         __syncwarp();
-        tile_pass<MODE, GUARD, false, R, W, FW_UNROLL>(buf, stream * W, 0, t, kk, eps2, A, P);
+        tile_pass<MODE, GUARD, false, R, W * FK, FW_UNROLL>(buf, stream * W * FK, 0, t, kk, eps2,
+                                                            A, P);
         __syncwarp();
     }
     // (2) the group's own members, j != i
