@@ -177,16 +177,21 @@ def force_source_hash():
     return h.hexdigest()[:16]
 
 
-def force_traffic_record():
+def force_traffic_record(list_entries=None):
     """DRAM bytes per force-kernel launch from the committed ncu summary,
-    valid only while the kernel source is the one that was profiled."""
+    valid only while the kernel source is the one that was profiled.  Every
+    list entry is read once per work item, so the captured launch's bytes
+    are scaled by this run's list entries over the captured launch's."""
     path = os.path.join(ROOT, "profiles", "k_force_traffic.txt")
     try:
         rec = dict(l.split("=", 1) for l in open(path).read().split() if "=" in l)
         h = force_source_hash()
         if rec.get("source_sha256_16") != h:
             return None
-        return float(rec["bytes_per_launch_scaled"])
+        b = float(rec["bytes_per_launch"])
+        if list_entries and rec.get("list_entries"):
+            b *= float(list_entries) / float(rec["list_entries"])
+        return b
     except Exception:
         return None
 
@@ -512,7 +517,7 @@ def run_ours(args, ws, rank, local):
     peak = sms * 128 * sm_max * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak,
-                "traffic": None if args.fused else force_traffic_record(),
+                "traffic": None if args.fused else force_traffic_record(st1["list_entries"]),
                 "kernel": "k_walk_force (walk included)" if args.fused else "k_force",
                 "ops": "FP32-pipe lane ops (13 per interaction)",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
