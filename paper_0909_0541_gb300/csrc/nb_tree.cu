@@ -138,11 +138,20 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x)
 
 __device__ __forceinline__ uint32_t grid_coord(double x, double corner, double scale)
 {
-    // floor by a round-down conversion (saturating outside int64), then the
-    // clamp to the grid in integers: fewer FP64-pipe instructions than
-    // floor + compares + conversion, same result
-    const long long f = __double2ll_rd(__dmul_rn(__dsub_rn(x, corner), scale));
-    return f < 0 ? 0u : (f > 2097151 ? 2097151u : (uint32_t)f);
+    // v = fl(fl(x - corner) * scale); its floor, clamped to the grid
+    // [0, 2^21 - 1], read off v's bits with integer instructions (GB300's
+    // FP64 pipe is its scarce unit): below 1 (negative numbers and NaNs with
+    // the sign bit included) gives 0, 2^21 or more gives the top cell, and in
+    // between the integer part is the significand shifted by the exponent.
+    // A positive NaN gives 0, as a round-down conversion would.
+    const double v = __dmul_rn(__dsub_rn(x, corner), scale);
+    const long long b = __double_as_longlong(v);
+    if (b < 0x3ff0000000000000ll) return 0u;
+    if (b > 0x7ff0000000000000ll) return 0u;   // NaN
+    const int e = (int)(b >> 52) - 1023;        // v in [2^e, 2^(e+1))
+    if (e >= 21) return 2097151u;
+    const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffull) | (1ull << 52);
+    return (uint32_t)(m >> (52 - e));
 }
 
 // Peano-Hilbert index of a grid point, the order the paper names as better
