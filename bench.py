@@ -247,13 +247,17 @@ def job_rate(units, ms, ws):
     return allreduce_sum(float(units), ws) / (ms_max / 1e3), ms_max
 
 
+L2_BYTES = 126 * 2 ** 20   # GB300 L2 (about 126 MiB)
+
+
 def workload_config(name, n, w, ws):
     """The workload both arms run, with the same keys and values."""
     return {"workload": name, "n": n, "theta": w["theta"], "eps": w["eps"],
             "n_crit": w["n_crit"], "dt": w["dt"],
             "step": "KDK leapfrog: tree build + group walk + force + kicks/drift",
-            "l2": "inputs larger than L2 (positions + velocities 138 MB; interaction lists "
-                  "about 2 GB per step)",
+            "l2": (f"{'inputs' if 48 * n > L2_BYTES else 'interaction lists'} larger than L2 "
+                   f"(positions + velocities {48 * n / 1e6:.0f} MB; the interaction lists, "
+                   f"20 B per entry, are written and read every step)"),
             "parallelism": f"replicas x{ws}" if ws > 1 else "1 replica"}
 
 

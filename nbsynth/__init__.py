@@ -326,6 +326,11 @@ WORKLOADS = {
     "halomix4.19m": dict(gen=lambda: halo_mix(4_194_304, BASE_SEED + 5,
                                               n_halos=3000), eps=5e-4,
                          theta=0.6, n_crit=256, dt=1.0 / 1024),
+    # the same mix at larger N (halo count in proportion), for size sweeps
+    "halomix8m": dict(gen=lambda: halo_mix(8_000_000, BASE_SEED + 7, n_halos=5575),
+                      eps=5e-4, theta=0.6, n_crit=256, dt=1.0 / 1024),
+    "halomix16m": dict(gen=lambda: halo_mix(16_000_000, BASE_SEED + 8, n_halos=11150),
+                       eps=5e-4, theta=0.6, n_crit=256, dt=1.0 / 1024),
 }
 
 
