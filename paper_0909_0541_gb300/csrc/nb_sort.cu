@@ -74,8 +74,10 @@ k_scan_reduce(const int32_t *__restrict__ in, int64_t n_max,
 
 // one block: exclusive scan of the tile sums; writes out[n] and the total
 // Second pass: each block adds up the totals of the tiles before its own
-// (at most a few thousand, read from L2 by the whole block), then scans its
-// tile.  Each thread holds 8 consecutive elements, loaded and stored as two
+// (read from L2 by the whole block), then scans its tile.  The reads grow
+// with the square of the tile count: about 9 MB for the 4.4M nodes of a
+// 2.87M-particle tree, 0.3 GB for a 16M-particle one, well under 1 % of a
+// step either way.  Each thread holds 8 consecutive elements, loaded and stored as two
 // 16-byte vectors when the arrays allow it (VEC).  The block of the last
 // non-empty tile (block 0 when n is 0) writes out[n] and the total.
 template <bool VEC>
