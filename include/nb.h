@@ -276,7 +276,10 @@ int nb_leapfrog_acc(nb_ctx *ctx, float *acc_dev);
 
 /* Capture nsteps leapfrog steps (offsets_dev NULL: one system; else a batch,
  * see nb_build_tree_batched) into a CUDA graph held by the context, and
- * replay it with nb_graph_launch on cfg.stream.  Needs a non-NULL cfg.stream
+ * replay it with nb_graph_launch on cfg.stream.  A replay gives the same bits
+ * as nsteps calls of nb_leapfrog_step; inside it, the second kick of each step
+ * but the last runs in one pass with the next step's first kick and drift, so
+ * the phase timing shows one integrate phase fewer per step boundary.  Needs a non-NULL cfg.stream
  * (the legacy stream cannot be captured) and a previous step of the same n
  * made with sync_checks on, which sizes the list storage; during replay
  * nothing synchronises or allocates, and a list that outgrows its slot is

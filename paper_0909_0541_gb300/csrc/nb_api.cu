@@ -902,9 +902,13 @@ int nb_set_fused(nb_ctx *c, int on)
 }
 
 // pos_out: host buffer that receives the positions as soon as the drift has
-// written them, copied on the copy stream while the step goes on (host steps)
+// written them, copied on the copy stream while the step goes on (host steps).
+// Within a captured sequence of steps, a step may leave its second kick owed
+// (owe_kick) and the next one pay it (kick_owed) in the same pass as its own
+// first kick and drift: the same operations in the same order.
 static int leapfrog(nb_ctx *c, double *pos, double *vel, const float *mass, int64_t n,
-                    double dt, const int64_t *off, int64_t nsys, double *pos_out = nullptr)
+                    double dt, const int64_t *off, int64_t nsys, double *pos_out = nullptr,
+                    bool kick_owed = false, bool owe_kick = false)
 {
     if (!c || n < 0 || n > c->max_n || (n > 0 && (!pos || !vel || !mass)) || !isfinite(dt))
         return NB_ERR_INVALID_ARG;
@@ -917,8 +921,12 @@ static int leapfrog(nb_ctx *c, double *pos, double *vel, const float *mass, int6
     }
     const double h = 0.5 * dt;
     int tk = phase_begin(c);
-    nb_launch_kick(c, vel, c->acc_cache, n, h);
-    nb_launch_drift(c, pos, vel, n, dt);
+    if (kick_owed) {
+        nb_launch_kick_kick_drift(c, pos, vel, c->acc_cache, n, h, dt);
+    } else {
+        nb_launch_kick(c, vel, c->acc_cache, n, h);
+        nb_launch_drift(c, pos, vel, n, dt);
+    }
     phase_end(c, tk, NB_PHASE_INTEGRATE);
     if (pos_out) {
         CK(cudaEventRecord(c->ev_drift, c->stream));
@@ -932,9 +940,11 @@ static int leapfrog(nb_ctx *c, double *pos, double *vel, const float *mass, int6
         c->acc_valid = 0;
         return rc;
     }
-    tk = phase_begin(c);
-    nb_launch_kick(c, vel, c->acc_cache, n, h);
-    phase_end(c, tk, NB_PHASE_INTEGRATE);
+    if (!owe_kick) {
+        tk = phase_begin(c);
+        nb_launch_kick(c, vel, c->acc_cache, n, h);
+        phase_end(c, tk, NB_PHASE_INTEGRATE);
+    }
     return finish(c);
 }
 
@@ -1015,8 +1025,11 @@ int nb_graph_capture_leapfrog(nb_ctx *c, double *pos, double *vel, const float *
         rc = NB_ERR_CUDA;
     } else {
         c->capturing = 1;
+        // the second kick of each step but the last is paid with the next
+        // step's first kick and drift
         for (int k = 0; k < nsteps && rc == NB_OK; k++)
-            rc = leapfrog(c, pos, vel, mass, n, dt, offsets, offsets ? nsys : 1);
+            rc = leapfrog(c, pos, vel, mass, n, dt, offsets, offsets ? nsys : 1, nullptr, k > 0,
+                          k + 1 < nsteps);
         c->capturing = 0;
         if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess && rc == NB_OK) rc = NB_ERR_CUDA;
         if (rc == NB_OK && cudaGraphInstantiate(&c->graph_exec, graph, 0) != cudaSuccess)

@@ -325,6 +325,8 @@ void nb_launch_fused(nb_ctx *c, float eps, float *acc, float *pot, int precision
 void nb_launch_features_tree(nb_ctx *c, float *feat);
 void nb_launch_group_theta(nb_ctx *c, const float *theta_g);
 void nb_launch_drift(nb_ctx *c, double *pos, const double *vel, int64_t n, double dt);
+void nb_launch_kick_kick_drift(nb_ctx *c, double *pos, double *vel, const float *acc,
+                               int64_t n, double h, double dt);
 
 __device__ __forceinline__ long long nb_atomic_add(long long *p, long long v)
 {
