@@ -1173,12 +1173,13 @@ __device__ __forceinline__ int32_t item_count(int32_t m, int iblock)
 }
 
 // group box over the members' FP32 positions, its FP32 centre, FP32
-// 1/theta, and the number of force work items of the group.  A warp takes 32
+// 1/theta, and the number of force work items of the group.  A warp takes GB
 // consecutive groups: for each in turn the members are strided over the lanes
 // and the box is reduced by shuffles (min and max are exact, so the order
 // does not matter), and lane k keeps group k's box.  The FP64 centre and
-// 1/theta then run once for all 32 groups, one per lane: an FP64 instruction
-// costs GB300's FP64 pipe as much for one active lane as for 32.
+// 1/theta then run once for the GB groups, one per lane: an FP64 instruction
+// costs GB300's FP64 pipe as much for one active lane as for 32.  (GB 8 was
+// faster than 16 and 32: more warps share the sequential reductions.)
 __global__ void __launch_bounds__(256)
 k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gcount,
               const float4 *__restrict__ p_hi, long long *__restrict__ cnt,
@@ -1189,9 +1190,10 @@ k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gc
     const int lane = threadIdx.x & 31;
     const int32_t G = (int32_t)cnt[CNT_GROUPS];
     const int32_t nw = gridDim.x * (blockDim.x >> 5);
-    for (int32_t g0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * NB_WARP; g0 < G;
-         g0 += nw * NB_WARP) {
-        const int32_t gl = g0 + lane;   // this lane's group
+    constexpr int GB = 8;
+    for (int32_t g0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * GB; g0 < G;
+         g0 += nw * GB) {
+        const int32_t gl = lane < GB ? g0 + lane : G;   // this lane's group (lanes < GB)
         int32_t fl = 0, ml = 0;
         if (gl < G) {
             fl = gfirst[gl];
@@ -1200,7 +1202,7 @@ k_group_boxes(const int32_t *__restrict__ gfirst, const int32_t *__restrict__ gc
         const bool okl = gl < G && fl >= 0 && ml >= 1 && (int64_t)fl + ml <= n;
         const unsigned okm = __ballot_sync(FULL, okl);
         float blx = 0.f, bly = 0.f, blz = 0.f, bhx = 0.f, bhy = 0.f, bhz = 0.f;
-        for (int k = 0; k < NB_WARP && g0 + k < G; k++) {
+        for (int k = 0; k < GB && g0 + k < G; k++) {
             if (!((okm >> k) & 1u)) continue;
             const int32_t f = __shfl_sync(FULL, fl, k), m = __shfl_sync(FULL, ml, k);
             float lx = INFINITY, ly = INFINITY, lz = INFINITY;
