@@ -25,7 +25,7 @@ __host__ __device__ constexpr int item_tile(int S, int tile)
     return S > 1 && tile < F_TILE_STREAMS ? F_TILE_STREAMS : tile;
 }
 static constexpr int F_MASK_UNROLL = 8;   // unroll of the masked phase
-// item word: first member | log2(source streams) << 27 | two-targets-per-lane flag
+// item word: first member | ls << 27 (an item of 32 >> ls targets) | 64-target flag
 #define ITEM_R2 (1 << 30)
 #define ITEM_LS_SHIFT 27
 #define ITEM_MEMBER_MASK ((1 << 27) - 1)
