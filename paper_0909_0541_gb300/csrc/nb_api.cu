@@ -411,8 +411,10 @@ int nb_create(nb_ctx **out, const nb_config *cfg)
     c->max_n = N;
     c->max_nodes = NN;
     const int64_t rs_tiles = (N + NB_RS_TILE - 1) / NB_RS_TILE;
+    // the single-pass sort may use tiles down to NB_RS_TILE_MIN keys
+    const int64_t rs_tiles_max = (N + NB_RS_TILE_MIN - 1) / NB_RS_TILE_MIN;
     c->sort_hist_len = 256 * rs_tiles + 1;
-    c->rs_status_len = 8 * 256 * rs_tiles + 8 * 256 + 8;
+    c->rs_status_len = 8 * 256 * rs_tiles_max + 8 * 256 + 8;
     c->dtiles = (NN + NB_DS_TILE - 1) / NB_DS_TILE;
     const int64_t dhist_len = NB_DEPTHS * c->dtiles + 1;
     int64_t scan_n = NN + 1 > c->sort_hist_len ? NN + 1 : c->sort_hist_len;

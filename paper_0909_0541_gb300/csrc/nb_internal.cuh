@@ -32,6 +32,7 @@
 #define NB_SPIN_LIMIT (1u << 20)  // polls before a wait for another warp gives up
 #define NB_WARP 32
 #define NB_RS_TILE 4096   // keys per radix-sort tile (sizes the sort's per-tile buffers)
+#define NB_RS_TILE_MIN 3072   // the tile of the context's single-pass sort (nb_sort.cu)
 #define NB_DS_TILE 4096   // nodes per tile of the stable sort by depth
 #define NB_EV_POOL 2048
 #define NB_IBLOCK 64   // targets per force work item (two per lane)

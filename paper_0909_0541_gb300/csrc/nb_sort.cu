@@ -2,11 +2,12 @@
 // (63-bit Morton key, particle index) pairs that puts particles in Morton
 // order (Sec. "Test and Optimization": depth-first leaf order of the tree).
 //
-// Radix sort: 8 passes of 8-bit digits over tiles of NB_RS_TILE keys.  The
-// context's sort is single-pass per digit (Onesweep, see k_rs_scatter): one
-// histogram of all eight digits, then one scatter launch per pass whose
-// tiles find their offsets by a bounded decoupled look-back.  The sort on
-// caller-supplied buffers (no context) keeps three phases per pass, none
+// Radix sort: 8 passes of 8-bit digits.  The context's sort is single-pass
+// per digit (Onesweep, see k_rs_scatter): one histogram of all eight digits,
+// then one scatter launch per pass over tiles of NB_RS_TILE_MIN keys, which
+// find their offsets by a bounded decoupled look-back.  The sort on
+// caller-supplied buffers (no context) keeps three phases per pass over
+// tiles of NB_RS_TILE keys, none
 // of which waits on another block: per-tile digit histograms -> exclusive
 // scan of the digit-major table -> stable scatter.  Stability inside a tile
 // comes from warp-level ranking of 32 consecutive keys at a time with
@@ -213,7 +214,9 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <bool ONESWEEP>
+// I keys per thread: a tile of RS_T * I keys (RS_I for the fixed-tile paths,
+// RS_I1 for the context's single-pass sort)
+template <bool ONESWEEP, int I = RS_I>
 __global__ void __launch_bounds__(RS_T, 3)
 k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -221,9 +224,10 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              long long *__restrict__ cnt, unsigned *__restrict__ err, uint32_t *status,
              const uint32_t *__restrict__ ghist, uint32_t *tilectr)
 {
+    constexpr int TILE = RS_T * I;
     extern __shared__ __align__(16) unsigned char rs_stage[];
     uint64_t *sk = (uint64_t *)rs_stage;
-    uint32_t *sv = (uint32_t *)(rs_stage + RS_TILE * sizeof(uint64_t));
+    uint32_t *sv = (uint32_t *)(rs_stage + TILE * sizeof(uint64_t));
     __shared__ uint32_t whist[RS_WARPS][256];
     __shared__ uint32_t boff[256];
     __shared__ uint32_t lstart[256];
@@ -237,20 +241,20 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     }
     __syncthreads();
     const int blk = ONESWEEP ? blk_s : (int)blockIdx.x;
-    const int64_t tile0 = (int64_t)blk * RS_TILE;
+    const int64_t tile0 = (int64_t)blk * TILE;
     const int64_t rem = n - tile0;
-    const int tn = rem < RS_TILE ? (int)rem : RS_TILE;   // keys in this tile
-    const int wbase = w * (RS_TILE / RS_WARPS);
+    const int tn = rem < TILE ? (int)rem : TILE;   // keys in this tile
+    const int wbase = w * (TILE / RS_WARPS);
     const unsigned lt = (1u << lane) - 1u;
-    uint64_t key[RS_I];
-    uint32_t rnk[RS_I];
+    uint64_t key[I];
+    uint32_t rnk[I];
 #pragma unroll
-    for (int r = 0; r < RS_I; r++) {
+    for (int r = 0; r < I; r++) {
         const int e = wbase + r * NB_WARP + lane;
         key[r] = e < tn ? kin[tile0 + e] : 0ull;
     }
 #pragma unroll
-    for (int r = 0; r < RS_I; r++) {
+    for (int r = 0; r < I; r++) {
         const bool ok = wbase + r * NB_WARP + lane < tn;
         const int d = ok ? (int)((key[r] >> shift) & 255u) : 256 + lane;
         const unsigned peers = nb_match_bits<8>((unsigned)d, ok);
@@ -337,14 +341,14 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     __syncthreads();
     // values are loaded only now (they need no ranking): fewer registers
     // held through the ranking rounds
-    uint32_t val[RS_I];
+    uint32_t val[I];
 #pragma unroll
-    for (int r = 0; r < RS_I; r++) {
+    for (int r = 0; r < I; r++) {
         const int e = wbase + r * NB_WARP + lane;
         val[r] = e < tn ? vin[tile0 + e] : 0u;
     }
 #pragma unroll
-    for (int r = 0; r < RS_I; r++) {
+    for (int r = 0; r < I; r++) {
         if (wbase + r * NB_WARP + lane < tn) {
             const int d = (int)((key[r] >> shift) & 255u);
             const uint32_t lp = lstart[d] + whist[w][d] + rnk[r];
@@ -371,15 +375,26 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     }
 }
 
+// Keys per thread of the context's single-pass scatter: 12 (tiles of 3072
+// keys) measured best of 10, 12, 13, 14 and 16 on the 2.87M-key sort (build
+// 1.224 against 1.256 ms for 16: 935 tiles keep the 3 x SMs block slots
+// fuller than 701 larger ones).  Any tile size gives the same sort.
+#define RS_I1 12
+
 // the staging buffer is dynamic shared memory above the 48 KB default
+static constexpr int rs_smem(int I)
+{
+    return RS_T * I * (int)(sizeof(uint64_t) + sizeof(uint32_t));
+}
+
 static void rs_setup()
 {
     static bool done = false;
     if (done) return;
     cudaFuncSetAttribute(k_rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          RS_SMEM);
-    cudaFuncSetAttribute(k_rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         RS_SMEM);
+    cudaFuncSetAttribute(k_rs_scatter<true, RS_I1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         rs_smem(RS_I1));
     done = true;
 }
 
@@ -407,10 +422,11 @@ k_rs_ghist(const uint64_t *__restrict__ key, int64_t n, uint32_t *__restrict__ g
 void nb_radix_sort(nb_ctx *c, int64_t n)
 {
     if (n <= 1) return;
-    const int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    const int nb16 = (int)((n + RS_TILE - 1) / RS_TILE);
     rs_setup();
     uint64_t *ka = c->keys, *kb = c->keys_alt;
     uint32_t *va = c->idx, *vb = c->idx_alt;
+    const int nb = (int)((n + (int64_t)RS_T * RS_I1 - 1) / ((int64_t)RS_T * RS_I1));
     if (n < (int64_t)RS_VAL && (int64_t)nb * 256 * 8 + 8 * 256 + 8 <= c->rs_status_len) {
         // onesweep: status words of the 8 passes, the 8 digit histograms and
         // the 8 tile counters, zeroed together
@@ -421,7 +437,7 @@ void nb_radix_sort(nb_ctx *c, int64_t n)
         k_rs_ghist<<<c->num_sms * 4, RS_T, 0, c->stream>>>(ka, n, ghist);
         nb_launched(c, "k_rs_ghist");
         for (int pass = 0; pass < 8; pass++) {
-            k_rs_scatter<true><<<nb, RS_T, RS_SMEM, c->stream>>>(
+            k_rs_scatter<true, RS_I1><<<nb, RS_T, rs_smem(RS_I1), c->stream>>>(
                 ka, va, kb, vb, nullptr, n, 8 * pass, nb, c->cnt, c->err,
                 c->rs_status + (int64_t)pass * nb * 256, ghist + 256 * pass, tctr + pass);
             nb_launched(c, "k_rs_scatter");
@@ -432,13 +448,13 @@ void nb_radix_sort(nb_ctx *c, int64_t n)
     }
     for (int pass = 0; pass < 8; pass++) {
         const int shift = 8 * pass;
-        k_rs_hist<<<nb, RS_T, 0, c->stream>>>(ka, n, shift, c->sort_hist, nb);
+        k_rs_hist<<<nb16, RS_T, 0, c->stream>>>(ka, n, shift, c->sort_hist, nb16);
         nb_launched(c, "k_rs_hist");
         nb_exclusive_scan(c, (const int32_t *)c->sort_hist, (int32_t *)c->sort_hist,
-                          (int64_t)256 * nb, nullptr, nullptr);
-        k_rs_scatter<false><<<nb, RS_T, RS_SMEM, c->stream>>>(ka, va, kb, vb, c->sort_hist, n,
-                                                              shift, nb, c->cnt, c->err, nullptr,
-                                                              nullptr, nullptr);
+                          (int64_t)256 * nb16, nullptr, nullptr);
+        k_rs_scatter<false><<<nb16, RS_T, RS_SMEM, c->stream>>>(ka, va, kb, vb, c->sort_hist, n,
+                                                                shift, nb16, c->cnt, c->err,
+                                                                nullptr, nullptr, nullptr);
         nb_launched(c, "k_rs_scatter");
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
