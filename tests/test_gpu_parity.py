@@ -140,7 +140,9 @@ def test_forces_within_tolerance(oracle_lib, name, precision, tol):
 
 def test_edge_sizes(oracle_lib):
     rng = np.random.default_rng(8)
-    for n in (1, 2, 3, 31, 33, 64, 65, 4095, 4096):
+    # 3071..3073 and 4095, 4096 straddle the radix sort's tiles (3072 keys in the
+    # context's single-pass sort, 4096 in the caller-buffer sort)
+    for n in (1, 2, 3, 31, 33, 64, 65, 3071, 3072, 3073, 4095, 4096):
         pos = rng.normal(size=(n, 3))
         mass = rng.uniform(0.5, 2, n).astype(np.float32)
         for n_crit in (1, 8, 4096):
