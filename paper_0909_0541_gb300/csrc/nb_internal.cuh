@@ -62,6 +62,7 @@ enum {
     CNT_QMAX,        // widest walk frontier
     CNT_MOM_Q,       // moments work queue head (32-cell chunks)
     CNT_MOM_CHUNKS,  // chunks in the moments work list
+    CNT_BBOX_DONE,   // blocks of k_bbox_root that have written their partial box
     CNT_PP_CUM,      // n_pp over every walk (never reset)
     CNT_PC_CUM,
     CNT_BAD_SITE,    // first failed self-check: site code (never reset)

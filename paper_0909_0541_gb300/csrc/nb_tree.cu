@@ -19,9 +19,8 @@
 
 
 // ------------------------------------------------------------ bbox, root
-__global__ void __launch_bounds__(256)
-k_bbox(const double *__restrict__ pos, int64_t n, double *__restrict__ part,
-       unsigned *__restrict__ err)
+__device__ __forceinline__ void bbox_block(const double *__restrict__ pos, int64_t n,
+                                           double *__restrict__ part, unsigned *__restrict__ err)
 {
     // min / max on an order-preserving integer image of the FP64 bits (the
     // FP64 pipe is slow on this part): k = bits for x >= 0, and the low 63
@@ -71,16 +70,24 @@ k_bbox(const double *__restrict__ pos, int64_t n, double *__restrict__ part,
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_bbox(const double *__restrict__ pos, int64_t n, double *__restrict__ part,
+       unsigned *__restrict__ err)
+{
+    bbox_block(pos, n, part, err);
+}
+
 // Root cube: centre = bbox centre, side = max extent * (1 + 2^-20), 1 when
 // every particle coincides; corner = centre - side/2; grid scale 2^21 / side.
-__global__ void __launch_bounds__(256)
-k_root(const double *__restrict__ part, int nblk, double *__restrict__ root)
+// (one block of 256 threads; the partials are read through L2, since in
+// k_bbox_root other blocks of the same launch wrote them)
+__device__ __forceinline__ void root_block(const double *part, int nblk, double *__restrict__ root)
 {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int b = threadIdx.x; b < nblk; b += blockDim.x)
         for (int k = 0; k < 3; k++) {
-            lo[k] = fmin(lo[k], part[6 * b + k]);
-            hi[k] = fmax(hi[k], part[6 * b + 3 + k]);
+            lo[k] = fmin(lo[k], __ldcg(&part[6 * b + k]));
+            hi[k] = fmax(hi[k], __ldcg(&part[6 * b + 3 + k]));
         }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -111,6 +118,33 @@ k_root(const double *__restrict__ part, int nblk, double *__restrict__ root)
     root[3] = L;
     for (int k = 0; k < 3; k++) root[4 + k] = __dsub_rn(root[k], __dmul_rn(0.5, L));
     root[7] = __ddiv_rn(2097152.0, L);
+}
+
+__global__ void __launch_bounds__(256)
+k_root(const double *__restrict__ part, int nblk, double *__restrict__ root)
+{
+    root_block(part, nblk, root);
+}
+
+// k_bbox and k_root in one launch: every block writes its partial box, and
+// the last one to finish (a fenced counter, zeroed with the build's counters)
+// reduces them all into the root cube.  The same min, max and root
+// arithmetic as the two launches.
+__global__ void __launch_bounds__(256)
+k_bbox_root(const double *__restrict__ pos, int64_t n, double *part, unsigned *__restrict__ err,
+            long long *__restrict__ cnt, double *__restrict__ root)
+{
+    __shared__ bool last;
+    bbox_block(pos, n, part, err);
+    __threadfence();   // this block's partial before its arrival
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last = atomicAdd((unsigned long long *)&cnt[CNT_BBOX_DONE], 1ull) ==
+               (unsigned long long)gridDim.x - 1ull;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();   // every partial before the reduction reads them
+    root_block(part, gridDim.x, root);
 }
 
 // ------------------------------------------------------------ Morton keys
@@ -897,10 +931,8 @@ void nb_launch_build(nb_ctx *c, const double *pos, const float *mass, int64_t n)
 {
     cudaStream_t s = c->stream;
     cudaMemsetAsync(c->cnt, 0, sizeof(long long) * CNT_PP_CUM, s);
-    k_bbox<<<c->bbox_blocks, 256, 0, s>>>(pos, n, c->bbox_part, c->err);
-    nb_launched(c, "k_bbox");
-    k_root<<<1, 256, 0, s>>>(c->bbox_part, c->bbox_blocks, c->root);
-    nb_launched(c, "k_root");
+    k_bbox_root<<<c->bbox_blocks, 256, 0, s>>>(pos, n, c->bbox_part, c->err, c->cnt, c->root);
+    nb_launched(c, "k_bbox_root");
     k_keys<<<nb_grid(n, 256), 256, 0, s>>>(pos, n, c->root, nullptr, c->keys, c->idx,
                                            c->key_order);
     nb_launched(c, "k_keys");
