@@ -301,7 +301,8 @@ int nb_graph_launch(nb_ctx *ctx);
  * is given, as nb_build_tree_batched; one system when it is NULL -- then
  * times `reps` walk + FP32 force passes with CUDA events for every n_crit of
  * the list x force work-item width (32 or 64 targets per warp) x j-tile depth
- * (32 or 64 list records staged per tile) x force block size (256 or 128
+ * (32 or 64 list records staged per tile; items of several source streams
+ * stage 64 either way) x force block size (256 or 128
  * threads), keeps the fastest combination in the context (cfg.n_crit and the
  * FP32 force shape used from then on) and returns it in the best_* outputs
  * (each nullable); ms_host (nullable, 8 x ncand) receives the mean times,
